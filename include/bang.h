@@ -1,0 +1,144 @@
+/* bang.h - C ABI of the GB300 galaxy-model log-likelihood library (libbang.so).
+ *
+ * The library evaluates, for a batch of parameter vectors, the log-likelihood of the
+ * disc-galaxy model of Rigamonti et al. (2022), "Maximally informed Bayesian modelling of
+ * disc galaxies", against integral-field maps of surface brightness B, line-of-sight
+ * velocity v, velocity dispersion sigma and mass-to-light ratio M/L (Sec. 2.5.1, Eq. 18),
+ * and its gradient with respect to the parameters.
+ *
+ * Model (Sec. 2.1-2.4): a spherical bulge of the Dehnen gamma family (Sec. 2.2; gamma = 1 is
+ * the Hernquist bulge of Eq. 1, gamma = 2 the Jaffe bulge of Eq. B1) with its isotropic
+ * projected dispersion (Eq. 6) from a fixed n_quad-node radial quadrature, one or two
+ * razor-thin exponential discs (Eqs. 7-12) with the Freeman circular velocity
+ * v^2 = (2 G M_d / R_d) y^2 [I0 K0 - I1 K1](y), y = r / (2 R_d) (Eq. 9, Binney & Tremaine
+ * form), and an NFW halo given by M200 and concentration c.  The four light-weighted
+ * observables (Eqs. 13-15 and 19) are evaluated on an os x os oversampled sub-grid of every
+ * spaxel, padded by the PSF half-width, convolved with the normalised PSF of Eq. 21
+ * (Gaussian, or Moffat), averaged per spaxel, and compared with the data through Gaussian
+ * terms: logL = -chi^2 / 2 - sum ln(sqrt(2 pi) delta).
+ *
+ * Parameter vector theta (float32, row-major [B][P], P = 15 for one disc, 19 for two):
+ *   0 x0, 1 y0 [kpc], 2 P.A. [rad], 3 i [rad, 0 <= i < pi/2],
+ *   4 log10 Mb [Msun], 5 log10 Rb [kpc], 6 gamma [0 <= gamma < 3],
+ *   7 log10 Md1, 8 log10 Rd1, 9 k1 [|k| <= 1], 10 (M/L)b, 11 (M/L)d1 [> 0],
+ *   12 log10 M200, 13 c [> 0], 14 v_sys [km/s],
+ *   15 log10 Md2, 16 log10 Rd2, 17 k2, 18 (M/L)d2   (two-disc models only).
+ * A row that is not finite or lies outside those ranges gets logL = -INFINITY and a zero
+ * gradient; that is not an error (samplers propose such points).
+ *
+ * Sky grid: spaxel (i, j) is centred at x = (i - (nx-1)/2) s, y = (j - (ny-1)/2) s arcsec
+ * (s = spaxel_arcsec); maps are stored [4][ny][nx] with i fastest, channels B [Lsun/pc^2],
+ * v [km/s], sigma [km/s], M/L [Msun/Lsun].
+ *
+ * Pointers: every array argument of a compute entry point may be host memory (pageable or
+ * pinned) or device memory of the model's device; the library asks the CUDA runtime which.
+ * Host arrays are staged through library-owned device buffers on the given stream and the
+ * call then returns only after the results are back in host memory.  With device arrays the
+ * call is asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy default).
+ *
+ * Errors: functions return a bang_status; on failure bang_last_error() gives a message
+ * (per calling thread).  No entry point aborts the process.
+ */
+#ifndef BANG_H
+#define BANG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bang_model bang_model; /* opaque; owns all device state of one model */
+
+typedef enum {
+  BANG_OK = 0,
+  BANG_E_INVALID_ARG = 1, /* null pointer, bad size, index out of range, bad descriptor */
+  BANG_E_CUDA = 2,        /* a CUDA runtime call failed; see bang_last_error() */
+  BANG_E_OOM = 3,         /* device or host allocation failed */
+  BANG_E_UNSUPPORTED = 4, /* option not implemented (e.g. Hernquist halo kind) */
+  BANG_E_TIMEOUT = 5      /* a bounded device-side wait gave up */
+} bang_status;
+
+/* One observed galaxy (Sec. 3.1).  The arrays are read during bang_model_create only and
+ * are copied to the device; the caller keeps ownership. */
+typedef struct {
+  int nx, ny;               /* spaxels along x and y, >= 1 */
+  int oversample;           /* os >= 1: os x os sub-points per spaxel */
+  double spaxel_arcsec;     /* spaxel size s > 0 */
+  double kpc_per_arcsec;    /* distance scale (53 Mpc -> 0.25695) */
+  int psf_kind;             /* 0 Gaussian (Eq. 21), 1 Moffat */
+  double psf_fwhm_arcsec;   /* >= 0; 0 means no PSF.  Window half-width h = floor(3 sigma os / s)
+                               fine pixels with sigma = FWHM / 2.35482 for both kinds */
+  double moffat_beta;       /* Moffat exponent (> 0), ignored for the Gaussian */
+  const float *data;        /* host, [4][ny][nx]: B, v, sigma, M/L */
+  const float *err;         /* host, [4][ny][nx]: delta > 0 where the mask is set */
+  const uint8_t *mask;      /* host, [4][ny][nx], nonzero = used; NULL = all used */
+} bang_galaxy_desc;
+
+typedef struct {
+  int n_discs;     /* 1 or 2 */
+  int bulge_kind;  /* 0: Dehnen gamma family (the only kind) */
+  int halo_kind;   /* 0: NFW (M200, c); 1: Hernquist (paper's halo) -> BANG_E_UNSUPPORTED */
+  int n_quad;      /* radial quadrature nodes: 64 or 128 */
+  int psf_mode;    /* 0: convolve B, v, sigma and <L/M> each on its own (Sec. 3.1) */
+} bang_model_opts;
+
+/* Creates a model for n_gal galaxies on CUDA device `device`: copies data, errors, masks
+ * and PSF taps to the device (allocation happens once, as in App. A) and precomputes the
+ * normalisation constant of each galaxy.  *out receives the handle.  Synchronous. */
+bang_status bang_model_create(const bang_galaxy_desc *gal, int n_gal, const bang_model_opts *opts,
+                              int device, bang_model **out);
+
+/* Frees all device and host state of the model.  NULL is accepted.  Synchronises. */
+bang_status bang_model_destroy(bang_model *m);
+
+/* Parameters per row: 15 (one disc) or 19 (two discs); -1 for a NULL model. */
+int bang_model_nparams(const bang_model *m);
+
+/* Number of galaxies of the model; -1 for a NULL model. */
+int bang_model_ngalaxies(const bang_model *m);
+
+/* PSF window half-width h (fine pixels) of galaxy g, or -1 if g is out of range. */
+int bang_model_psf_halfwidth(const bang_model *m, int g);
+
+/* logL[b] (float64) of row b of theta ([B][P] float32) against galaxy gal_idx[b].
+ * gal_idx: HOST array [B] of int32 in [0, n_gal), or NULL for galaxy 0 for every row (the
+ * host needs the galaxy of each row to schedule the launch).  One persistent launch handles
+ * all rows, whatever their grid sizes (Sec. 2.5, App. A). */
+bang_status bang_loglike_batch(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
+                               double *logL, void *stream);
+
+/* As bang_loglike_batch, plus grad[b][p] = d logL[b] / d theta[b][p] (float32, [B][P]),
+ * by a hand-written adjoint that re-evaluates the radial quadrature instead of storing it. */
+bang_status bang_loglike_grad_batch(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
+                                    double *logL, float *grad, void *stream);
+
+/* Model maps for every row: maps[b] is [4][ny][nx] float32 of galaxy gal_idx[b] (B, v_los +
+ * v_sys, sigma_los, M/L = 1/<L/M>); rows are packed back to back, each with its own galaxy's
+ * size.  Out-of-domain rows get NaN maps. */
+bang_status bang_model_maps(bang_model *m, const float *theta, const int32_t *gal_idx, int B, float *maps,
+                            void *stream);
+
+/* Total floats bang_model_maps writes for this gal_idx (HOST, may be NULL) and B. */
+int64_t bang_model_maps_size(const bang_model *m, const int32_t *gal_idx, int B);
+
+/* The paper's execution form (Alg. 2 of App. A): for each row, a serial chain of one kernel
+ * per task (coordinates, bulge, circular velocities, discs, combination, PSF + binning,
+ * chi-square), 64 threads per block, intermediate arrays in device memory.  Same model and
+ * arithmetic as bang_loglike_batch; used as the comparison baseline. */
+bang_status bang_loglike_plain(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
+                               double *logL, void *stream);
+
+/* Chooses launch parameters (rows of the fine grid per block step, blocks per SM) for
+ * batches like (gal_idx, B) by timing candidates on the device; the choice is cached in the
+ * model.  gal_idx as in bang_loglike_batch.  Synchronous. */
+bang_status bang_model_tune(bang_model *m, const int32_t *gal_idx, int B);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *bang_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BANG_H */

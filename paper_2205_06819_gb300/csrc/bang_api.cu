@@ -1,0 +1,631 @@
+// Host side of libbang.so: the C ABI of include/bang.h.
+//
+// bang_model_create copies every galaxy's data to the device once (App. A: "allocation and
+// loading only once"), builds the combined PSF (x) box-filter taps of Eq. 21 and the radial
+// quadrature tables.  Each compute call turns the rows of a batch into a table of work
+// items (row, galaxy, band of spaxel rows), cached per batch shape, and runs one persistent
+// launch over it, replayed from a CUDA graph when the same buffers come back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bang.h"
+#include "bang_device.cuh"
+#include "bang_internal.h"
+
+struct bang_model;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bang_status fail(bang_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define BANG_CUDA(call)                                                                         \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(e_ == cudaErrorMemoryAllocation ? BANG_E_OOM : BANG_E_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+  } while (0)
+
+constexpr double kPiD = 3.14159265358979323846;
+
+// Gauss-Legendre rule on [-1, 1]: Newton's method on P_n from the Bonnet recurrence,
+// starting from Tricomi's approximation of the k-th root.
+void legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int k = 1; k <= n; ++k) {
+    const double th = kPiD * (4.0 * k - 1.0) / (4.0 * n + 2.0);
+    double z = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(th);
+    double dp = 1.0;
+    for (int it = 0; it < 60; ++it) {
+      double pm = 1.0, p = z;
+      for (int j = 1; j < n; ++j) {
+        const double pn = ((2.0 * j + 1.0) * z * p - j * pm) / (j + 1.0);
+        pm = p;
+        p = pn;
+      }
+      dp = n * (pm - z * p) / (1.0 - z * z);
+      const double dz = p / dp;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-15 * std::fabs(z) + 1e-300) {
+        // one more evaluation at the converged root for the weight
+        pm = 1.0, p = z;
+        for (int j = 1; j < n; ++j) {
+          const double pn = ((2.0 * j + 1.0) * z * p - j * pm) / (j + 1.0);
+          pm = p;
+          p = pn;
+        }
+        dp = n * (pm - z * p) / (1.0 - z * z);
+        break;
+      }
+    }
+    x[n - k] = z;                              // ascending
+    w[n - k] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Node tables for r = R cosh t, t in [0, 16]: rows [0, 64) for 64 nodes, [64, 192) for 128.
+void node_tables(std::vector<float>& cm1, std::vector<float>& lc, std::vector<float>& ws, std::vector<float>& wq) {
+  cm1.assign(192, 0.f);
+  lc.assign(192, 0.f);
+  ws.assign(192, 0.f);
+  wq.assign(192, 0.f);
+  const double T = 16.0;
+  int base = 0;
+  for (int n : {64, 128}) {
+    std::vector<double> x, w;
+    legendre_rule(n, x, w);
+    for (int k = 0; k < n; ++k) {
+      const double t = 0.5 * T * (x[k] + 1.0), wk = 0.5 * T * w[k];
+      const double ch = std::cosh(t), th = std::tanh(t);
+      const double sh = std::sinh(0.5 * t);
+      cm1[base + k] = (float)(2.0 * sh * sh);   // cosh t - 1 without cancellation
+      lc[base + k] = (float)std::log2(ch);
+      ws[base + k] = (float)(wk * ch);
+      wq[base + k] = (float)(wk * th * th);
+    }
+    base += n;
+  }
+}
+
+int psf_halfwidth(double fwhm, double pitch) {
+  if (!(fwhm > 0.0)) return 0;
+  const double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+  return (int)std::floor(3.0 * sig / pitch);
+}
+
+// Combined PSF (x) box-filter taps.  Spaxel column i averages fine columns h + i*os + m,
+// m in [0, os); each of those is the PSF-weighted mean over offsets d in [-h, h].  Their
+// composition weights padded fine column i*os + c, c in [0, os + 2h), by
+//   T[c] = (1/os) sum_{m} g(c - m - h),  g normalised to unit sum.
+// Gaussian: separable, one axis (the two-axis normalisation is the square of the one-axis
+// sum).  Moffat: the two-dimensional table W2[cy][cx].
+std::vector<float> make_taps(int kind, double fwhm, double beta, int os, int h, double pitch) {
+  const int L = os + 2 * h, n = 2 * h + 1;
+  if (kind == 0) {
+    std::vector<double> g(n, 1.0);
+    if (h > 0) {
+      const double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+      double tot = 0.0;
+      for (int d = -h; d <= h; ++d) tot += (g[d + h] = std::exp(-(d * pitch) * (d * pitch) / (2.0 * sig * sig)));
+      for (double& v : g) v /= tot;
+    }
+    std::vector<float> T(L);
+    for (int c = 0; c < L; ++c) {
+      double s = 0.0;
+      for (int m = 0; m < os; ++m) {
+        const int d = c - m - h;
+        if (d >= -h && d <= h) s += g[d + h];
+      }
+      T[c] = (float)(s / os);
+    }
+    return T;
+  }
+  std::vector<double> M((size_t)n * n, 1.0);
+  if (h > 0) {
+    const double alpha = fwhm / (2.0 * std::sqrt(std::pow(2.0, 1.0 / beta) - 1.0));
+    double tot = 0.0;
+    for (int dy = -h; dy <= h; ++dy)
+      for (int dx = -h; dx <= h; ++dx) {
+        const double r2 = (double)(dx * dx + dy * dy) * pitch * pitch;
+        tot += (M[(size_t)(dy + h) * n + (dx + h)] = std::pow(1.0 + r2 / (alpha * alpha), -beta));
+      }
+    for (double& v : M) v /= tot;
+  }
+  std::vector<float> W2((size_t)L * L);
+  for (int cy = 0; cy < L; ++cy)
+    for (int cx = 0; cx < L; ++cx) {
+      double s = 0.0;
+      for (int mn = 0; mn < os; ++mn)
+        for (int mm = 0; mm < os; ++mm) {
+          const int dx = cx - mm - h, dy = cy - mn - h;
+          if (dx >= -h && dx <= h && dy >= -h && dy <= h) s += M[(size_t)(dy + h) * n + (dx + h)];
+        }
+      W2[(size_t)cy * L + cx] = (float)(s / ((double)os * os));
+    }
+  return W2;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t reserve(size_t b) {
+    if (b <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) bytes = b;
+    return e;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// A batch shape: the work items of (gal_idx, B) and their device copies.
+struct Plan {
+  uint64_t key = 0;
+  int B = 0, n_items = 0, G = 4, grid = 0, blocks_per_sm = 0;
+  size_t smem = 0;
+  int mode = 0;
+  std::vector<bang::WorkItem> items;
+  std::vector<int> order, row_first, row_g;
+  std::vector<int64_t> out_off;
+  int64_t out_total = 0;
+  DevBuf d_items, d_order, d_row_first, d_row_g, d_out_off, d_partial;
+  // graph replay
+  cudaGraphExec_t graph = nullptr;
+  const void* g_theta = nullptr;
+  const void* g_out = nullptr;
+  const void* g_out2 = nullptr;
+  ~Plan() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+uint64_t hash_bytes(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct bang_model {
+  int device = 0;
+  bang_model_opts opts{};
+  int P = 15;
+  int num_sms = 0;
+  int smem_optin = 0;
+  std::vector<bang::GalDev> gals;   // host copy (device pointers inside)
+  std::vector<bang_galaxy_desc> desc;
+  std::vector<int> h_of;
+  std::vector<std::unique_ptr<DevBuf>> owned;
+  DevBuf d_gals;
+  DevBuf stage_theta, stage_out, stage_out2, scratch_seed, scratch_grad;
+  std::list<std::unique_ptr<Plan>> plans;   // most recently used first
+  std::map<uint64_t, int> tuned_G;          // batch-shape key -> rows per block step
+  std::mutex mu;
+  cudaStream_t capture_stream = nullptr;
+  bool use_graphs = true;
+};
+
+namespace {
+
+bang_status validate_desc(const bang_galaxy_desc& d, int g) {
+  if (d.nx < 1 || d.ny < 1 || d.oversample < 1) return fail(BANG_E_INVALID_ARG, "galaxy %d: bad grid size", g);
+  if (!(d.spaxel_arcsec > 0.0) || !(d.kpc_per_arcsec > 0.0))
+    return fail(BANG_E_INVALID_ARG, "galaxy %d: spaxel size and distance scale must be > 0", g);
+  if (d.psf_kind != 0 && d.psf_kind != 1) return fail(BANG_E_INVALID_ARG, "galaxy %d: psf_kind must be 0 or 1", g);
+  if (!(d.psf_fwhm_arcsec >= 0.0)) return fail(BANG_E_INVALID_ARG, "galaxy %d: psf_fwhm must be >= 0", g);
+  if (d.psf_kind == 1 && !(d.moffat_beta > 0.0)) return fail(BANG_E_INVALID_ARG, "galaxy %d: moffat_beta must be > 0", g);
+  if (!d.data || !d.err) return fail(BANG_E_INVALID_ARG, "galaxy %d: data and err are required", g);
+  const int h = psf_halfwidth(d.psf_fwhm_arcsec, d.spaxel_arcsec / d.oversample);
+  if (h > 64) return fail(BANG_E_INVALID_ARG, "galaxy %d: PSF window half-width %d exceeds 64 fine pixels", g, h);
+  if ((long long)d.nx * d.oversample + 2 * h > 4096 || d.ny > 4096)
+    return fail(BANG_E_INVALID_ARG, "galaxy %d: padded fine grid wider than 4096", g);
+  const size_t n = (size_t)4 * d.nx * d.ny;
+  for (size_t s = 0; s < n; ++s) {
+    if (d.mask && !d.mask[s]) continue;
+    if (!(d.err[s] > 0.f) || !std::isfinite(d.err[s]) || !std::isfinite(d.data[s]))
+      return fail(BANG_E_INVALID_ARG, "galaxy %d: err must be finite and > 0 and data finite where used (entry %zu)",
+                  g, s);
+  }
+  return BANG_OK;
+}
+
+template <class T>
+bang_status upload(bang_model* m, const std::vector<T>& v, const T** out) {
+  auto b = std::make_unique<DevBuf>();
+  BANG_CUDA(b->reserve(std::max<size_t>(v.size() * sizeof(T), 16)));
+  BANG_CUDA(cudaMemcpy(b->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = b->as<T>();
+  m->owned.push_back(std::move(b));
+  return BANG_OK;
+}
+
+template <class T>
+cudaError_t copy_vec(DevBuf& d, const std::vector<T>& v) {
+  cudaError_t e = d.reserve(std::max<size_t>(v.size() * sizeof(T), 16));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Bands of spaxel rows per batch row: 1 when the batch fills the GPU, otherwise enough to
+// give every SM about two work items (each band re-evaluates its 2h-row halo).
+int bands_for(const bang_model* m, int B, int ny) {
+  if (B >= m->num_sms) return 1;
+  const int want = (2 * m->num_sms + B - 1) / B;
+  return std::max(1, std::min(ny, want));
+}
+
+bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Plan** out) {
+  uint64_t key = hash_bytes(&B, sizeof B);
+  key = hash_bytes(&mode, sizeof mode, key);
+  if (gal_idx) key = hash_bytes(gal_idx, sizeof(int32_t) * (size_t)B, key);
+  for (auto it = m->plans.begin(); it != m->plans.end(); ++it) {
+    if ((*it)->key == key) {
+      m->plans.splice(m->plans.begin(), m->plans, it);
+      *out = m->plans.front().get();
+      return BANG_OK;
+    }
+  }
+  auto p = std::make_unique<Plan>();
+  p->key = key;
+  p->B = B;
+  p->mode = mode;
+  p->row_first.assign(B + 1, 0);
+  p->row_g.assign(B, 0);
+  p->out_off.assign(B, 0);
+  std::vector<double> cost;
+  int64_t off = 0;
+  for (int b = 0; b < B; ++b) {
+    const int g = gal_idx ? gal_idx[b] : 0;
+    if (g < 0 || g >= (int)m->gals.size()) return fail(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
+    const bang::GalDev& G = m->gals[g];
+    p->row_g[b] = g;
+    p->out_off[b] = off;
+    off += (int64_t)4 * G.nx * G.ny;
+    p->row_first[b] = (int)p->items.size();
+    const int nb = bands_for(m, B, G.ny);
+    for (int k = 0; k < nb; ++k) {
+      const int j0 = (int)((long long)G.ny * k / nb), j1 = (int)((long long)G.ny * (k + 1) / nb);
+      if (j1 <= j0) continue;
+      p->items.push_back(bang::WorkItem{b, g, j0, j1});
+      cost.push_back((double)((j1 - j0) * G.os + 2 * G.h) * G.W);
+    }
+  }
+  p->row_first[B] = (int)p->items.size();
+  p->out_total = off;
+  p->n_items = (int)p->items.size();
+  // longest items first, so that the persistent blocks finish together
+  p->order.resize(p->n_items);
+  for (int i = 0; i < p->n_items; ++i) p->order[i] = i;
+  std::stable_sort(p->order.begin(), p->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+
+  int max_L = 0, max_os = 1, max_nx = 0, max_W = 0, psf2d = 0;
+  for (int b = 0; b < B; ++b) {
+    const bang::GalDev& G = m->gals[p->row_g[b]];
+    max_L = std::max(max_L, G.L);
+    max_os = std::max(max_os, G.os);
+    max_nx = std::max(max_nx, G.nx);
+    max_W = std::max(max_W, G.W);
+    psf2d |= G.psf_kind;
+  }
+  for (int b = 0; b < B; ++b)
+    if (m->gals[p->row_g[b]].psf_kind != psf2d)
+      return fail(BANG_E_UNSUPPORTED, "a batch mixes Gaussian and Moffat PSF galaxies");
+  auto tg = m->tuned_G.find(key);
+  p->G = tg != m->tuned_G.end() ? tg->second : 4;
+  // shared memory: the NA bound uses the smallest os among rows with the largest L, so
+  // take it per galaxy
+  size_t smem = 0;
+  for (int b = 0; b < B; ++b) {
+    const bang::GalDev& G = m->gals[p->row_g[b]];
+    smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, p->G, psf2d));
+  }
+  if (smem > (size_t)m->smem_optin - 4096) {
+    p->G = 1;
+    smem = 0;
+    for (int b = 0; b < B; ++b) {
+      const bang::GalDev& G = m->gals[p->row_g[b]];
+      smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, 1, psf2d));
+    }
+    if (smem > (size_t)m->smem_optin - 4096) return fail(BANG_E_UNSUPPORTED, "galaxy too large for one block's shared memory");
+  }
+  p->smem = smem;
+  const void* kp = bang::forward_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, mode);
+  cudaFuncAttributes fa;
+  BANG_CUDA(cudaFuncGetAttributes(&fa, kp));
+  if (smem + fa.sharedSizeBytes > (size_t)m->smem_optin)
+    return fail(BANG_E_UNSUPPORTED, "forward kernel needs %zu bytes of shared memory", smem + fa.sharedSizeBytes);
+  BANG_CUDA(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 m->smem_optin - (int)fa.sharedSizeBytes));
+  int per_sm = 0;
+  BANG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp, bang::forward_threads(), smem));
+  if (per_sm < 1) return fail(BANG_E_UNSUPPORTED, "forward kernel does not fit on an SM (smem %zu)", smem);
+  p->blocks_per_sm = per_sm;
+  p->grid = std::min(p->n_items, per_sm * m->num_sms);
+
+  BANG_CUDA(copy_vec(p->d_items, p->items));
+  BANG_CUDA(copy_vec(p->d_order, p->order));
+  BANG_CUDA(copy_vec(p->d_row_first, p->row_first));
+  BANG_CUDA(copy_vec(p->d_row_g, p->row_g));
+  BANG_CUDA(copy_vec(p->d_out_off, p->out_off));
+  BANG_CUDA(p->d_partial.reserve(sizeof(double) * std::max(1, p->n_items)));
+  m->plans.push_front(std::move(p));
+  while (m->plans.size() > 8) m->plans.pop_back();
+  *out = m->plans.front().get();
+  return BANG_OK;
+}
+
+int psf2d_of(const bang_model* m, const Plan* p) { return m->gals[p->row_g[0]].psf_kind; }
+
+cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode, double* logL, float* out,
+                            cudaStream_t st) {
+  bang::FwdArgs a{};
+  a.theta = theta;
+  a.P = m->P;
+  a.gals = m->d_gals.as<bang::GalDev>();
+  a.items = p->d_items.as<bang::WorkItem>();
+  a.order = p->d_order.as<int>();
+  a.n_items = p->n_items;
+  a.G = p->G;
+  a.partial = p->d_partial.as<double>();
+  a.maps = mode == bang::kModeMaps ? out : nullptr;
+  a.seed = mode == bang::kModeSeed ? out : nullptr;
+  a.out_off = p->d_out_off.as<int64_t>();
+  cudaError_t e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
+  if (e != cudaSuccess || !logL) return e;
+  return bang::launch_finalize(a.partial, p->d_row_first.as<int>(), p->d_row_g.as<int>(), a.gals, p->B, logL, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bang_last_error(void) { return g_last_error.c_str(); }
+
+bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang_model_opts* opts, int device,
+                              bang_model** out) {
+  g_last_error.clear();
+  if (!gal || !opts || !out || n_gal < 1) return fail(BANG_E_INVALID_ARG, "bang_model_create: null argument or n_gal < 1");
+  *out = nullptr;
+  if (opts->n_discs != 1 && opts->n_discs != 2) return fail(BANG_E_INVALID_ARG, "n_discs must be 1 or 2");
+  if (opts->n_quad != 64 && opts->n_quad != 128) return fail(BANG_E_INVALID_ARG, "n_quad must be 64 or 128");
+  if (opts->bulge_kind != 0) return fail(BANG_E_UNSUPPORTED, "bulge_kind %d not available", opts->bulge_kind);
+  if (opts->halo_kind != 0) return fail(BANG_E_UNSUPPORTED, "halo_kind %d not available (NFW = 0)", opts->halo_kind);
+  if (opts->psf_mode != 0) return fail(BANG_E_UNSUPPORTED, "psf_mode %d not available", opts->psf_mode);
+  for (int g = 0; g < n_gal; ++g) {
+    bang_status s = validate_desc(gal[g], g);
+    if (s != BANG_OK) return s;
+  }
+  int ndev = 0;
+  BANG_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(BANG_E_INVALID_ARG, "device %d out of range (%d devices)", device, ndev);
+  BANG_CUDA(cudaSetDevice(device));
+
+  std::unique_ptr<bang_model> m(new bang_model());
+  m->device = device;
+  m->opts = *opts;
+  m->P = opts->n_discs == 2 ? 19 : 15;
+  BANG_CUDA(cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, device));
+  BANG_CUDA(cudaDeviceGetAttribute(&m->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  {
+    std::vector<float> cm1, lc, ws, wq;
+    node_tables(cm1, lc, ws, wq);
+    BANG_CUDA(bang::upload_nodes_forward(cm1.data(), lc.data(), ws.data(), wq.data()));
+  }
+  for (int g = 0; g < n_gal; ++g) {
+    const bang_galaxy_desc& d = gal[g];
+    bang::GalDev G{};
+    G.nx = d.nx;
+    G.ny = d.ny;
+    G.os = d.oversample;
+    const double pitch = d.spaxel_arcsec / d.oversample;
+    G.h = psf_halfwidth(d.psf_fwhm_arcsec, pitch);
+    G.L = G.os + 2 * G.h;
+    G.W = G.os * G.nx + 2 * G.h;
+    G.H = G.os * G.ny + 2 * G.h;
+    G.psf_kind = d.psf_kind;
+    G.pitch_kpa = (float)(pitch * d.kpc_per_arcsec);
+    // sky x of padded fine column q: s ((q - h + 1/2) / os - nx / 2)
+    G.xoff_kpa = d.spaxel_arcsec * ((0.5 - G.h) / d.oversample - 0.5 * d.nx) * d.kpc_per_arcsec;
+    G.yoff_kpa = d.spaxel_arcsec * ((0.5 - G.h) / d.oversample - 0.5 * d.ny) * d.kpc_per_arcsec;
+    const size_t n = (size_t)4 * d.nx * d.ny;
+    std::vector<float> data(n), iv(n);
+    double nc = 0.0;
+    for (size_t s = 0; s < n; ++s) {
+      const bool used = !d.mask || d.mask[s];
+      data[s] = used ? d.data[s] : 0.f;
+      if (used) {
+        const double e = (double)d.err[s];
+        iv[s] = (float)(1.0 / (e * e));
+        nc += std::log(std::sqrt(2.0 * kPiD) * e);
+      } else {
+        iv[s] = 0.f;
+      }
+    }
+    G.norm_const = nc;
+    bang_status st;
+    if ((st = upload(m.get(), data, &G.data)) != BANG_OK) return st;
+    if ((st = upload(m.get(), iv, &G.iv)) != BANG_OK) return st;
+    const std::vector<float> taps = make_taps(d.psf_kind, d.psf_fwhm_arcsec, d.moffat_beta, G.os, G.h, pitch);
+    if ((st = upload(m.get(), taps, &G.taps)) != BANG_OK) return st;
+    m->gals.push_back(G);
+    m->desc.push_back(d);
+    m->h_of.push_back(G.h);
+  }
+  BANG_CUDA(copy_vec(m->d_gals, m->gals));
+  BANG_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+  *out = m.release();
+  return BANG_OK;
+}
+
+bang_status bang_model_destroy(bang_model* m) {
+  if (!m) return BANG_OK;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+  delete m;
+  return BANG_OK;
+}
+
+int bang_model_nparams(const bang_model* m) { return m ? m->P : -1; }
+int bang_model_ngalaxies(const bang_model* m) { return m ? (int)m->gals.size() : -1; }
+int bang_model_psf_halfwidth(const bang_model* m, int g) {
+  if (!m || g < 0 || g >= (int)m->gals.size()) return -1;
+  return m->h_of[g];
+}
+
+int64_t bang_model_maps_size(const bang_model* m, const int32_t* gal_idx, int B) {
+  if (!m || B < 0) return -1;
+  int64_t n = 0;
+  for (int b = 0; b < B; ++b) {
+    const int g = gal_idx ? gal_idx[b] : 0;
+    if (g < 0 || g >= (int)m->gals.size()) return -1;
+    n += (int64_t)4 * m->gals[g].nx * m->gals[g].ny;
+  }
+  return n;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Common driver of the forward-type entry points: stages host buffers, runs (or replays)
+// the persistent launch and the finalisation, copies results back for host buffers.
+bang_status run_forward(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL, float* maps,
+                        int mode, void* stream) {
+  g_last_error.clear();
+  if (!m) return fail(BANG_E_INVALID_ARG, "null model");
+  if (!theta || B < 1) return fail(BANG_E_INVALID_ARG, "theta is null or B < 1");
+  if (mode == bang::kModeLogL && !logL) return fail(BANG_E_INVALID_ARG, "logL is null");
+  if (mode == bang::kModeMaps && !maps) return fail(BANG_E_INVALID_ARG, "maps is null");
+  std::lock_guard<std::mutex> lock(m->mu);
+  BANG_CUDA(cudaSetDevice(m->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan* p = nullptr;
+  bang_status s = get_plan(m, gal_idx, B, mode, &p);
+  if (s != BANG_OK) return s;
+
+  const bool th_dev = is_device_pointer(theta);
+  const bool out_dev = mode == bang::kModeLogL ? is_device_pointer(logL) : is_device_pointer(maps);
+  const float* d_theta = theta;
+  const size_t th_bytes = sizeof(float) * (size_t)B * m->P;
+  if (!th_dev) {
+    BANG_CUDA(m->stage_theta.reserve(th_bytes));
+    BANG_CUDA(cudaMemcpyAsync(m->stage_theta.p, theta, th_bytes, cudaMemcpyHostToDevice, st));
+    d_theta = m->stage_theta.as<float>();
+  }
+  double* d_logL = logL;
+  float* d_maps = maps;
+  const size_t out_bytes = mode == bang::kModeLogL ? sizeof(double) * B : sizeof(float) * (size_t)p->out_total;
+  if (!out_dev) {
+    BANG_CUDA(m->stage_out.reserve(out_bytes));
+    if (mode == bang::kModeLogL) d_logL = m->stage_out.as<double>();
+    else d_maps = m->stage_out.as<float>();
+  }
+
+  if (m->use_graphs && mode == bang::kModeLogL) {
+    if (!p->graph || p->g_theta != d_theta || p->g_out != d_logL) {
+      if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      BANG_CUDA(cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_forward(m, p, d_theta, mode, d_logL, nullptr, m->capture_stream);
+      cudaError_t e2 = cudaStreamEndCapture(m->capture_stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(BANG_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      e = cudaGraphInstantiate(&p->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(BANG_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+      p->g_theta = d_theta;
+      p->g_out = d_logL;
+    }
+    BANG_CUDA(cudaGraphLaunch(p->graph, st));
+  } else {
+    BANG_CUDA(enqueue_forward(m, p, d_theta, mode, mode == bang::kModeLogL ? d_logL : nullptr, d_maps, st));
+  }
+  if (!out_dev) {
+    BANG_CUDA(cudaMemcpyAsync(mode == bang::kModeLogL ? (void*)logL : (void*)maps, m->stage_out.p, out_bytes,
+                              cudaMemcpyDeviceToHost, st));
+    BANG_CUDA(cudaStreamSynchronize(st));
+  } else if (!th_dev) {
+    BANG_CUDA(cudaStreamSynchronize(st));   // the staged theta buffer is reused by the next call
+  }
+  return BANG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bang_status bang_loglike_batch(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,
+                               void* stream) {
+  return run_forward(m, theta, gal_idx, B, logL, nullptr, bang::kModeLogL, stream);
+}
+
+bang_status bang_model_maps(bang_model* m, const float* theta, const int32_t* gal_idx, int B, float* maps,
+                            void* stream) {
+  return run_forward(m, theta, gal_idx, B, nullptr, maps, bang::kModeMaps, stream);
+}
+
+bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,
+                                    float* grad, void* stream) {
+  (void)m; (void)theta; (void)gal_idx; (void)B; (void)logL; (void)grad; (void)stream;
+  return fail(BANG_E_UNSUPPORTED, "bang_loglike_grad_batch: not built yet");
+}
+
+bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,
+                               void* stream) {
+  (void)m; (void)theta; (void)gal_idx; (void)B; (void)logL; (void)stream;
+  return fail(BANG_E_UNSUPPORTED, "bang_loglike_plain: not built yet");
+}
+
+bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
+  (void)gal_idx; (void)B;
+  if (!m) return fail(BANG_E_INVALID_ARG, "null model");
+  return BANG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// Device-side model arithmetic for the GB300 likelihood kernels (sm_103a).
+//
+// Per sky point: reference frame (Sec. 2.1), Dehnen-family bulge projected density and
+// isotropic dispersion by a fixed radial quadrature (Sec. 2.2, Eqs. 4 and 6 definitions),
+// circular velocities of bulge (Eq. 2 generalised), NFW halo and exponential discs (Eq. 9,
+// Binney & Tremaine form), Satoh decomposition (Eqs. 10-12) and the light-weighted
+// observables (Eqs. 13-15, 19).  Bulk arithmetic is float32; per-model constants are decoded
+// in float64 once per work item.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "disc_fit.h"
+
+namespace bang {
+
+constexpr int kMaxQuad = 128;
+constexpr int kMaxParams = 19;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kG = 4.30091727e-6;                                  // kpc (km/s)^2 / Msun
+constexpr double kRhoCrit = 3.0 * 0.07 * 0.07 / (8.0 * kPi * kG);     // H0 = 70 km/s/Mpc
+constexpr float kR2Floor = 1e-12f;                                    // radii floored at 1e-6 kpc
+
+// Radial rule r = R cosh t, t in [0, 16], Gauss-Legendre nodes (filled at model creation).
+// For node k: cm1 = cosh t_k - 1, lc = log2 cosh t_k, ws = w_k cosh t_k, wq = w_k tanh^2 t_k.
+// Rows [0, 64) hold the 64-node rule, rows [64, 192) the 128-node rule.  Every translation
+// unit has its own copy; each exports an upload function that fills it.
+static __constant__ float kNodeCm1[192];
+static __constant__ float kNodeLc[192];
+static __constant__ float kNodeWs[192];
+static __constant__ float kNodeWq[192];
+
+template <int NQ> struct NodeBase { static constexpr int value = NQ == 64 ? 0 : 64; };
+
+// One galaxy on the device.
+struct GalDev {
+  int nx, ny, os, h;
+  int L;                 // os + 2h: taps of the combined PSF (x) box filter per axis
+  int W, H;              // padded fine grid: os*nx + 2h by os*ny + 2h
+  int psf_kind;          // 0 separable Gaussian, 1 two-dimensional (Moffat)
+  float pitch_kpa;       // fine pitch in kpc
+  double xoff_kpa;       // x (kpc) of padded fine column 0 is xoff_kpa + 0 * pitch_kpa
+  double yoff_kpa;
+  const float* taps;     // [L] (Gaussian) or [L][L] (Moffat)
+  const float* data;     // [4][ny][nx]
+  const float* iv;       // [4][ny][nx]: mask / delta^2
+  double norm_const;     // sum over used spaxels of ln(sqrt(2 pi) delta)
+};
+
+// One block-sized unit of work: spaxel rows [j0, j1) of row b against galaxy g.
+struct WorkItem {
+  int b, g, j0, j1;
+};
+
+// Per-model constants, decoded in float64 and stored as float32 in shared memory.
+struct ModelConst {
+  float X0, Y0;            // kpc offset of fine column/row 0 relative to the model centre
+  float cpa, spa;          // cos, sin of the position angle
+  float inv_ci, si;        // 1 / cos i, sin i
+  // bulge (Dehnen): a, gamma
+  float inv_a, ngam, g4, g7, g3, three_mg;
+  float cS, cQ, vb_c;      // Sigma = cS x pS S; Sigma sigma^2 = cQ pQ Q; vb^2 = vb_c u^(3-g) / (r/a)
+  float Lb;                // 1e-6 / (M/L)_b
+  // halo (NFW)
+  float inv_rs, vh_c;      // x = r / rs; vh^2 = vh_c m(x) / r
+  // discs
+  float inv_Rd[2], half_inv_Rd[2], vd_c[2], Sd_c[2], Ld[2], ks[2], omk[2];
+  float vsys;
+  int valid;
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Decode row theta (float32) into per-model constants.  Returns 0 when the row is outside
+// the parameter domain (non-finite, i not in [0, pi/2), gamma not in [0, 3), |k| > 1,
+// c <= 0, M/L <= 0).
+__device__ inline int decode_model(const float* __restrict__ th, int nd, const GalDev& g, ModelConst& m) {
+  const int np = nd == 2 ? 19 : 15;
+  double t[kMaxParams];
+  for (int i = 0; i < np; ++i) {
+    t[i] = (double)th[i];
+    if (!isfinite(t[i])) return 0;
+  }
+  if (!(t[3] >= 0.0 && t[3] < 0.5 * kPi)) return 0;
+  if (!(t[6] >= 0.0 && t[6] < 3.0)) return 0;
+  if (!(fabs(t[9]) <= 1.0)) return 0;
+  if (!(t[10] > 0.0 && t[11] > 0.0)) return 0;
+  if (!(t[13] > 0.0)) return 0;
+  if (nd == 2 && !(fabs(t[17]) <= 1.0 && t[18] > 0.0)) return 0;
+
+  const double ci = cos(t[3]), si = sin(t[3]);
+  m.X0 = (float)(g.xoff_kpa - t[0]);
+  m.Y0 = (float)(g.yoff_kpa - t[1]);
+  m.cpa = (float)cos(t[2]);
+  m.spa = (float)sin(t[2]);
+  m.inv_ci = (float)(1.0 / ci);
+  m.si = (float)si;
+  // bulge
+  const double Mb = pow(10.0, t[4]), a = pow(10.0, t[5]), gam = t[6];
+  m.inv_a = (float)(1.0 / a);
+  m.ngam = (float)(-gam);
+  m.g4 = (float)(gam - 4.0);
+  m.g7 = (float)(2.0 * gam - 7.0);
+  m.g3 = (float)(3.0 - 2.0 * gam);
+  m.three_mg = (float)(3.0 - gam);
+  m.cS = (float)((3.0 - gam) * Mb / (2.0 * kPi * a * a));
+  m.cQ = (float)(kG * (3.0 - gam) * Mb * Mb / (2.0 * kPi * a * a * a));
+  m.vb_c = (float)(kG * Mb / a);
+  m.Lb = (float)(1e-6 / t[10]);
+  // halo
+  const double M200 = pow(10.0, t[12]), c = t[13];
+  const double r200 = cbrt(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit));
+  const double mc = log1p(c) - c / (1.0 + c);
+  m.inv_rs = (float)(c / r200);
+  m.vh_c = (float)(kG * M200 / mc);
+  // discs
+  for (int j = 0; j < 2; ++j) {
+    if (j >= nd) {
+      m.inv_Rd[j] = m.half_inv_Rd[j] = m.vd_c[j] = m.Sd_c[j] = m.Ld[j] = m.ks[j] = m.omk[j] = 0.f;
+      continue;
+    }
+    const int o = j == 0 ? 7 : 15;
+    const double Md = pow(10.0, t[o]), Rd = pow(10.0, t[o + 1]), k = t[o + 2];
+    const double ml = j == 0 ? t[11] : t[18];
+    m.inv_Rd[j] = (float)(1.0 / Rd);
+    m.half_inv_Rd[j] = (float)(0.5 / Rd);
+    m.vd_c[j] = (float)(2.0 * kG * Md / Rd);
+    m.Sd_c[j] = (float)(Md / (2.0 * kPi * Rd * Rd * ci));
+    m.Ld[j] = (float)(1e-6 / ml);
+    m.ks[j] = (float)(-k * si);
+    m.omk[j] = (float)((1.0 - k * k) / 3.0);
+  }
+  m.vsys = (float)t[14];
+  return 1;
+}
+
+// F(y) = y^2 [I0 K0 - I1 K1](y) from the generated float32 fits (see disc_fit.h).
+__device__ __forceinline__ float disc_F(float y) {
+  if (y <= 1.0f) {
+    const float s = y * y;
+    float P = kDiscP[BANG_DISC_DEG_A], Q = kDiscQ[BANG_DISC_DEG_A];
+#pragma unroll
+    for (int k = BANG_DISC_DEG_A - 1; k >= 0; --k) {
+      P = fmaf(P, s, kDiscP[k]);
+      Q = fmaf(Q, s, kDiscQ[k]);
+    }
+    return s * (P - logf(y) * Q);
+  }
+  const float u = __frcp_rn(y);
+  const int e = (int)((__float_as_uint(u) >> 23) & 0xff) - 127;   // u in [2^e, 2^(e+1))
+  int k = -e - 1;
+  k = k < 0 ? 0 : (k > BANG_DISC_NPIECE_B - 1 ? BANG_DISC_NPIECE_B - 1 : k);
+  const float t = (u - kDiscMid[k]) * kDiscInvHalf[k];
+  float gv = kDiscG[k][BANG_DISC_DEG_B];
+#pragma unroll
+  for (int i = BANG_DISC_DEG_B - 1; i >= 0; --i) gv = fmaf(gv, t, kDiscG[k][i]);
+  return gv * (0.25f * u);
+}
+
+// m(x) = ln(1 + x) - x / (1 + x) of the NFW enclosed mass.  For x <= 1, with z = x / (2 + x):
+// m = 2 z^2 / (1 + z) + 2 z^3 (1/3 + z^2/5 + z^4/7 + ...), free of the cancellation at small x.
+__device__ __forceinline__ float nfw_m(float x) {
+  if (x <= 1.0f) {
+    const float z = x / (2.0f + x);
+    const float z2 = z * z;
+    float s = 1.0f / 19.0f;
+    s = fmaf(s, z2, 1.0f / 17.0f);
+    s = fmaf(s, z2, 1.0f / 15.0f);
+    s = fmaf(s, z2, 1.0f / 13.0f);
+    s = fmaf(s, z2, 1.0f / 11.0f);
+    s = fmaf(s, z2, 1.0f / 9.0f);
+    s = fmaf(s, z2, 1.0f / 7.0f);
+    s = fmaf(s, z2, 1.0f / 5.0f);
+    s = fmaf(s, z2, 1.0f / 3.0f);
+    return 2.0f * z2 / (1.0f + z) + 2.0f * z2 * z * s;
+  }
+  return log1pf(x) - x / (1.0f + x);
+}
+
+// Projected density and Sigma sigma^2 of the bulge at sky radius R (kpc).
+// With x = R / a, w = x / (x + 1) and node k at r = R cosh t_k:
+//   rho(r) r^-1-part:  (x c)^-g (x c + 1)^(g-4) = x^-g (x+1)^(g-4) * c^-g q^(g-4),  q = 1 + w (c - 1)
+//   rho M part:        (x c)^(3-2g) (x c + 1)^(2g-7) = x^(3-2g) (x+1)^(2g-7) * c^(3-2g) q^(2g-7)
+// so each node costs one lg2 and two ex2 of small arguments; the large per-point powers are
+// taken once, accurately, outside the sum.
+template <int NQ>
+__device__ __forceinline__ void bulge_projected(const ModelConst& m, float R, float& Sigma, float& SigS2) {
+  constexpr int base = NodeBase<NQ>::value;
+  const float x = R * m.inv_a;
+  const float xp1 = x + 1.0f;
+  const float w = x / xp1;
+  const float lw = log2f(w);
+  const float i2 = 1.0f / (xp1 * xp1);
+  const float ip4 = i2 * i2;
+  const float pS = exp2f(m.ngam * lw) * ip4;
+  const float pQ = exp2f(m.g3 * lw) * ip4;
+  float S = 0.f, Q = 0.f;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const float q = fmaf(w, kNodeCm1[base + k], 1.0f);
+    const float d = lg2_approx(q);
+    const float e1 = fmaf(m.g4, d, m.ngam * kNodeLc[base + k]);
+    const float e2 = fmaf(m.g7, d, m.g3 * kNodeLc[base + k]);
+    S = fmaf(kNodeWs[base + k], ex2_approx(e1), S);
+    Q = fmaf(kNodeWq[base + k], ex2_approx(e2), Q);
+  }
+  Sigma = m.cS * x * pS * S;
+  SigS2 = m.cQ * pQ * Q;
+}
+
+// The four observables at one padded fine grid point: (B, v_los, sigma_los, <L/M>).
+template <int NQ, int ND>
+__device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float Y) {
+  // Sec. 2.1: rotate the major axis onto x; deproject the razor-thin discs by 1 / cos i
+  const float xr = fmaf(X, m.cpa, Y * m.spa);
+  const float yr = fmaf(Y, m.cpa, -X * m.spa);
+  const float R2 = fmaf(X, X, Y * Y);
+  const float yd = yr * m.inv_ci;
+  const float r2 = fmaf(xr, xr, yd * yd);
+  const float R = sqrtf(fmaxf(R2, kR2Floor));
+  const float r = sqrtf(fmaxf(r2, kR2Floor));
+  const float inv_r = 1.0f / r;
+  const float cphi = xr * inv_r;
+
+  float Sb, SbS2;
+  bulge_projected<NQ>(m, R, Sb, SbS2);
+
+  // circular velocities in the disc plane (Eq. 10)
+  const float xa = r * m.inv_a;
+  const float ub = xa / (xa + 1.0f);
+  float vint2 = m.vb_c * exp2f(m.three_mg * log2f(ub)) / xa;
+  vint2 += m.vh_c * nfw_m(r * m.inv_rs) * inv_r;
+  float Sd[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    vint2 += m.vd_c[j] * disc_F(r * m.half_inv_Rd[j]);
+    Sd[j] = m.Sd_c[j] * expf(-r * m.inv_Rd[j]);
+  }
+  const float vint = sqrtf(vint2);
+
+  // light weighting (Eqs. 13-15, 19)
+  const float Bb = Sb * m.Lb;
+  float B = Bb, Bv = 0.f, Bs2 = SbS2 * m.Lb, Stot = Sb;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const float Bd = Sd[j] * m.Ld[j];
+    B += Bd;
+    Bv = fmaf(Bd, m.ks[j] * cphi * vint, Bv);
+    Bs2 = fmaf(Bd, m.omk[j] * vint2, Bs2);
+    Stot += Sd[j];
+  }
+  const float iB = 1.0f / B;
+  return make_float4(B, Bv * iB, sqrtf(Bs2 * iB), B * 1e6f / Stot);
+}
+
+}  // namespace bang

@@ -1,0 +1,284 @@
+// Fused forward kernel: model evaluation -> PSF -> binning -> chi-square, one launch.
+//
+// Each block takes work items (row b, galaxy g, spaxel rows [j0, j1)) and streams the fine
+// rows those spaxel rows depend on from top to bottom, G rows at a time:
+//   1. every thread evaluates points of the G x W chunk (the per-point model, Sec. 2.1-2.4)
+//      into a shared-memory stage of float4 (B, v, sigma, <L/M>);
+//   2. the combined PSF (x) box filter (Eq. 21 followed by the os x os average) is applied:
+//      separable Gaussian - one thread per spaxel column forms the horizontal sum of each
+//      fine row and scatters it with the vertical weights into the accumulators of the
+//      spaxel rows still open; Moffat - one thread per (open spaxel row, column) applies
+//      the two-dimensional weights row by row;
+//   3. a spaxel row whose last fine row has arrived is finished at once: residuals against
+//      the data, chi-square in float32 per spaxel, float64 per thread, then a warp-shuffle
+//      tree and a cross-warp float64 sum per work item.
+// The fine field never leaves shared memory.  Only ceil((os + 2h) / os) spaxel rows of
+// accumulators are live at any time.
+#include <cuda_runtime.h>
+
+#include "bang_device.cuh"
+#include "bang_internal.h"
+
+namespace bang {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Residual terms of spaxel (i, j) of galaxy g from the filtered value F = (B, v, sigma, <L/M>).
+// Writes the model maps / adjoint seeds when requested.  Returns chi^2 of the four maps.
+template <int MODE>
+__device__ __forceinline__ float finish_spaxel(const GalDev& g, const ModelConst& m, float4 F, int i, int j,
+                                               float* __restrict__ out) {
+  const int n = g.nx * g.ny;
+  const int s = j * g.nx + i;
+  const float model[4] = {F.x, F.y + m.vsys, F.z, 1.0f / F.w};
+  float chi = 0.f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float iv = __ldg(g.iv + c * n + s);
+    const float r = model[c] - __ldg(g.data + c * n + s);
+    chi = fmaf(r * iv, r, chi);
+    if (MODE == kModeMaps) out[c * n + s] = model[c];
+    if (MODE == kModeSeed) {
+      // d logL / dF for each filtered channel; M/L = 1 / F_l
+      const float lam = -r * iv;
+      out[c * n + s] = c == 3 ? -lam * model[3] * model[3] : lam;
+    }
+  }
+  return chi;
+}
+
+template <int NQ, int ND, int PSF, int MODE>
+__global__ void __launch_bounds__(kThreads) forward_kernel(FwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ModelConst mc;
+  __shared__ GalDev gs;
+  __shared__ double red[kThreads / 32];
+
+  const int tid = threadIdx.x;
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int item_id = a.order ? a.order[it] : it;
+    const WorkItem w = a.items[item_id];
+    if (tid == 0) {
+      gs = a.gals[w.g];
+      mc.valid = decode_model(a.theta + (size_t)w.b * a.P, ND, gs, mc);
+    }
+    __syncthreads();
+    const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx;
+    const int NA = (L + os - 1) / os;                       // open spaxel rows
+    float* taps = reinterpret_cast<float*>(smem_raw);
+    const int ntaps = PSF == 0 ? L : L * L;
+    float4* acc = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 4 + 15) / 16) * 16);
+    float4* stage = acc + (size_t)NA * nx;
+    float* out = nullptr;
+    if (MODE == kModeMaps) out = a.maps + a.out_off[w.b];
+    if (MODE == kModeSeed) out = a.seed + a.out_off[w.b];
+
+    if (!mc.valid) {
+      if (MODE == kModeMaps) {
+        for (int s = tid; s < 4 * (w.j1 - w.j0) * nx; s += kThreads) {
+          const int c = s / ((w.j1 - w.j0) * nx), rem = s - c * (w.j1 - w.j0) * nx;
+          out[c * nx * gs.ny + w.j0 * nx + rem] = __int_as_float(0x7fc00000);
+        }
+      }
+      if (MODE == kModeSeed) {
+        for (int s = tid; s < 4 * (w.j1 - w.j0) * nx; s += kThreads) {
+          const int c = s / ((w.j1 - w.j0) * nx), rem = s - c * (w.j1 - w.j0) * nx;
+          out[c * nx * gs.ny + w.j0 * nx + rem] = 0.f;
+        }
+      }
+      if (tid == 0) a.partial[item_id] = __longlong_as_double(0x7ff8000000000000ll);
+      __syncthreads();
+      continue;
+    }
+
+    for (int t = tid; t < ntaps; t += kThreads) taps[t] = __ldg(gs.taps + t);
+    for (int t = tid; t < NA * nx; t += kThreads) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+
+    double chi_thread = 0.0;
+    const int y_begin = w.j0 * os;
+    const int y_end = (w.j1 - 1) * os + L;                   // exclusive
+    const float pk = gs.pitch_kpa;
+    for (int y0 = y_begin; y0 < y_end; y0 += a.G) {
+      const int G = min(a.G, y_end - y0);
+      // 1. evaluate the chunk of G fine rows
+      const int npts = G * W;
+      for (int p = tid; p < npts; p += kThreads) {
+        const int gr = p / W;
+        const int qx = p - gr * W;
+        const float X = fmaf((float)qx, pk, mc.X0);
+        const float Y = fmaf((float)(y0 + gr), pk, mc.Y0);
+        stage[p] = eval_point<NQ, ND>(mc, X, Y);
+      }
+      __syncthreads();
+      // 2 + 3. filter into open spaxel rows; finish the rows that complete
+      if (PSF == 0) {
+        for (int i = tid; i < nx; i += kThreads) {
+          for (int gr = 0; gr < G; ++gr) {
+            const int y = y0 + gr;
+            const float4* srow = stage + gr * W + i * os;
+            float4 hs = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < L; ++c) {
+              const float tw = taps[c];
+              const float4 v = srow[c];
+              hs.x = fmaf(tw, v.x, hs.x); hs.y = fmaf(tw, v.y, hs.y);
+              hs.z = fmaf(tw, v.z, hs.z); hs.w = fmaf(tw, v.w, hs.w);
+            }
+            int jlo = y - L + 1 <= 0 ? 0 : (y - L + os) / os;  // ceil((y - L + 1) / os)
+            jlo = max(jlo, w.j0);
+            const int jhi = min(y / os, w.j1 - 1);
+            for (int j = jlo; j <= jhi; ++j) {
+              const float tv = taps[y - j * os];
+              float4& A = acc[(j % NA) * nx + i];
+              A.x = fmaf(tv, hs.x, A.x); A.y = fmaf(tv, hs.y, A.y);
+              A.z = fmaf(tv, hs.z, A.z); A.w = fmaf(tv, hs.w, A.w);
+            }
+            const int yl = y - L + 1;                             // spaxel row ending here
+            if (yl >= 0 && yl % os == 0) {
+              const int j = yl / os;
+              if (j >= w.j0 && j < w.j1) {
+                float4& A = acc[(j % NA) * nx + i];
+                chi_thread += (double)finish_spaxel<MODE>(gs, mc, A, i, j, out);
+                A = make_float4(0.f, 0.f, 0.f, 0.f);
+              }
+            }
+          }
+        }
+      } else {
+        // open spaxel rows touched by this chunk
+        const int ylast = y0 + G - 1;
+        int jlo = y0 - L + 1 <= 0 ? 0 : (y0 - L + os) / os;
+        jlo = max(jlo, w.j0);
+        const int jhi = min(ylast / os, w.j1 - 1);
+        const int nj = jhi - jlo + 1;
+        for (int t = tid; t < nj * nx; t += kThreads) {
+          const int j = jlo + t / nx;
+          const int i = t - (t / nx) * nx;
+          float4 A = acc[(j % NA) * nx + i];
+          const int ga = max(0, j * os - y0);
+          const int gb = min(G - 1, j * os + L - 1 - y0);
+          for (int gr = ga; gr <= gb; ++gr) {
+            const float* wrow = taps + (y0 + gr - j * os) * L;
+            const float4* srow = stage + gr * W + i * os;
+            for (int c = 0; c < L; ++c) {
+              const float tw = wrow[c];
+              const float4 v = srow[c];
+              A.x = fmaf(tw, v.x, A.x); A.y = fmaf(tw, v.y, A.y);
+              A.z = fmaf(tw, v.z, A.z); A.w = fmaf(tw, v.w, A.w);
+            }
+          }
+          if (j * os + L - 1 <= ylast) {
+            chi_thread += (double)finish_spaxel<MODE>(gs, mc, A, i, j, out);
+            A = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          acc[(j % NA) * nx + i] = A;
+        }
+      }
+      __syncthreads();
+    }
+
+    // float64 reduction of the work item's chi^2: warp shuffles, then across warps
+    double v = warp_sum(chi_thread);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int k = 0; k < kThreads / 32; ++k) s += red[k];
+      a.partial[item_id] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// logL[b] = -chi^2/2 - const from the per-item partial sums (items of row b are contiguous).
+__global__ void finalize_kernel(const double* __restrict__ partial, const int* __restrict__ row_first,
+                                const int* __restrict__ row_g, const GalDev* __restrict__ gals, int B,
+                                double* __restrict__ logL) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double s = 0.0;
+  bool bad = false;
+  for (int k = row_first[b]; k < row_first[b + 1]; ++k) {
+    const double v = partial[k];
+    bad |= isnan(v);
+    s += v;
+  }
+  logL[b] = bad ? -INFINITY : -0.5 * s - gals[row_g[b]].norm_const;
+}
+
+template <int NQ, int ND, int PSF, int MODE>
+cudaError_t launch_t(const FwdArgs& a, int grid, size_t smem, cudaStream_t st) {
+  forward_kernel<NQ, ND, PSF, MODE><<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NQ, int ND, int PSF>
+cudaError_t launch_mode(const FwdArgs& a, int mode, int grid, size_t smem, cudaStream_t st) {
+  switch (mode) {
+    case kModeLogL: return launch_t<NQ, ND, PSF, kModeLogL>(a, grid, smem, st);
+    case kModeMaps: return launch_t<NQ, ND, PSF, kModeMaps>(a, grid, smem, st);
+    default: return launch_t<NQ, ND, PSF, kModeSeed>(a, grid, smem, st);
+  }
+}
+
+template <int NQ, int ND>
+cudaError_t launch_psf(const FwdArgs& a, int psf2d, int mode, int grid, size_t smem, cudaStream_t st) {
+  return psf2d ? launch_mode<NQ, ND, 1>(a, mode, grid, smem, st) : launch_mode<NQ, ND, 0>(a, mode, grid, smem, st);
+}
+
+}  // namespace
+
+int forward_threads() { return kThreads; }
+
+size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d) {
+  const int ntaps = psf2d ? L * L : L;
+  const int NA = (L + os - 1) / os;
+  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)NA * nx * 16 + (size_t)G * W * 16;
+}
+
+const void* forward_kernel_ptr(int n_quad, int n_discs, int psf2d, int mode) {
+#define BANG_PICK(NQ, ND, PSF)                                                    \
+  if (n_quad == NQ && n_discs == ND && psf2d == PSF) {                            \
+    if (mode == kModeLogL) return (const void*)forward_kernel<NQ, ND, PSF, kModeLogL>; \
+    if (mode == kModeMaps) return (const void*)forward_kernel<NQ, ND, PSF, kModeMaps>; \
+    return (const void*)forward_kernel<NQ, ND, PSF, kModeSeed>;                   \
+  }
+  BANG_PICK(64, 1, 0) BANG_PICK(64, 1, 1) BANG_PICK(64, 2, 0) BANG_PICK(64, 2, 1)
+  BANG_PICK(128, 1, 0) BANG_PICK(128, 1, 1) BANG_PICK(128, 2, 0) BANG_PICK(128, 2, 1)
+#undef BANG_PICK
+  return nullptr;
+}
+
+cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d, int mode, int grid, size_t smem,
+                           cudaStream_t st) {
+  if (n_quad == 64) {
+    return n_discs == 2 ? launch_psf<64, 2>(a, psf2d, mode, grid, smem, st)
+                        : launch_psf<64, 1>(a, psf2d, mode, grid, smem, st);
+  }
+  return n_discs == 2 ? launch_psf<128, 2>(a, psf2d, mode, grid, smem, st)
+                      : launch_psf<128, 1>(a, psf2d, mode, grid, smem, st);
+}
+
+cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
+                            double* logL, cudaStream_t st) {
+  finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(partial, row_first, row_g, gals, B, logL);
+  return cudaGetLastError();
+}
+
+cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float* ws, const float* wq) {
+  cudaError_t e = cudaMemcpyToSymbol(kNodeCm1, cm1, 192 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeLc, lc, 192 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeWs, ws, 192 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeWq, wq, 192 * sizeof(float));
+  return e;
+}
+
+}  // namespace bang

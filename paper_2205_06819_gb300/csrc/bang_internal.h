@@ -1,0 +1,52 @@
+// Internal interfaces between the host library (bang_api.cu) and the kernel translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bang {
+
+struct GalDev;
+struct WorkItem;
+
+enum { kModeLogL = 0, kModeMaps = 1, kModeSeed = 2 };
+
+// Arguments of the fused forward kernel.
+struct FwdArgs {
+  const float* theta;       // [B][P]
+  int P;
+  const GalDev* gals;
+  const WorkItem* items;    // [n_items], items of one row contiguous, rows in order
+  const int* order;         // execution order of items (NULL = table order)
+  int n_items;
+  int G;                    // fine rows per block step
+  double* partial;          // [n_items] chi^2 of each item (NaN for an out-of-domain row)
+  float* maps;              // kModeMaps: model maps, row b at out_off[b]
+  float* seed;              // kModeSeed: d logL / dF per spaxel, row b at out_off[b]
+  const int64_t* out_off;   // [B] float offsets of each row's [4][ny][nx] block
+};
+
+// Arguments of the adjoint sweep.
+struct AdjArgs {
+  const float* theta;
+  int P;
+  const GalDev* gals;
+  const WorkItem* items;    // fine-row bands (j0/j1 hold fine padded rows [y0, y1))
+  const int* order;
+  int n_items;
+  const float* seed;        // d logL / dF at the spaxels, row b at out_off[b]
+  const int64_t* out_off;
+  double* grad_acc;         // [B][P] float64 accumulators (zeroed before the launch)
+};
+
+int forward_threads();
+size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d);
+const void* forward_kernel_ptr(int n_quad, int n_discs, int psf2d, int mode);
+cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d, int mode, int grid, size_t smem,
+                           cudaStream_t st);
+cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
+                            double* logL, cudaStream_t st);
+cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float* ws, const float* wq);
+
+}  // namespace bang

@@ -1,0 +1,42 @@
+"""Test datasets: seeded draws from paper_2205_06819_gb300.synth, noise-free maps from the
+oracle, noisy float32 data.  The CUDA path and the oracle read the same float32 bytes."""
+import numpy as np
+
+import oracle
+from paper_2205_06819_gb300 import synth
+
+
+class Dataset:
+    def __init__(self, spec: synth.GalaxySpec, theta_true, n_discs=1, n_quad=64, seed=1, noise=True, mask=None):
+        self.spec, self.n_discs, self.n_quad = spec, n_discs, n_quad
+        self.theta_true = np.asarray(theta_true, dtype=np.float64)
+        g0 = self.oracle_galaxy(None, None, None)
+        true = oracle.maps(g0, self.theta_true, n_discs=n_discs, n_quad=n_quad)
+        self.data, self.err, m = synth.noisy_data(true, seed=seed, noise=noise)
+        self.mask = m if mask is None else np.asarray(mask, dtype=np.uint8)
+        self.og = self.oracle_galaxy(self.data.astype(np.float64), self.err.astype(np.float64), self.mask)
+
+    def oracle_galaxy(self, data, err, mask):
+        s = self.spec
+        return oracle.Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec,
+                             spaxel_arcsec=s.spaxel_arcsec, psf_kind=s.psf_kind, moffat_beta=s.moffat_beta,
+                             data=data, err=err, mask=mask)
+
+    def model_galaxy(self):
+        from paper_2205_06819_gb300.model import Galaxy
+        s = self.spec
+        return Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, self.data, self.err, self.mask,
+                      spaxel_arcsec=s.spaxel_arcsec, psf_kind=s.psf_kind, moffat_beta=s.moffat_beta)
+
+    def oracle_loglike(self, theta32, nthreads=0):
+        th = np.asarray(theta32, dtype=np.float32).astype(np.float64)
+        return oracle.loglike(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad, nthreads=nthreads)
+
+    def oracle_maps(self, theta32):
+        th = np.asarray(theta32, dtype=np.float32).astype(np.float64)
+        return oracle.maps(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad)
+
+
+def theta_batch(n_discs, theta_true, B, seed, gamma_fixed=None):
+    box = synth.prior_box(n_discs, gamma_fixed)
+    return synth.draw_theta_batch(box, np.asarray(theta_true), B, seed).astype(np.float32)
