@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the batched galaxy-model log-likelihood on GB300.
+
+Default workload: 1024 parameter vectors against one 80x80-spaxel galaxy with 5x5
+oversampling and a Gaussian PSF of FWHM 2.5" (Dehnen bulge with gamma in [0, 2], one
+exponential disc, NFW halo, 64 radial quadrature nodes), float32 compute with float64
+chi-square accumulation.  One step = logL of the whole batch (one persistent launch).
+
+Prints one JSON line: device-timed evals/s (`value`), end-to-end evals/s through the C
+ABI with host buffers (`e2e`), the roofline of the dominant kernel, SM clocks sampled
+during the timed region, and the FP64 CPU oracle timed on a bounded sample
+(`cpu_baseline`).  ``--impl reference`` times the oracle alone in the same format.
+
+Multi-GPU: launched by torchrun, every rank evaluates its own batch (weak scaling, no
+collective on the data path); the timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2205_06819_gb300 import synth  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT_NOMINAL = 152
+SM_MAX_MHZ_NOMINAL = 2070.0
+# Per-SM issue rates measured on this GB300 (sm_103a) by a clock64 microbenchmark of
+# dependent-free chains of the PTX instructions ("Roofline").
+MUFU_EX2_PER_CLK_SM = 32.0
+MUFU_LG2_PER_CLK_SM = 16.0
+FP32_PER_CLK_SM = 128.0
+# DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
+# it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
+NCU_TRAFFIC = {"stamp": None, "bytes_per_launch": None}
+
+
+def kernel_stamp() -> str:
+    h = hashlib.sha256()
+    for f in ("bang_forward.cu", "bang_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2205_06819_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="batched", choices=synth.WORKLOADS)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain-form and adjoint side measurements")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, n in enumerate(names):
+                if "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def points_per_eval(spec: synth.GalaxySpec) -> int:
+    sig = spec.psf_fwhm_arcsec / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    h = int(math.floor(3.0 * sig / (spec.spaxel_arcsec / spec.oversample))) if spec.psf_fwhm_arcsec > 0 else 0
+    return (spec.oversample * spec.nx + 2 * h) * (spec.oversample * spec.ny + 2 * h)
+
+
+def algorithmic_sfu_ops(wl: synth.Workload) -> float:
+    """Transcendental (SFU) operations of one evaluation: per padded fine point, one log2 and
+    two exp2 per radial quadrature node, plus 16 for the rest of the point (two square
+    roots of the radii, two of the velocities' roots, the bulge, halo and disc powers,
+    logarithms and exponentials, and the reciprocals of the light weighting)."""
+    return float(points_per_eval(wl.galaxies[0])) * (3 * wl.n_quad + 16)
+
+
+def sfu_peak_ops_per_s(n_quad: int, mhz: float, sms: int) -> float:
+    """Peak transcendental rate for the radial-rule mix (one lg2 per two ex2)."""
+    per_op_clk = (1.0 / MUFU_LG2_PER_CLK_SM + 2.0 / MUFU_EX2_PER_CLK_SM) / 3.0   # SM-clocks per op
+    return sms * mhz * 1e6 / per_op_clk
+
+
+# ----------------------------------------------------------------------------- data
+def make_model(wl: synth.Workload, rank: int, torch):
+    """Seeded synthetic galaxy: noise-free maps from the library at theta_true plus noise."""
+    from paper_2205_06819_gb300.model import Galaxy, Model
+    wid = synth.workload_id(wl.name)
+    box = synth.prior_box(wl.n_discs, wl.gamma_fixed)
+    s = wl.galaxies[0]
+    tt = synth.draw_theta_true(box, synth.dataset_seed(wid))
+    ones = np.ones((4, s.ny, s.nx), np.float32)
+    probe = Model(Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, ones, ones,
+                         psf_kind=s.psf_kind, moffat_beta=s.moffat_beta), n_discs=wl.n_discs, n_quad=wl.n_quad)
+    true = probe.maps(torch.from_numpy(tt.astype(np.float32)[None]).cuda())[0].cpu().numpy().astype(np.float64)
+    probe.close()
+    data, err, mask = synth.noisy_data(true, seed=synth.dataset_seed(wid))
+    gal = Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, data, err, mask,
+                 psf_kind=s.psf_kind, moffat_beta=s.moffat_beta)
+    model = Model(gal, n_discs=wl.n_discs, n_quad=wl.n_quad)
+    theta = synth.draw_theta_batch(box, tt, wl.batch, synth.batch_seed(wid) + 1000 * rank).astype(np.float32)
+    return model, gal, theta
+
+
+def cpu_oracle_sample(wl, gal, theta, seconds: float):
+    """The FP64 oracle, as it stands, on consecutive rows until the time budget is spent."""
+    import oracle
+    oracle.build()
+    og = oracle.Galaxy(gal.nx, gal.ny, gal.oversample, gal.psf_fwhm_arcsec, gal.kpc_per_arcsec,
+                       psf_kind=gal.psf_kind, moffat_beta=gal.moffat_beta,
+                       data=np.asarray(gal.data, np.float64), err=np.asarray(gal.err, np.float64), mask=gal.mask)
+    t0 = time.perf_counter()
+    n = 0
+    while n < theta.shape[0]:
+        oracle.loglike(og, theta[n:n + 1].astype(np.float64), n_discs=wl.n_discs, n_quad=wl.n_quad)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "logL evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"first {n} of the {theta.shape[0]} rows, one oracle call per row (OpenMP over fine-grid rows), "
+                      f"{dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- arms
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    wl = synth.workload(args.workload)
+    wid = synth.workload_id(wl.name)
+    box = synth.prior_box(wl.n_discs, wl.gamma_fixed)
+    s = wl.galaxies[0]
+    tt = synth.draw_theta_true(box, synth.dataset_seed(wid))
+    g0 = oracle.Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, psf_kind=s.psf_kind,
+                       moffat_beta=s.moffat_beta)
+    data, err, mask = synth.noisy_data(oracle.maps(g0, tt, n_discs=wl.n_discs, n_quad=wl.n_quad),
+                                       seed=synth.dataset_seed(wid))
+    og = oracle.Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, psf_kind=s.psf_kind,
+                       moffat_beta=s.moffat_beta, data=data.astype(np.float64), err=err.astype(np.float64), mask=mask)
+    theta = synth.draw_theta_batch(box, tt, wl.batch, synth.batch_seed(wid)).astype(np.float32).astype(np.float64)
+    rows_per_step = 1
+    k = 0
+    for _ in range(args.warmup):
+        oracle.loglike(og, theta[k % wl.batch:k % wl.batch + rows_per_step], n_discs=wl.n_discs, n_quad=wl.n_quad)
+        k += rows_per_step
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.loglike(og, theta[k % wl.batch:k % wl.batch + rows_per_step], n_discs=wl.n_discs, n_quad=wl.n_quad)
+        k += rows_per_step
+    dt = time.perf_counter() - t0
+    value = args.steps * rows_per_step / dt
+    line = {
+        "impl": "reference", "metric": "logL evals/s", "value": value, "unit": "logL evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{wl.name}: {wl.description}", "rows_per_step": rows_per_step},
+        "cpu_baseline": {"value": value, "unit": "logL evals/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"{rows_per_step} row per step of the {wl.batch}-row batch"},
+        "e2e": {"value": value, "unit": "logL evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    from paper_2205_06819_gb300 import build as bmod
+    bmod.build()
+    wl = synth.workload(args.workload)
+    if len(wl.galaxies) != 1:
+        raise SystemExit("bench.py times single-galaxy workloads; the uneven batch is a parity case")
+    model, gal, theta_np = make_model(wl, rank, torch)
+    B, P = theta_np.shape
+    theta = torch.from_numpy(theta_np).cuda()
+    logL = torch.empty(B, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        model.loglike(theta, out=logL)
+    torch.cuda.synchronize()
+
+    # device-timed steps (L2 flushed between steps, outside the events)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        starts[k].record(stream)
+        model.loglike(theta, out=logL)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - w0
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = ws * B * args.steps / dev_s
+    assert np.isfinite(logL.cpu().numpy()).any()
+
+    # end to end through the C ABI with pinned host buffers
+    th_host = torch.from_numpy(theta_np).pin_memory()
+    out_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        model.loglike(th_host, out=out_host)
+    e2e_t = []
+    barrier()
+    for k in range(max(3, args.steps // 4)):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        model.loglike(th_host, out=out_host)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t)
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * B * len(e2e_t) / e2e_s
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL))
+    step_s = dev_s / args.steps
+    ops = algorithmic_sfu_ops(wl) * B
+    achieved = ops / step_s / 1e9
+    peak = sfu_peak_ops_per_s(wl.n_quad, mhz, sms) / 1e9
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["stamp"] == kernel_stamp() else None
+
+    line = {
+        "metric": "logL evals/s", "value": value, "unit": "logL evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{wl.name}: {wl.description}", "rows": B, "padded_fine_points": points_per_eval(
+            wl.galaxies[0]), "n_quad": wl.n_quad, "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "e2e": {"value": e2e_value, "unit": "logL evals/s", "h2d_bytes_per_step": int(B * P * 4),
+                "d2h_bytes_per_step": int(B * 8)},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SFU op/s", "frac": achieved / peak,
+                     "traffic": traffic,
+                     "peak_basis": f"{sms} SMs x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz) x measured per-SM rates "
+                                   f"lg2 {MUFU_LG2_PER_CLK_SM:.0f}/clk, ex2 {MUFU_EX2_PER_CLK_SM:.0f}/clk for the "
+                                   "radial-rule mix (1 lg2 : 2 ex2)"},
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if ws == 1 and not args.no_extras:
+        line["cpu_baseline"] = cpu_oracle_sample(wl, gal, theta_np, args.cpu_seconds)
+    elif ws == 1:
+        line["cpu_baseline"] = None
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
