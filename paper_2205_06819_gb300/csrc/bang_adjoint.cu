@@ -1,0 +1,442 @@
+// Hand-written adjoint of the log-likelihood: d logL / d theta.
+//
+// Input: the per-spaxel seeds lambda_c(s) = d logL / d F_c(s) written by the forward kernel
+// (kModeSeed), F_c the PSF-convolved, binned channel c (B, v, sigma, <L/M>).  Because
+// F_c(s) = sum_p K(s, p) f_c(p) is linear in the fine-grid field f, the seed of fine point p
+// is a_c(p) = sum_s K(s, p) lambda_c(s): the transposed PSF (x) box stencil.  For the
+// separable Gaussian this is a vertical pass (spaxel rows -> fine row) followed by a
+// horizontal one; for the Moffat PSF the two-dimensional weights are applied directly.
+// Each fine point then runs the vector-Jacobian product of the point model
+// (Sec. 2.1-2.4): the forward values are recomputed, the radial quadrature included, and
+// the seeds are pushed back through the light weighting, the Satoh decomposition, the
+// circular velocities and the geometry onto the per-model constants.  The quadrature
+// carries, besides its two sums, the sums weighted by u = r / (r + a) and by ln u, from
+// which d/dR, d/da and d/dgamma of both projected integrals follow in closed form:
+//   Sigma = 2 R sum w c rho(R c),   rho ~ r^-g (r + a)^(g-4):
+//     R dSigma/dR = (1 - g) Sigma + (g - 4) Su,   a dSigma/da = (g - 3) Sigma + (4 - g) Su,
+//     dSigma/dg = -Sigma / (3 - g) - Sl,
+//   Sigma sigma^2 = 2 G sum w tanh^2 rho M,   rho M ~ r^(3-2g) (r + a)^(2g-7):
+//     R dQ/dR = (3 - 2g) Q + (2g - 7) Qu,   a dQ/da = (2g - 6) Q + (7 - 2g) Qu,
+//     dQ/dg = -Q / (3 - g) - 2 Ql,
+// with Su, Qu the u-weighted and Sl, Ql the (ln u)-weighted sums.  Nothing is stored
+// between the forward and the backward evaluation: the quadrature is recomputed.
+// Work items are bands of fine rows (no halo is needed: the seeds live in global memory).
+// Per-thread float32 partials are reduced per block in float64 and added atomically to
+// float64 accumulators; the per-model constants are mapped to theta in float64.
+#include <cuda_runtime.h>
+
+#include "bang_device.cuh"
+#include "bang_internal.h"
+
+namespace bang {
+namespace {
+
+constexpr int kAdjThreads = 256;
+constexpr float kLn2 = 0.69314718055994531f;
+
+// adjoint accumulators (per thread), adjoints of the per-model constants
+enum {
+  A_X0 = 0,   // d/dX0 (X0 = xoff - x0)
+  A_Y0,
+  A_PA,       // d/dPA through the rotation
+  A_INVCI,    // d/d(1/cos i)
+  A_LB,       // d/dLb,  Lb = 1e-6 / (M/L)_b
+  A_A,        // d/da   (bulge scale)
+  A_G,        // d/dgamma
+  A_MB,       // Mb d/dMb
+  A_VHC,      // d/dvh_c
+  A_IRS,      // d/d(1/rs)
+  A_D0        // per disc: SDC, VDC, IRD, HIRD, LD, KS, OMK
+};
+constexpr int kPerDisc = 7;
+enum { D_SDC = 0, D_VDC, D_IRD, D_HIRD, D_LD, D_KS, D_OMK };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct BulgeDer {
+  float Sb, Qb, dSb_dR, dQb_dR, dSb_da, dQb_da, dSb_dg, dQb_dg;
+};
+
+template <int NQ>
+__device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, float R) {
+  constexpr int base = NodeBase<NQ>::value;
+  const float x = R * m.inv_a;
+  const float xp1 = x + 1.0f;
+  const float w = x / xp1;
+  const float lw = log2f(w);
+  const float i2 = 1.0f / (xp1 * xp1);
+  const float ip4 = i2 * i2;
+  const float pS = exp2f(m.ngam * lw) * ip4;
+  const float pQ = exp2f(m.g3 * lw) * ip4;
+  float S = 0.f, Su = 0.f, Sl = 0.f, Q = 0.f, Qu = 0.f, Ql = 0.f;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const float lc = kNodeLc[base + k];
+    const float q = fmaf(w, kNodeCm1[base + k], 1.0f);
+    const float d = lg2_approx(q);
+    const float t1 = kNodeWs[base + k] * ex2_approx(fmaf(m.g4, d, m.ngam * lc));
+    const float t2 = kNodeWq[base + k] * ex2_approx(fmaf(m.g7, d, m.g3 * lc));
+    const float lu = (lw + lc) - d;                  // log2 u_k, u_k = r_k / (r_k + a)
+    const float u = ex2_approx(lu);
+    S += t1;
+    Su = fmaf(t1, u, Su);
+    Sl = fmaf(t1, lu, Sl);
+    Q += t2;
+    Qu = fmaf(t2, u, Qu);
+    Ql = fmaf(t2, lu, Ql);
+  }
+  const float fS = m.cS * x * pS, fQ = m.cQ * pQ;
+  const float g = -m.ngam;
+  const float inv3g = 1.0f / m.three_mg;
+  BulgeDer o;
+  o.Sb = fS * S;
+  o.Qb = fQ * Q;
+  const float SU = fS * Su, SL = fS * Sl * kLn2, QU = fQ * Qu, QL = fQ * Ql * kLn2;
+  const float iR = 1.0f / R;
+  o.dSb_dR = ((1.0f - g) * o.Sb + (g - 4.0f) * SU) * iR;
+  o.dSb_da = ((g - 3.0f) * o.Sb + (4.0f - g) * SU) * m.inv_a;
+  o.dSb_dg = -o.Sb * inv3g - SL;
+  o.dQb_dR = ((3.0f - 2.0f * g) * o.Qb + (2.0f * g - 7.0f) * QU) * iR;
+  o.dQb_da = ((2.0f * g - 6.0f) * o.Qb + (7.0f - 2.0f * g) * QU) * m.inv_a;
+  o.dQb_dg = -o.Qb * inv3g - 2.0f * QL;
+  return o;
+}
+
+// Vector-Jacobian product of one fine point: adds sum_c a_c d f_c / d(constants) to acc.
+template <int NQ, int ND>
+__device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y, float4 a, float* acc) {
+  // ---- forward (Sec. 2.1-2.4), keeping what the reverse sweep needs
+  const float xr = fmaf(X, m.cpa, Y * m.spa);
+  const float yr = fmaf(Y, m.cpa, -X * m.spa);
+  const float R2 = fmaf(X, X, Y * Y);
+  const float yd = yr * m.inv_ci;
+  const float r2 = fmaf(xr, xr, yd * yd);
+  const bool Rfree = R2 > kR2Floor, rfree = r2 > kR2Floor;
+  const float R = sqrtf(fmaxf(R2, kR2Floor));
+  const float r = sqrtf(fmaxf(r2, kR2Floor));
+  const float inv_r = 1.0f / r;
+  const float cphi = xr * inv_r;
+
+  const BulgeDer bd = bulge_projected_vjp<NQ>(m, R);
+
+  const float xa = r * m.inv_a;
+  const float ub = xa / (xa + 1.0f);
+  const float lub = log2f(ub);
+  const float vb2 = m.vb_c * exp2f(m.three_mg * lub) / xa;
+  const float xh = r * m.inv_rs;
+  const float mh = nfw_m(xh);
+  const float vh2 = m.vh_c * mh * inv_r;
+  float vint2 = vb2 + vh2;
+  float Fd[ND], dFd[ND], ex[ND], Sd[ND];
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    disc_F_d(r * m.half_inv_Rd[j], Fd[j], dFd[j]);
+    vint2 = fmaf(m.vd_c[j], Fd[j], vint2);
+    ex[j] = expf(-r * m.inv_Rd[j]);
+    Sd[j] = m.Sd_c[j] * ex[j];
+  }
+  const float vint = sqrtf(vint2);
+  float B = bd.Sb * m.Lb, Bv = 0.f, Bs2 = bd.Qb * m.Lb, Stot = bd.Sb;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const float Bd = Sd[j] * m.Ld[j];
+    B += Bd;
+    Bv = fmaf(Bd, m.ks[j] * cphi * vint, Bv);
+    Bs2 = fmaf(Bd, m.omk[j] * vint2, Bs2);
+    Stot += Sd[j];
+  }
+  const float iB = 1.0f / B;
+  const float f1 = Bv * iB;
+  const float f2 = sqrtf(Bs2 * iB);
+  const float iS = 1.0f / Stot;
+  const float f3 = B * 1e6f * iS;
+
+  // ---- reverse
+  const float gB = a.x - a.y * f1 * iB - 0.5f * a.z * f2 * iB + a.w * f3 * iB;
+  const float gBv = a.y * iB;
+  const float gBs2 = f2 > 0.f ? 0.5f * a.z / (f2 * B) : 0.f;
+  const float gStot = -a.w * f3 * iS;
+  const float gSb = fmaf(gB, m.Lb, gStot);
+  const float gQb = gBs2 * m.Lb;
+  acc[A_LB] += fmaf(gB, bd.Sb, gBs2 * bd.Qb);
+  float gcphi = 0.f, gvint = 0.f, gvint2 = 0.f, gr = 0.f;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    float* dj = acc + A_D0 + kPerDisc * j;
+    const float Bd = Sd[j] * m.Ld[j];
+    const float gBd = gB + gBv * m.ks[j] * cphi * vint + gBs2 * m.omk[j] * vint2;
+    const float gSd = fmaf(gBd, m.Ld[j], gStot);
+    dj[D_LD] += gBd * Sd[j];
+    dj[D_KS] += gBv * Bd * cphi * vint;
+    dj[D_OMK] += gBs2 * Bd * vint2;
+    gcphi = fmaf(gBv * Bd, m.ks[j] * vint, gcphi);
+    gvint = fmaf(gBv * Bd, m.ks[j] * cphi, gvint);
+    gvint2 = fmaf(gBs2 * Bd, m.omk[j], gvint2);
+    dj[D_SDC] += gSd * ex[j];
+    gr -= gSd * Sd[j] * m.inv_Rd[j];
+    dj[D_IRD] -= gSd * Sd[j] * r;
+  }
+  gvint2 += 0.5f * gvint / vint;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    float* dj = acc + A_D0 + kPerDisc * j;
+    dj[D_VDC] += gvint2 * Fd[j];
+    const float gy = gvint2 * m.vd_c[j] * dFd[j];
+    gr = fmaf(gy, m.half_inv_Rd[j], gr);
+    dj[D_HIRD] += gy * r;
+  }
+  // NFW halo: vh2 = vh_c m(x) / r, x = r / rs, m'(x) = x / (1 + x)^2
+  acc[A_VHC] += gvint2 * mh * inv_r;
+  const float xh1 = 1.0f + xh;
+  const float gxh = gvint2 * m.vh_c * (xh / (xh1 * xh1)) * inv_r;
+  gr += gxh * m.inv_rs - gvint2 * vh2 * inv_r;
+  acc[A_IRS] += gxh * r;
+  // bulge circular velocity: vb2 = G Mb u^(3-g) / r, u = r / (r + a)
+  const float omu = 1.0f - ub;
+  gr += gvint2 * vb2 * inv_r * (m.three_mg * omu - 1.0f);
+  acc[A_A] -= gvint2 * vb2 * m.three_mg * omu * m.inv_a;
+  acc[A_G] -= gvint2 * vb2 * lub * kLn2;
+  acc[A_MB] += gvint2 * vb2;
+  // bulge projected density and dispersion
+  acc[A_A] += gSb * bd.dSb_da + gQb * bd.dQb_da;
+  acc[A_G] += gSb * bd.dSb_dg + gQb * bd.dQb_dg;
+  acc[A_MB] += gSb * bd.Sb + 2.0f * gQb * bd.Qb;
+  const float gR = gSb * bd.dSb_dR + gQb * bd.dQb_dR;
+  // geometry
+  float gxr = gcphi * inv_r;
+  gr -= gcphi * cphi * inv_r;
+  float gyd = 0.f;
+  if (rfree) {
+    gxr = fmaf(gr * inv_r, xr, gxr);
+    gyd = gr * inv_r * yd;
+  }
+  const float gyr = gyd * m.inv_ci;
+  acc[A_INVCI] += gyd * yr;
+  float gX = gxr * m.cpa - gyr * m.spa;
+  float gY = gxr * m.spa + gyr * m.cpa;
+  if (Rfree) {
+    const float iR = 1.0f / R;
+    gX = fmaf(gR * iR, X, gX);
+    gY = fmaf(gR * iR, Y, gY);
+  }
+  acc[A_X0] += gX;
+  acc[A_Y0] += gY;
+  acc[A_PA] += gxr * yr - gyr * xr;
+}
+
+// d logL / d theta from the reduced constant adjoints (float64, one thread).
+__device__ void constants_to_theta(const float* __restrict__ th, int nd, const double* s, double* g) {
+  const double ln10 = 2.302585092994045684;
+  const double ci = cos((double)th[3]), si = sin((double)th[3]);
+  const double a = pow(10.0, (double)th[5]);
+  g[0] = -s[A_X0];
+  g[1] = -s[A_Y0];
+  g[2] = s[A_PA];
+  double gi = s[A_INVCI] * si / (ci * ci);
+  g[4] = ln10 * s[A_MB];
+  g[5] = ln10 * a * s[A_A];
+  g[6] = s[A_G];
+  g[10] = -s[A_LB] * (1e-6 / th[10]) / th[10];
+  // NFW
+  const double M200 = pow(10.0, (double)th[12]), c = th[13];
+  const double r200 = cbrt(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit));
+  const double mc = log1p(c) - c / (1.0 + c), dmc = c / ((1.0 + c) * (1.0 + c));
+  const double vh_c = kG * M200 / mc, inv_rs = c / r200;
+  g[12] = ln10 * (s[A_VHC] * vh_c - s[A_IRS] * inv_rs / 3.0);
+  g[13] = -s[A_VHC] * vh_c * dmc / mc + s[A_IRS] * inv_rs / c;
+  for (int j = 0; j < nd; ++j) {
+    const double* dj = s + A_D0 + kPerDisc * j;
+    const int o = j == 0 ? 7 : 15;
+    const double Md = pow(10.0, (double)th[o]), Rd = pow(10.0, (double)th[o + 1]), k = th[o + 2];
+    const double ml = j == 0 ? th[11] : th[18];
+    const double Sd_c = Md / (2.0 * kPi * Rd * Rd * ci), vd_c = 2.0 * kG * Md / Rd;
+    g[o] = ln10 * (dj[D_SDC] * Sd_c + dj[D_VDC] * vd_c);
+    g[o + 1] = ln10 * (-2.0 * dj[D_SDC] * Sd_c - dj[D_VDC] * vd_c - dj[D_IRD] / Rd - dj[D_HIRD] * 0.5 / Rd);
+    g[o + 2] = -dj[D_KS] * si - dj[D_OMK] * 2.0 * k / 3.0;
+    g[j == 0 ? 11 : 18] = -dj[D_LD] * (1e-6 / ml) / ml;
+    gi += dj[D_SDC] * Sd_c * si / ci - dj[D_KS] * k * ci;
+  }
+  g[3] = gi;
+}
+
+template <int NQ, int ND, int PSF>
+__global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
+  constexpr int NACC = A_D0 + kPerDisc * ND;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ModelConst mc;
+  __shared__ GalDev gs;
+  __shared__ double red[kAdjThreads / 32][NACC + 1];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const WorkItem w = a.items[a.order ? a.order[it] : it];
+    if (tid == 0) {
+      gs = a.gals[w.g];
+      mc.valid = decode_model(a.theta + (size_t)w.b * a.P, ND, gs, mc);
+    }
+    __syncthreads();
+    if (!mc.valid) {
+      __syncthreads();
+      continue;
+    }
+    const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx, ny = gs.ny, n = nx * ny;
+    const float* seed = a.seed + a.out_off[w.b];
+    float* taps = reinterpret_cast<float*>(smem_raw);
+    const int ntaps = PSF == 0 ? L : L * L;
+    float4* lam = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 4 + 15) / 16) * 16);
+    const int nj_max = (a.G + L - 1) / os + 2;
+    float4* V = lam + (size_t)nj_max * nx;
+    for (int t = tid; t < ntaps; t += kAdjThreads) taps[t] = __ldg(gs.taps + t);
+
+    float acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = 0.f;
+    double vsys_part = 0.0;
+    if (w.j0 == 0) {   // the first band of a row also adds d logL / d v_sys = sum_s lambda_v
+      for (int s = tid; s < n; s += kAdjThreads) vsys_part += (double)__ldg(seed + n + s);
+    }
+    const float pk = gs.pitch_kpa;
+    for (int y0 = w.j0; y0 < w.j1; y0 += a.G) {
+      const int G = min(a.G, w.j1 - y0);
+      int jlo = y0 - L + 1 <= 0 ? 0 : (y0 - L + os) / os;
+      const int jhi = min(ny - 1, (y0 + G - 1) / os);
+      const int nj = jhi - jlo + 1;
+      __syncthreads();   // taps loaded / previous chunk's lam and V no longer read
+      for (int t = tid; t < nj * nx; t += kAdjThreads) {
+        const int s = (jlo + t / nx) * nx + (t % nx);
+        lam[t] = make_float4(__ldg(seed + s), __ldg(seed + n + s), __ldg(seed + 2 * n + s), __ldg(seed + 3 * n + s));
+      }
+      __syncthreads();
+      if (PSF == 0) {
+        // vertical transposed pass: V[g][i] = sum_j T[y - j os] lambda(i, j)
+        for (int t = tid; t < G * nx; t += kAdjThreads) {
+          const int gr = t / nx, i = t - gr * nx;
+          const int y = y0 + gr;
+          int j0 = y - L + 1 <= 0 ? 0 : (y - L + os) / os;
+          const int j1 = min(ny - 1, y / os);
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int j = j0; j <= j1; ++j) {
+            const float tv = taps[y - j * os];
+            const float4 l = lam[(j - jlo) * nx + i];
+            v.x = fmaf(tv, l.x, v.x); v.y = fmaf(tv, l.y, v.y);
+            v.z = fmaf(tv, l.z, v.z); v.w = fmaf(tv, l.w, v.w);
+          }
+          V[t] = v;
+        }
+        __syncthreads();
+      }
+      for (int p = tid; p < G * W; p += kAdjThreads) {
+        const int gr = p / W, qx = p - gr * W;
+        const int y = y0 + gr;
+        int i0 = qx - L + 1 <= 0 ? 0 : (qx - L + os) / os;
+        const int i1 = min(nx - 1, qx / os);
+        float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (PSF == 0) {
+          for (int i = i0; i <= i1; ++i) {
+            const float th_ = taps[qx - i * os];
+            const float4 v = V[gr * nx + i];
+            s4.x = fmaf(th_, v.x, s4.x); s4.y = fmaf(th_, v.y, s4.y);
+            s4.z = fmaf(th_, v.z, s4.z); s4.w = fmaf(th_, v.w, s4.w);
+          }
+        } else {
+          int j0 = y - L + 1 <= 0 ? 0 : (y - L + os) / os;
+          const int j1 = min(ny - 1, y / os);
+          for (int j = j0; j <= j1; ++j) {
+            const float* wrow = taps + (y - j * os) * L;
+            for (int i = i0; i <= i1; ++i) {
+              const float tw = wrow[qx - i * os];
+              const float4 l = lam[(j - jlo) * nx + i];
+              s4.x = fmaf(tw, l.x, s4.x); s4.y = fmaf(tw, l.y, s4.y);
+              s4.z = fmaf(tw, l.z, s4.z); s4.w = fmaf(tw, l.w, s4.w);
+            }
+          }
+        }
+        const float X = fmaf((float)qx, pk, mc.X0);
+        const float Y = fmaf((float)y, pk, mc.Y0);
+        point_vjp<NQ, ND>(mc, X, Y, s4, acc);
+      }
+    }
+    // float64 block reduction of the adjoints, then theta-space gradient (one thread)
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) {
+      const double v = warp_sum((double)acc[k]);
+      if (lane == 0) red[warp][k] = v;
+    }
+    {
+      const double v = warp_sum(vsys_part);
+      if (lane == 0) red[warp][NACC] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double s[NACC + 1];
+      for (int k = 0; k <= NACC; ++k) {
+        s[k] = 0.0;
+        for (int q = 0; q < kAdjThreads / 32; ++q) s[k] += red[q][k];
+      }
+      double g[kMaxParams];
+      for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
+      constants_to_theta(a.theta + (size_t)w.b * a.P, ND, s, g);
+      g[14] = s[NACC];
+      double* dst = a.grad_acc + (size_t)w.b * a.P;
+      for (int p = 0; p < a.P; ++p)
+        if (g[p] != 0.0) atomicAdd(dst + p, g[p]);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void grad_out_kernel(const double* __restrict__ acc, int n, float* __restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) grad[i] = (float)acc[i];
+}
+
+template <int NQ, int ND>
+cudaError_t launch_nd(const AdjArgs& a, int psf2d, int grid, size_t smem, cudaStream_t st) {
+  if (psf2d) adjoint_kernel<NQ, ND, 1><<<grid, kAdjThreads, smem, st>>>(a);
+  else adjoint_kernel<NQ, ND, 0><<<grid, kAdjThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int adjoint_threads() { return kAdjThreads; }
+
+size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d) {
+  const int ntaps = psf2d ? L * L : L;
+  const int nj_max = (G + L - 1) / os + 2;
+  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)nj_max * nx * 16 + (psf2d ? 0 : (size_t)G * nx * 16);
+}
+
+const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d) {
+#define BANG_PICK(NQ, ND, PSF) \
+  if (n_quad == NQ && n_discs == ND && psf2d == PSF) return (const void*)adjoint_kernel<NQ, ND, PSF>;
+  BANG_PICK(64, 1, 0) BANG_PICK(64, 1, 1) BANG_PICK(64, 2, 0) BANG_PICK(64, 2, 1)
+  BANG_PICK(128, 1, 0) BANG_PICK(128, 1, 1) BANG_PICK(128, 2, 0) BANG_PICK(128, 2, 1)
+#undef BANG_PICK
+  return nullptr;
+}
+
+cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
+                           cudaStream_t st) {
+  if (n_quad == 64) return n_discs == 2 ? launch_nd<64, 2>(a, psf2d, grid, smem, st) : launch_nd<64, 1>(a, psf2d, grid, smem, st);
+  return n_discs == 2 ? launch_nd<128, 2>(a, psf2d, grid, smem, st) : launch_nd<128, 1>(a, psf2d, grid, smem, st);
+}
+
+cudaError_t launch_grad_out(const double* acc, int n, float* grad, cudaStream_t st) {
+  grad_out_kernel<<<(n + 255) / 256, 256, 0, st>>>(acc, n, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq) {
+  cudaError_t e = cudaMemcpyToSymbol(kNodeCm1, cm1, 192 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeLc, lc, 192 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeWs, ws, 192 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeWq, wq, 192 * sizeof(float));
+  return e;
+}
+
+}  // namespace bang

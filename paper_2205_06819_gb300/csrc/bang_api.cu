@@ -196,6 +196,10 @@ struct Plan {
   std::vector<int64_t> out_off;
   int64_t out_total = 0;
   DevBuf d_items, d_order, d_row_first, d_row_g, d_out_off, d_partial;
+  // adjoint sweep (kModeSeed plans only): bands of fine rows
+  int adj_items = 0, adj_G = 4, adj_grid = 0;
+  size_t adj_smem = 0;
+  DevBuf d_adj_items, d_adj_order;
   // graph replay
   cudaGraphExec_t graph = nullptr;
   const void* g_theta = nullptr;
@@ -382,6 +386,46 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   p->blocks_per_sm = per_sm;
   p->grid = std::min(p->n_items, per_sm * m->num_sms);
 
+  if (mode == bang::kModeSeed) {
+    // adjoint work items: bands of fine rows, sized for ~16 items per SM
+    long long total_rows = 0;
+    for (int b = 0; b < B; ++b) total_rows += m->gals[p->row_g[b]].H;
+    const long long target = 16LL * m->num_sms;
+    int rows = (int)std::min<long long>(64, std::max<long long>(p->adj_G, (total_rows + target - 1) / target));
+    rows = (rows + p->adj_G - 1) / p->adj_G * p->adj_G;
+    std::vector<bang::WorkItem> ai;
+    std::vector<double> acost;
+    for (int b = 0; b < B; ++b) {
+      const bang::GalDev& G = m->gals[p->row_g[b]];
+      for (int y = 0; y < G.H; y += rows) {
+        ai.push_back(bang::WorkItem{b, p->row_g[b], y, std::min(G.H, y + rows)});
+        acost.push_back((double)(std::min(G.H, y + rows) - y) * G.W);
+      }
+    }
+    std::vector<int> aorder(ai.size());
+    for (size_t i = 0; i < ai.size(); ++i) aorder[i] = (int)i;
+    std::stable_sort(aorder.begin(), aorder.end(), [&](int x, int y) { return acost[x] > acost[y]; });
+    p->adj_items = (int)ai.size();
+    size_t asmem = 0;
+    for (int b = 0; b < B; ++b) {
+      const bang::GalDev& G = m->gals[p->row_g[b]];
+      asmem = std::max(asmem, bang::adjoint_smem_bytes(G.L, G.os, G.nx, p->adj_G, psf2d));
+    }
+    p->adj_smem = asmem;
+    const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d);
+    cudaFuncAttributes afa;
+    BANG_CUDA(cudaFuncGetAttributes(&afa, ak));
+    if (asmem + afa.sharedSizeBytes > (size_t)m->smem_optin)
+      return fail(BANG_E_UNSUPPORTED, "adjoint kernel needs %zu bytes of shared memory", asmem + afa.sharedSizeBytes);
+    BANG_CUDA(cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   m->smem_optin - (int)afa.sharedSizeBytes));
+    int aper = 0;
+    BANG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&aper, ak, bang::adjoint_threads(), asmem));
+    if (aper < 1) return fail(BANG_E_UNSUPPORTED, "adjoint kernel does not fit on an SM");
+    p->adj_grid = std::min(p->adj_items, aper * m->num_sms);
+    BANG_CUDA(copy_vec(p->d_adj_items, ai));
+    BANG_CUDA(copy_vec(p->d_adj_order, aorder));
+  }
   BANG_CUDA(copy_vec(p->d_items, p->items));
   BANG_CUDA(copy_vec(p->d_order, p->order));
   BANG_CUDA(copy_vec(p->d_row_first, p->row_first));
@@ -413,6 +457,28 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   cudaError_t e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
   if (e != cudaSuccess || !logL) return e;
   return bang::launch_finalize(a.partial, p->d_row_first.as<int>(), p->d_row_g.as<int>(), a.gals, p->B, logL, st);
+}
+
+cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* logL, float* seed, double* grad_acc,
+                         float* grad, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->B * m->P, st);
+  if (e != cudaSuccess) return e;
+  e = enqueue_forward(m, p, theta, bang::kModeSeed, logL, seed, st);
+  if (e != cudaSuccess) return e;
+  bang::AdjArgs a{};
+  a.theta = theta;
+  a.P = m->P;
+  a.gals = m->d_gals.as<bang::GalDev>();
+  a.items = p->d_adj_items.as<bang::WorkItem>();
+  a.order = p->d_adj_order.as<int>();
+  a.n_items = p->adj_items;
+  a.G = p->adj_G;
+  a.seed = seed;
+  a.out_off = p->d_out_off.as<int64_t>();
+  a.grad_acc = grad_acc;
+  e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
+  if (e != cudaSuccess) return e;
+  return bang::launch_grad_out(grad_acc, p->B * m->P, grad, st);
 }
 
 }  // namespace
@@ -450,6 +516,7 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
     std::vector<float> cm1, lc, ws, wq;
     node_tables(cm1, lc, ws, wq);
     BANG_CUDA(bang::upload_nodes_forward(cm1.data(), lc.data(), ws.data(), wq.data()));
+    BANG_CUDA(bang::upload_nodes_adjoint(cm1.data(), lc.data(), ws.data(), wq.data()));
   }
   for (int g = 0; g < n_gal; ++g) {
     const bang_galaxy_desc& d = gal[g];
@@ -612,8 +679,37 @@ bang_status bang_model_maps(bang_model* m, const float* theta, const int32_t* ga
 
 bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,
                                     float* grad, void* stream) {
-  (void)m; (void)theta; (void)gal_idx; (void)B; (void)logL; (void)grad; (void)stream;
-  return fail(BANG_E_UNSUPPORTED, "bang_loglike_grad_batch: not built yet");
+  g_last_error.clear();
+  if (!m) return fail(BANG_E_INVALID_ARG, "null model");
+  if (!theta || !logL || !grad || B < 1) return fail(BANG_E_INVALID_ARG, "theta, logL or grad is null, or B < 1");
+  std::lock_guard<std::mutex> lock(m->mu);
+  BANG_CUDA(cudaSetDevice(m->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan* p = nullptr;
+  bang_status s = get_plan(m, gal_idx, B, bang::kModeSeed, &p);
+  if (s != BANG_OK) return s;
+  const size_t th_bytes = sizeof(float) * (size_t)B * m->P;
+  const bool th_dev = is_device_pointer(theta), l_dev = is_device_pointer(logL), g_dev = is_device_pointer(grad);
+  const float* d_theta = theta;
+  if (!th_dev) {
+    BANG_CUDA(m->stage_theta.reserve(th_bytes));
+    BANG_CUDA(cudaMemcpyAsync(m->stage_theta.p, theta, th_bytes, cudaMemcpyHostToDevice, st));
+    d_theta = m->stage_theta.as<float>();
+  }
+  double* d_logL = logL;
+  float* d_grad = grad;
+  if (!l_dev || !g_dev) {
+    BANG_CUDA(m->stage_out.reserve(sizeof(double) * B + th_bytes + 16));
+    if (!l_dev) d_logL = m->stage_out.as<double>();
+    if (!g_dev) d_grad = reinterpret_cast<float*>(m->stage_out.as<char>() + sizeof(double) * B);
+  }
+  BANG_CUDA(m->scratch_seed.reserve(sizeof(float) * (size_t)std::max<int64_t>(p->out_total, 4)));
+  BANG_CUDA(m->scratch_grad.reserve(sizeof(double) * (size_t)B * m->P));
+  BANG_CUDA(enqueue_grad(m, p, d_theta, d_logL, m->scratch_seed.as<float>(), m->scratch_grad.as<double>(), d_grad, st));
+  if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  if (!g_dev) BANG_CUDA(cudaMemcpyAsync(grad, d_grad, th_bytes, cudaMemcpyDeviceToHost, st));
+  if (!th_dev || !l_dev || !g_dev) BANG_CUDA(cudaStreamSynchronize(st));
+  return BANG_OK;
 }
 
 bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,

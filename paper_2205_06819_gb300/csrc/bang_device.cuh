@@ -167,6 +167,41 @@ __device__ __forceinline__ float disc_F(float y) {
   return gv * (0.25f * u);
 }
 
+// F(y) and dF/dy from the same fits (Horner carries the derivative along).
+//   y <= 1: F = s (P - ln y Q)  ->  F' = 2y [P + s P' - ln y (Q + s Q') - Q/2]
+//   y >  1: F = g(t) u / 4      ->  F' = -(u^2 / 4) [g + u g'(t) invhalf]
+__device__ __forceinline__ void disc_F_d(float y, float& F, float& dF) {
+  if (y <= 1.0f) {
+    const float s = y * y;
+    float P = kDiscP[BANG_DISC_DEG_A], Q = kDiscQ[BANG_DISC_DEG_A], dP = 0.f, dQ = 0.f;
+#pragma unroll
+    for (int k = BANG_DISC_DEG_A - 1; k >= 0; --k) {
+      dP = fmaf(dP, s, P);
+      dQ = fmaf(dQ, s, Q);
+      P = fmaf(P, s, kDiscP[k]);
+      Q = fmaf(Q, s, kDiscQ[k]);
+    }
+    const float ly = logf(y);
+    F = s * (P - ly * Q);
+    dF = 2.0f * y * (P + s * dP - ly * (Q + s * dQ) - 0.5f * Q);
+    return;
+  }
+  const float u = __frcp_rn(y);
+  const int e = (int)((__float_as_uint(u) >> 23) & 0xff) - 127;
+  int k = -e - 1;
+  k = k < 0 ? 0 : (k > BANG_DISC_NPIECE_B - 1 ? BANG_DISC_NPIECE_B - 1 : k);
+  const float ih = kDiscInvHalf[k];
+  const float t = (u - kDiscMid[k]) * ih;
+  float gv = kDiscG[k][BANG_DISC_DEG_B], dg = 0.f;
+#pragma unroll
+  for (int i = BANG_DISC_DEG_B - 1; i >= 0; --i) {
+    dg = fmaf(dg, t, gv);
+    gv = fmaf(gv, t, kDiscG[k][i]);
+  }
+  F = gv * (0.25f * u);
+  dF = -0.25f * u * u * fmaf(u * ih, dg, gv);
+}
+
 // m(x) = ln(1 + x) - x / (1 + x) of the NFW enclosed mass.  For x <= 1, with z = x / (2 + x):
 // m = 2 z^2 / (1 + z) + 2 z^3 (1/3 + z^2/5 + z^4/7 + ...), free of the cancellation at small x.
 __device__ __forceinline__ float nfw_m(float x) {

@@ -35,6 +35,7 @@ struct AdjArgs {
   const WorkItem* items;    // fine-row bands (j0/j1 hold fine padded rows [y0, y1))
   const int* order;
   int n_items;
+  int G;                    // fine rows per block step
   const float* seed;        // d logL / dF at the spaxels, row b at out_off[b]
   const int64_t* out_off;
   double* grad_acc;         // [B][P] float64 accumulators (zeroed before the launch)
@@ -48,5 +49,13 @@ cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d,
 cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
                             double* logL, cudaStream_t st);
 cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float* ws, const float* wq);
+
+int adjoint_threads();
+size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d);
+const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d);
+cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
+                           cudaStream_t st);
+cudaError_t launch_grad_out(const double* acc, int n, float* grad, cudaStream_t st);
+cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq);
 
 }  // namespace bang
