@@ -129,6 +129,36 @@ int64_t bang_model_maps_size(const bang_model *m, const int32_t *gal_idx, int B)
 bang_status bang_loglike_plain(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
                                double *logL, void *stream);
 
+/* No-allocation variant of bang_loglike_batch.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory while they run.
+ *
+ * bang_loglike_batch allocates per-batch scratch (its work-item table and per-item chi^2
+ * partial sums) with cudaMalloc the first time it meets a batch shape, and stages host
+ * arrays through library-owned buffers.  Some callers cannot allow that: a program whose
+ * device memory is handed in full to another allocator (for example a framework's caching
+ * allocator that has reserved the GPU), a sampler loop that cannot take the device-wide
+ * synchronisation cudaMalloc and cudaFree may cause, or an application that must know the
+ * library's device footprint before it starts.  This call makes no cudaMalloc, cudaFree or
+ * other allocating call.  Its scratch is one fixed array of about 1.2 MB compiled into the
+ * library's device code; every GPU that loads the library holds it until the process exits.
+ *
+ * theta [B][P] float32 and logL [B] float64 must be device memory of the model's device
+ * (host pointers give BANG_E_INVALID_ARG; there is no staging).  gal_idx is a HOST array
+ * [B] of galaxy indices or NULL (galaxy 0 for every row); it is copied on `stream`, so a
+ * pinned gal_idx must stay unchanged until the stream has passed this call.  B is at most
+ * 32768 (the size the scratch was built for); a larger B returns BANG_E_INVALID_ARG and
+ * launches nothing.  Each row is one work item (no bands), so logL equals
+ * bang_loglike_batch's result up to the order of float64 additions.
+ *
+ * The first call on a device looks up the scratch's device address (cudaGetSymbolAddress,
+ * with that device current) and keeps it; make that first call before any stream capture.
+ * All calls share the one scratch array, which keeps what the last call wrote; every entry
+ * a call reads is written earlier in the same call, so nothing has to be cleared between
+ * calls.  Two calls that overlap on the GPU (two streams, or two host threads) race on the
+ * scratch: serialise them.  Asynchronous on `stream`. */
+bang_status bang_loglike_batch_noalloc(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
+                                       double *logL, void *stream);
+
 /* Chooses launch parameters (rows of the fine grid per block step, blocks per SM) for
  * batches like (gal_idx, B) by timing candidates on the device; the choice is cached in the
  * model.  gal_idx as in bang_loglike_batch.  Synchronous. */

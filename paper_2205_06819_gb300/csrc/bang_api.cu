@@ -483,6 +483,34 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
 
 }  // namespace
 
+namespace bang {
+
+bool model_view(const bang_model* m, ModelView* v) {
+  if (!m || !v) return false;
+  v->device = m->device;
+  v->n_gal = (int)m->gals.size();
+  v->n_quad = m->opts.n_quad;
+  v->n_discs = m->opts.n_discs;
+  v->P = m->P;
+  v->num_sms = m->num_sms;
+  v->smem_optin = m->smem_optin;
+  v->h_gals = m->gals.data();
+  v->d_gals = m->d_gals.as<GalDev>();
+  return true;
+}
+
+bang_status set_error(bang_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+}  // namespace bang
+
 extern "C" {
 
 const char* bang_last_error(void) { return g_last_error.c_str(); }

@@ -16,6 +16,9 @@
 // accumulators are live at any time.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <mutex>
+
 #include "bang_device.cuh"
 #include "bang_internal.h"
 
@@ -282,3 +285,146 @@ cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float*
 }
 
 }  // namespace bang
+
+// ============================================================================================
+// bang_loglike_batch_noalloc: the forward launch with its scratch in a fixed device array.
+//
+// bang_loglike_batch keeps per-batch scratch (the work-item table and the per-item chi^2
+// partial sums) in device memory that it allocates the first time it sees a batch shape.
+// This variant allocates nothing: the same scratch lives in g_noalloc_scratch, a file-scope
+// __device__ array of kNoAllocScratchBytes that every device which loads the library holds
+// until the process exits.  Host code cannot use the array's name as a device address (it
+// names a host-side shadow), so the address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, and passed to the kernels.
+namespace bang {
+namespace {
+
+constexpr int kNoAllocMaxRows = 32768;
+constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t kNaItemsOff = 0;
+constexpr size_t kNaPartialOff = align256(kNaItemsOff + sizeof(WorkItem) * kNoAllocMaxRows);
+constexpr size_t kNaRowFirstOff = align256(kNaPartialOff + sizeof(double) * kNoAllocMaxRows);
+constexpr size_t kNaRowGOff = align256(kNaRowFirstOff + sizeof(int) * (kNoAllocMaxRows + 1));
+constexpr size_t kNaGalIdxOff = align256(kNaRowGOff + sizeof(int) * kNoAllocMaxRows);
+constexpr size_t kNoAllocScratchBytes = align256(kNaGalIdxOff + sizeof(int) * kNoAllocMaxRows);   // ~1.2 MB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mu;
+unsigned char* g_na_ptr[kNaMaxDevices] = {};
+
+// One work item per row (whole spaxel grid), row b against galaxy gal[b] (0 when gal is NULL).
+__global__ void noalloc_items_kernel(const int* __restrict__ gal, const GalDev* __restrict__ gals, int B,
+                                     WorkItem* __restrict__ items, int* __restrict__ row_first,
+                                     int* __restrict__ row_g) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const int g = gal ? gal[b] : 0;
+  items[b] = WorkItem{b, g, 0, gals[g].ny};
+  row_first[b] = b;
+  row_g[b] = g;
+  if (b == B - 1) row_first[B] = B;
+}
+
+}  // namespace
+}  // namespace bang
+
+extern "C" bang_status bang_loglike_batch_noalloc(bang_model* m, const float* theta, const int32_t* gal_idx, int B,
+                                                  double* logL, void* stream) {
+  using namespace bang;
+  ModelView v;
+  if (!model_view(m, &v)) return set_error(BANG_E_INVALID_ARG, "null model");
+  if (!theta || !logL) return set_error(BANG_E_INVALID_ARG, "theta or logL is null");
+  if (B < 1 || B > kNoAllocMaxRows)
+    return set_error(BANG_E_INVALID_ARG, "bang_loglike_batch_noalloc: B = %d outside [1, %d] (fixed scratch of %zu bytes)",
+                     B, kNoAllocMaxRows, kNoAllocScratchBytes);
+  if (v.device < 0 || v.device >= kNaMaxDevices) return set_error(BANG_E_UNSUPPORTED, "device index %d", v.device);
+  cudaError_t e = cudaSetDevice(v.device);
+  if (e != cudaSuccess) return set_error(BANG_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  for (const void* ptr : {(const void*)theta, (const void*)logL}) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      return set_error(BANG_E_INVALID_ARG, "bang_loglike_batch_noalloc: theta and logL must be device memory");
+    }
+  }
+  int psf2d = -1;
+  size_t smem = 0;
+  for (int b = 0; b < B; ++b) {
+    const int g = gal_idx ? gal_idx[b] : 0;
+    if (g < 0 || g >= v.n_gal) return set_error(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
+    const GalDev& G = v.h_gals[g];
+    if (psf2d < 0) psf2d = G.psf_kind;
+    if (G.psf_kind != psf2d) return set_error(BANG_E_UNSUPPORTED, "a batch mixes Gaussian and Moffat PSF galaxies");
+    smem = std::max(smem, forward_smem_bytes(G.L, G.os, G.nx, G.W, 4, psf2d));
+    if (!gal_idx) break;
+  }
+  int rows_per_step = 4;
+  const void* kp = forward_kernel_ptr(v.n_quad, v.n_discs, psf2d, kModeLogL);
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kp)) != cudaSuccess)
+    return set_error(BANG_E_CUDA, "cudaFuncGetAttributes: %s", cudaGetErrorString(e));
+  if (smem + fa.sharedSizeBytes > (size_t)v.smem_optin) {
+    rows_per_step = 1;
+    smem = 0;
+    for (int b = 0; b < B; ++b) {
+      const GalDev& G = v.h_gals[gal_idx ? gal_idx[b] : 0];
+      smem = std::max(smem, forward_smem_bytes(G.L, G.os, G.nx, G.W, 1, psf2d));
+      if (!gal_idx) break;
+    }
+    if (smem + fa.sharedSizeBytes > (size_t)v.smem_optin)
+      return set_error(BANG_E_UNSUPPORTED, "galaxy too large for one block's shared memory");
+  }
+
+  // set-up, once per device: the device address of the scratch array
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_ptr[v.device]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return set_error(BANG_E_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
+      g_na_ptr[v.device] = static_cast<unsigned char*>(p);
+    }
+    scratch = g_na_ptr[v.device];
+  }
+  if ((e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                v.smem_optin - (int)fa.sharedSizeBytes)) != cudaSuccess)
+    return set_error(BANG_E_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp, forward_threads(), smem)) != cudaSuccess ||
+      per_sm < 1)
+    return set_error(BANG_E_CUDA, "occupancy query failed");
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WorkItem* items = reinterpret_cast<WorkItem*>(scratch + kNaItemsOff);
+  double* partial = reinterpret_cast<double*>(scratch + kNaPartialOff);
+  int* row_first = reinterpret_cast<int*>(scratch + kNaRowFirstOff);
+  int* row_g = reinterpret_cast<int*>(scratch + kNaRowGOff);
+  int* gal_dev = nullptr;
+  if (gal_idx) {
+    gal_dev = reinterpret_cast<int*>(scratch + kNaGalIdxOff);
+    if ((e = cudaMemcpyAsync(gal_dev, gal_idx, sizeof(int) * (size_t)B, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return set_error(BANG_E_CUDA, "copy of gal_idx: %s", cudaGetErrorString(e));
+  }
+  noalloc_items_kernel<<<(B + 127) / 128, 128, 0, st>>>(gal_dev, v.d_gals, B, items, row_first, row_g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return set_error(BANG_E_CUDA, "item kernel: %s", cudaGetErrorString(e));
+  FwdArgs a{};
+  a.theta = theta;
+  a.P = v.P;
+  a.gals = v.d_gals;
+  a.items = items;
+  a.order = nullptr;
+  a.n_items = B;
+  a.G = rows_per_step;
+  a.partial = partial;
+  a.out_off = nullptr;
+  const int grid = std::min(B, per_sm * v.num_sms);
+  if ((e = launch_forward(a, v.n_quad, v.n_discs, psf2d, kModeLogL, grid, smem, st)) != cudaSuccess)
+    return set_error(BANG_E_CUDA, "forward kernel: %s", cudaGetErrorString(e));
+  if ((e = launch_finalize(partial, row_first, row_g, v.d_gals, B, logL, st)) != cudaSuccess)
+    return set_error(BANG_E_CUDA, "finalize kernel: %s", cudaGetErrorString(e));
+  return BANG_OK;
+}

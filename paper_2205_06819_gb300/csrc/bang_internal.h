@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/bang.h"
+
 namespace bang {
 
 struct GalDev;
@@ -40,6 +42,17 @@ struct AdjArgs {
   const int64_t* out_off;
   double* grad_acc;         // [B][P] float64 accumulators (zeroed before the launch)
 };
+
+// Read-only view of a model's immutable device state (for entry points defined outside
+// bang_api.cu).
+struct ModelView {
+  int device, n_gal, n_quad, n_discs, P, num_sms, smem_optin;
+  const GalDev* h_gals;   // host copies (device pointers inside)
+  const GalDev* d_gals;   // device array [n_gal]
+};
+bool model_view(const bang_model* m, ModelView* v);
+// Records a message for bang_last_error() on this thread and returns s.
+bang_status set_error(bang_status s, const char* fmt, ...);
 
 int forward_threads();
 size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d);
