@@ -181,6 +181,56 @@ def cpu_oracle_sample(wl, gal, theta, seconds: float):
                       f"{dt:.1f} s"}
 
 
+def time_plain(model, theta, logL, B):
+    """The same batch through the paper's one-kernel-per-task form (bang_loglike_plain)."""
+    import torch
+    from paper_2205_06819_gb300 import _lib
+    per_row = 9
+    model.loglike_plain(theta[:8])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = model.loglike_plain(theta)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ref = model.loglike(theta)
+    fin = torch.isfinite(ref)
+    rel = ((out[fin] - ref[fin]).abs() / ref[fin].abs()).max().item()
+    return {"value": B / ms * 1e3, "unit": "logL evals/s", "ms_per_batch": ms, "launches": per_row * B,
+            "max_rel_logL_vs_fused": rel,
+            "form": "one kernel per task per parameter vector, 64 threads/block, intermediates in HBM"}
+
+
+def time_adjoint(torch, steps=10):
+    """logL + gradient for the 256-row adjoint workload (80x80, os 5), device-timed."""
+    wl = synth.workload("adjoint")
+    model, _, theta_np = make_model(wl, 0, torch)
+    theta = torch.from_numpy(theta_np).cuda()
+    for _ in range(2):
+        model.loglike_grad(theta)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        model.loglike_grad(theta)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    fwd0, fwd1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = torch.empty(theta.shape[0], dtype=torch.float64, device="cuda")
+    fwd0.record()
+    for _ in range(steps):
+        model.loglike(theta, out=out)
+    fwd1.record()
+    torch.cuda.synchronize()
+    fms = fwd0.elapsed_time(fwd1) / steps
+    model.close()
+    return {"value": wl.batch / ms * 1e3, "unit": "fwd+adjoint evals/s", "ms_per_batch": ms,
+            "rows": wl.batch, "forward_only_ms": fms, "adjoint_over_forward": ms / fms,
+            "workload": f"adjoint: {wl.description}"}
+
+
 # ----------------------------------------------------------------------------- arms
 def run_reference(args):
     ws, rank, _ = dist_env()
@@ -333,6 +383,8 @@ def run_ours(args):
         "wall_s_timed": wall,
     }
     if ws == 1 and not args.no_extras:
+        line["plain_gpu"] = time_plain(model, theta, logL, B)
+        line["fwd_adjoint"] = time_adjoint(torch)
         line["cpu_baseline"] = cpu_oracle_sample(wl, gal, theta_np, args.cpu_seconds)
     elif ws == 1:
         line["cpu_baseline"] = None

@@ -241,7 +241,7 @@ struct bang_model {
   std::vector<int> h_of;
   std::vector<std::unique_ptr<DevBuf>> owned;
   DevBuf d_gals;
-  DevBuf stage_theta, stage_out, stage_out2, scratch_seed, scratch_grad;
+  DevBuf stage_theta, stage_out, stage_out2, scratch_seed, scratch_grad, scratch_plain;
   std::list<std::unique_ptr<Plan>> plans;   // most recently used first
   std::map<uint64_t, int> tuned_G;          // batch-shape key -> rows per block step
   std::mutex mu;
@@ -545,6 +545,7 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
     node_tables(cm1, lc, ws, wq);
     BANG_CUDA(bang::upload_nodes_forward(cm1.data(), lc.data(), ws.data(), wq.data()));
     BANG_CUDA(bang::upload_nodes_adjoint(cm1.data(), lc.data(), ws.data(), wq.data()));
+    BANG_CUDA(bang::upload_nodes_plain(cm1.data(), lc.data(), ws.data(), wq.data()));
   }
   for (int g = 0; g < n_gal; ++g) {
     const bang_galaxy_desc& d = gal[g];
@@ -742,8 +743,41 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
 
 bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,
                                void* stream) {
-  (void)m; (void)theta; (void)gal_idx; (void)B; (void)logL; (void)stream;
-  return fail(BANG_E_UNSUPPORTED, "bang_loglike_plain: not built yet");
+  g_last_error.clear();
+  if (!m) return fail(BANG_E_INVALID_ARG, "null model");
+  if (!theta || !logL || B < 1) return fail(BANG_E_INVALID_ARG, "theta or logL is null, or B < 1");
+  std::lock_guard<std::mutex> lock(m->mu);
+  BANG_CUDA(cudaSetDevice(m->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  size_t need = 0;
+  for (int b = 0; b < B; ++b) {
+    const int g = gal_idx ? gal_idx[b] : 0;
+    if (g < 0 || g >= (int)m->gals.size()) return fail(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
+    const bang::GalDev& G = m->gals[g];
+    need = std::max(need, bang::plain_scratch_bytes(G.W * G.H, G.nx * G.ny));
+  }
+  BANG_CUDA(m->scratch_plain.reserve(need));
+  const size_t th_bytes = sizeof(float) * (size_t)B * m->P;
+  const bool th_dev = is_device_pointer(theta), l_dev = is_device_pointer(logL);
+  const float* d_theta = theta;
+  if (!th_dev) {
+    BANG_CUDA(m->stage_theta.reserve(th_bytes));
+    BANG_CUDA(cudaMemcpyAsync(m->stage_theta.p, theta, th_bytes, cudaMemcpyHostToDevice, st));
+    d_theta = m->stage_theta.as<float>();
+  }
+  double* d_logL = logL;
+  if (!l_dev) {
+    BANG_CUDA(m->stage_out.reserve(sizeof(double) * B));
+    d_logL = m->stage_out.as<double>();
+  }
+  for (int b = 0; b < B; ++b) {
+    const int g = gal_idx ? gal_idx[b] : 0;
+    BANG_CUDA(bang::launch_plain_row(d_theta + (size_t)b * m->P, m->P, m->opts.n_quad, m->opts.n_discs,
+                                     m->d_gals.as<bang::GalDev>() + g, m->gals[g], m->scratch_plain.p, d_logL + b, st));
+  }
+  if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  if (!th_dev || !l_dev) BANG_CUDA(cudaStreamSynchronize(st));
+  return BANG_OK;
 }
 
 bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {

@@ -71,4 +71,10 @@ cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d,
 cudaError_t launch_grad_out(const double* acc, int n, float* grad, cudaStream_t st);
 cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq);
 
+size_t plain_scratch_bytes(int N, int n);
+int plain_launches_per_row();
+cudaError_t launch_plain_row(const float* theta, int P, int n_quad, int n_discs, const GalDev* d_gal,
+                             const GalDev& h_gal, void* scratch, double* logL, cudaStream_t st);
+cudaError_t upload_nodes_plain(const float* cm1, const float* lc, const float* ws, const float* wq);
+
 }  // namespace bang
