@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--workload", default="batched", choices=synth.WORKLOADS)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain-form and adjoint side measurements")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (bang_model_tune) before timing")
     return ap.parse_args()
 
 
@@ -127,11 +128,28 @@ def points_per_eval(spec: synth.GalaxySpec) -> int:
 
 
 def algorithmic_sfu_ops(wl: synth.Workload) -> float:
-    """Transcendental (SFU) operations of one evaluation: per padded fine point, one log2 and
-    two exp2 per radial quadrature node, plus 16 for the rest of the point (two square
-    roots of the radii, two of the velocities' roots, the bulge, halo and disc powers,
-    logarithms and exponentials, and the reciprocals of the light weighting)."""
-    return float(points_per_eval(wl.galaxies[0])) * (3 * wl.n_quad + 16)
+    """Transcendental (SFU) operations of one batch: per padded fine point, one log2 and two
+    exp2 per radial quadrature node, plus 16 for the rest of the point (two square roots of
+    the radii, one of the velocity, the bulge, halo and disc powers, logarithms and
+    exponentials, and the reciprocals of the light weighting)."""
+    pts = sum(points_per_eval(g) for g in wl.galaxies) * wl.rows_per_galaxy
+    return float(pts) * (3 * wl.n_quad + 16)
+
+
+def combine_max(local: float, dist, device) -> float:
+    """The maximum of a per-rank number over all ranks (the job takes as long as its slowest
+    rank); the identity without torch.distributed."""
+    if dist is None:
+        return local
+    import torch
+    t = torch.tensor([local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_batch_seed(workload_id: int, rank: int) -> int:
+    """Each rank evaluates its own batch of the same size (weak scaling)."""
+    return synth.batch_seed(workload_id) + 1000 * rank
 
 
 def sfu_peak_ops_per_s(n_quad: int, mhz: float, sms: int) -> float:
@@ -142,23 +160,30 @@ def sfu_peak_ops_per_s(n_quad: int, mhz: float, sms: int) -> float:
 
 # ----------------------------------------------------------------------------- data
 def make_model(wl: synth.Workload, rank: int, torch):
-    """Seeded synthetic galaxy: noise-free maps from the library at theta_true plus noise."""
+    """Seeded synthetic galaxies: noise-free maps from the library at each galaxy's
+    theta_true plus noise; the batch is rows_per_galaxy rows per galaxy."""
     from paper_2205_06819_gb300.model import Galaxy, Model
     wid = synth.workload_id(wl.name)
     box = synth.prior_box(wl.n_discs, wl.gamma_fixed)
-    s = wl.galaxies[0]
-    tt = synth.draw_theta_true(box, synth.dataset_seed(wid))
-    ones = np.ones((4, s.ny, s.nx), np.float32)
-    probe = Model(Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, ones, ones,
-                         psf_kind=s.psf_kind, moffat_beta=s.moffat_beta), n_discs=wl.n_discs, n_quad=wl.n_quad)
-    true = probe.maps(torch.from_numpy(tt.astype(np.float32)[None]).cuda())[0].cpu().numpy().astype(np.float64)
+    tts = [synth.draw_theta_true(box, synth.dataset_seed(wid, g)) for g in range(len(wl.galaxies))]
+    probes = [Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec,
+                     np.ones((4, s.ny, s.nx), np.float32), np.ones((4, s.ny, s.nx), np.float32),
+                     psf_kind=s.psf_kind, moffat_beta=s.moffat_beta) for s in wl.galaxies]
+    probe = Model(probes, n_discs=wl.n_discs, n_quad=wl.n_quad)
+    gi = np.arange(len(wl.galaxies), dtype=np.int32)
+    true = probe.maps(torch.from_numpy(np.stack(tts).astype(np.float32)).cuda(), gi if len(gi) > 1 else None)
     probe.close()
-    data, err, mask = synth.noisy_data(true, seed=synth.dataset_seed(wid))
-    gal = Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, data, err, mask,
-                 psf_kind=s.psf_kind, moffat_beta=s.moffat_beta)
-    model = Model(gal, n_discs=wl.n_discs, n_quad=wl.n_quad)
-    theta = synth.draw_theta_batch(box, tt, wl.batch, synth.batch_seed(wid) + 1000 * rank).astype(np.float32)
-    return model, gal, theta
+    gals = []
+    for g, s in enumerate(wl.galaxies):
+        data, err, mask = synth.noisy_data(true[g].cpu().numpy().astype(np.float64), seed=synth.dataset_seed(wid, g))
+        gals.append(Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, data, err, mask,
+                           psf_kind=s.psf_kind, moffat_beta=s.moffat_beta))
+    model = Model(gals, n_discs=wl.n_discs, n_quad=wl.n_quad)
+    seed = rank_batch_seed(wid, rank)
+    theta = np.concatenate([synth.draw_theta_batch(box, tts[g], wl.rows_per_galaxy, seed + 7 * g)
+                            for g in range(len(gals))]).astype(np.float32)
+    gal_idx = np.repeat(gi, wl.rows_per_galaxy) if len(gals) > 1 else None
+    return model, gals, theta, gal_idx
 
 
 def cpu_oracle_sample(wl, gal, theta, seconds: float):
@@ -205,7 +230,8 @@ def time_plain(model, theta, logL, B):
 def time_adjoint(torch, steps=10):
     """logL + gradient for the 256-row adjoint workload (80x80, os 5), device-timed."""
     wl = synth.workload("adjoint")
-    model, _, theta_np = make_model(wl, 0, torch)
+    model, _, theta_np, _ = make_model(wl, 0, torch)
+    model.tune(theta_np.shape[0])
     theta = torch.from_numpy(theta_np).cuda()
     for _ in range(2):
         model.loglike_grad(theta)
@@ -287,9 +313,10 @@ def run_ours(args):
     from paper_2205_06819_gb300 import build as bmod
     bmod.build()
     wl = synth.workload(args.workload)
-    if len(wl.galaxies) != 1:
-        raise SystemExit("bench.py times single-galaxy workloads; the uneven batch is a parity case")
-    model, gal, theta_np = make_model(wl, rank, torch)
+    model, gals, theta_np, gal_idx = make_model(wl, rank, torch)
+    gal = gals[0]
+    if not args.no_tune:
+        model.tune(theta_np.shape[0], gal_idx)
     B, P = theta_np.shape
     theta = torch.from_numpy(theta_np).cuda()
     logL = torch.empty(B, dtype=torch.float64, device="cuda")
@@ -301,7 +328,7 @@ def run_ours(args):
             dist.barrier()
 
     for _ in range(args.warmup):
-        model.loglike(theta, out=logL)
+        model.loglike(theta, gal_idx, out=logL)
     torch.cuda.synchronize()
 
     # device-timed steps (L2 flushed between steps, outside the events)
@@ -316,18 +343,14 @@ def run_ours(args):
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         starts[k].record(stream)
-        model.loglike(theta, out=logL)
+        model.loglike(theta, gal_idx, out=logL)
         ends[k].record(stream)
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - w0
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    dev_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
+    dev_s = combine_max(sum(step_ms) / 1e3, dist, "cuda")
     value = ws * B * args.steps / dev_s
     assert np.isfinite(logL.cpu().numpy()).any()
 
@@ -335,20 +358,16 @@ def run_ours(args):
     th_host = torch.from_numpy(theta_np).pin_memory()
     out_host = torch.empty(B, dtype=torch.float64).pin_memory()
     for _ in range(2):
-        model.loglike(th_host, out=out_host)
+        model.loglike(th_host, gal_idx, out=out_host)
     e2e_t = []
     barrier()
     for k in range(max(3, args.steps // 4)):
         flush.fill_(k & 0xff)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        model.loglike(th_host, out=out_host)
+        model.loglike(th_host, gal_idx, out=out_host)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = combine_max(sum(e2e_t), dist, "cuda")
     e2e_value = ws * B * len(e2e_t) / e2e_s
 
     if rank != 0:
@@ -360,7 +379,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL))
     step_s = dev_s / args.steps
-    ops = algorithmic_sfu_ops(wl) * B
+    ops = algorithmic_sfu_ops(wl)
     achieved = ops / step_s / 1e9
     peak = sfu_peak_ops_per_s(wl.n_quad, mhz, sms) / 1e9
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["stamp"] == kernel_stamp() else None
@@ -369,8 +388,10 @@ def run_ours(args):
         "metric": "logL evals/s", "value": value, "unit": "logL evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{wl.name}: {wl.description}", "rows": B, "padded_fine_points": points_per_eval(
-            wl.galaxies[0]), "n_quad": wl.n_quad, "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "config": {"workload": f"{wl.name}: {wl.description}", "rows": B,
+                   "padded_fine_points_per_row": points_per_eval(wl.galaxies[0]) if len(wl.galaxies) == 1 else
+                   "per galaxy", "n_quad": wl.n_quad, "galaxies": len(wl.galaxies),
+                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
         "e2e": {"value": e2e_value, "unit": "logL evals/s", "h2d_bytes_per_step": int(B * P * 4),
                 "d2h_bytes_per_step": int(B * 8)},
         "gpu_launches": 2 * args.steps,
@@ -382,7 +403,7 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed": wall,
     }
-    if ws == 1 and not args.no_extras:
+    if ws == 1 and not args.no_extras and len(wl.galaxies) == 1:
         line["plain_gpu"] = time_plain(model, theta, logL, B)
         line["fwd_adjoint"] = time_adjoint(torch)
         line["cpu_baseline"] = cpu_oracle_sample(wl, gal, theta_np, args.cpu_seconds)

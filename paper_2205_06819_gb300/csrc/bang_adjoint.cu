@@ -34,6 +34,21 @@ namespace {
 constexpr int kAdjThreads = 256;
 constexpr float kLn2 = 0.69314718055994531f;
 
+// Next work item: from the shared counter when the launch has one (dynamic scheduling),
+// otherwise the fixed grid stride.  Always a block-wide barrier, so that thread 0 may
+// overwrite the shared item state afterwards.
+#define BANG_NEXT_ITEM(it)                                                     \
+  do {                                                                         \
+    if (a.queue) {                                                             \
+      if (threadIdx.x == 0) next_item = atomicAdd(a.queue, 1) + (int)gridDim.x; \
+      __syncthreads();                                                         \
+      it = next_item;                                                          \
+    } else {                                                                   \
+      __syncthreads();                                                         \
+      it += (int)gridDim.x;                                                    \
+    }                                                                          \
+  } while (0)
+
 // adjoint accumulators (per thread), adjoints of the per-model constants
 enum {
   A_X0 = 0,   // d/dX0 (X0 = xoff - x0)
@@ -272,7 +287,10 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
   __shared__ double red[kAdjThreads / 32][NACC + 1];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+  __shared__ int next_item;
+  // first item by block index, then either the next one from the shared counter (dynamic
+  // scheduling, longest items first) or a fixed stride
+  for (int it = blockIdx.x; it < a.n_items;) {
     const WorkItem w = a.items[a.order ? a.order[it] : it];
     if (tid == 0) {
       gs = a.gals[w.g];
@@ -280,7 +298,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
     }
     __syncthreads();
     if (!mc.valid) {
-      __syncthreads();
+      BANG_NEXT_ITEM(it);
       continue;
     }
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx, ny = gs.ny, n = nx * ny;
@@ -385,7 +403,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
       for (int p = 0; p < a.P; ++p)
         if (g[p] != 0.0) atomicAdd(dst + p, g[p]);
     }
-    __syncthreads();
+    BANG_NEXT_ITEM(it);
   }
 }
 

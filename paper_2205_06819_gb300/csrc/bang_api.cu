@@ -195,7 +195,8 @@ struct Plan {
   std::vector<int> order, row_first, row_g;
   std::vector<int64_t> out_off;
   int64_t out_total = 0;
-  DevBuf d_items, d_order, d_row_first, d_row_g, d_out_off, d_partial;
+  DevBuf d_items, d_order, d_row_first, d_row_g, d_out_off, d_partial, d_queue;
+  int bands = 1;
   // adjoint sweep (kModeSeed plans only): bands of fine rows
   int adj_items = 0, adj_G = 4, adj_grid = 0;
   size_t adj_smem = 0;
@@ -243,7 +244,11 @@ struct bang_model {
   DevBuf d_gals;
   DevBuf stage_theta, stage_out, stage_out2, scratch_seed, scratch_grad, scratch_plain;
   std::list<std::unique_ptr<Plan>> plans;   // most recently used first
-  std::map<uint64_t, int> tuned_G;          // batch-shape key -> rows per block step
+  struct Tuning {
+    int G = 4;       // fine rows per block step of the forward kernel
+    int bands = 0;   // spaxel-row bands per batch row (0: default policy)
+  };
+  std::map<uint64_t, Tuning> tuned;         // batch-shape key -> launch parameters
   std::mutex mu;
   cudaStream_t capture_stream = nullptr;
   bool use_graphs = true;
@@ -292,16 +297,27 @@ cudaError_t copy_vec(DevBuf& d, const std::vector<T>& v) {
 
 // Bands of spaxel rows per batch row: 1 when the batch fills the GPU, otherwise enough to
 // give every SM about two work items (each band re-evaluates its 2h-row halo).
-int bands_for(const bang_model* m, int B, int ny) {
+int bands_for(const bang_model* m, int B, int ny, int forced) {
+  if (forced > 0) return std::max(1, std::min(ny, forced));
   if (B >= m->num_sms) return 1;
   const int want = (2 * m->num_sms + B - 1) / B;
   return std::max(1, std::min(ny, want));
 }
 
-bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Plan** out) {
+uint64_t shape_key(const int32_t* gal_idx, int B) {
   uint64_t key = hash_bytes(&B, sizeof B);
-  key = hash_bytes(&mode, sizeof mode, key);
   if (gal_idx) key = hash_bytes(gal_idx, sizeof(int32_t) * (size_t)B, key);
+  return key;
+}
+
+bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Plan** out) {
+  const uint64_t skey = shape_key(gal_idx, B);
+  const uint64_t key = hash_bytes(&mode, sizeof mode, skey);
+  bang_model::Tuning tune;
+  {
+    auto t = m->tuned.find(skey);
+    if (t != m->tuned.end()) tune = t->second;
+  }
   for (auto it = m->plans.begin(); it != m->plans.end(); ++it) {
     if ((*it)->key == key) {
       m->plans.splice(m->plans.begin(), m->plans, it);
@@ -326,7 +342,8 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     p->out_off[b] = off;
     off += (int64_t)4 * G.nx * G.ny;
     p->row_first[b] = (int)p->items.size();
-    const int nb = bands_for(m, B, G.ny);
+    const int nb = bands_for(m, B, G.ny, tune.bands);
+    p->bands = std::max(p->bands, nb);
     for (int k = 0; k < nb; ++k) {
       const int j0 = (int)((long long)G.ny * k / nb), j1 = (int)((long long)G.ny * (k + 1) / nb);
       if (j1 <= j0) continue;
@@ -354,8 +371,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   for (int b = 0; b < B; ++b)
     if (m->gals[p->row_g[b]].psf_kind != psf2d)
       return fail(BANG_E_UNSUPPORTED, "a batch mixes Gaussian and Moffat PSF galaxies");
-  auto tg = m->tuned_G.find(key);
-  p->G = tg != m->tuned_G.end() ? tg->second : 4;
+  p->G = tune.G;
   // shared memory: the NA bound uses the smallest os among rows with the largest L, so
   // take it per galaxy
   size_t smem = 0;
@@ -432,6 +448,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   BANG_CUDA(copy_vec(p->d_row_g, p->row_g));
   BANG_CUDA(copy_vec(p->d_out_off, p->out_off));
   BANG_CUDA(p->d_partial.reserve(sizeof(double) * std::max(1, p->n_items)));
+  BANG_CUDA(p->d_queue.reserve(2 * sizeof(int)));
   m->plans.push_front(std::move(p));
   while (m->plans.size() > 8) m->plans.pop_back();
   *out = m->plans.front().get();
@@ -454,7 +471,10 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.maps = mode == bang::kModeMaps ? out : nullptr;
   a.seed = mode == bang::kModeSeed ? out : nullptr;
   a.out_off = p->d_out_off.as<int64_t>();
-  cudaError_t e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
+  a.queue = p->d_queue.as<int>();
+  cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
   if (e != cudaSuccess || !logL) return e;
   return bang::launch_finalize(a.partial, p->d_row_first.as<int>(), p->d_row_g.as<int>(), a.gals, p->B, logL, st);
 }
@@ -476,6 +496,9 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   a.seed = seed;
   a.out_off = p->d_out_off.as<int64_t>();
   a.grad_acc = grad_acc;
+  a.queue = p->d_queue.as<int>() + 1;
+  e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
   if (e != cudaSuccess) return e;
   return bang::launch_grad_out(grad_acc, p->B * m->P, grad, st);
@@ -780,9 +803,74 @@ bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t*
   return BANG_OK;
 }
 
+// Autotuner: times the forward launch for every (fine rows per block step G, spaxel-row
+// bands per row) candidate on this batch shape and keeps the fastest for later calls.
 bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
-  (void)gal_idx; (void)B;
+  g_last_error.clear();
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
+  if (B < 1) return fail(BANG_E_INVALID_ARG, "B < 1");
+  std::lock_guard<std::mutex> lock(m->mu);
+  BANG_CUDA(cudaSetDevice(m->device));
+  int ny_max = 1;
+  for (int b = 0; b < B; ++b) {
+    const int g = gal_idx ? gal_idx[b] : 0;
+    if (g < 0 || g >= (int)m->gals.size()) return fail(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
+    ny_max = std::max(ny_max, m->gals[g].ny);
+  }
+  // in-domain parameter vectors of typical size (the cost does not depend on the values)
+  static const float kTypical[19] = {0.02f, -0.03f, 0.5f, 0.9f, 10.0f, 0.0f, 1.0f, 10.5f, 0.5f, 0.5f,
+                                     4.0f, 2.5f, 12.5f, 10.0f, 0.0f, 10.2f, 0.6f, 0.6f, 2.5f};
+  std::vector<float> th((size_t)B * m->P);
+  for (int b = 0; b < B; ++b)
+    for (int k = 0; k < m->P; ++k) th[(size_t)b * m->P + k] = kTypical[k] + (k == 2 ? 0.001f * (b % 97) : 0.f);
+  BANG_CUDA(m->stage_theta.reserve(th.size() * sizeof(float)));
+  BANG_CUDA(cudaMemcpy(m->stage_theta.p, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice));
+  BANG_CUDA(m->stage_out.reserve(sizeof(double) * B));
+  const uint64_t skey = shape_key(gal_idx, B);
+  std::vector<int> bands = {0};
+  if (B < 4 * m->num_sms)
+    for (int nb : {1, 2, 4, 8, 16})
+      if (nb <= ny_max) bands.push_back(nb);
+  cudaStream_t st = m->capture_stream;
+  cudaEvent_t e0, e1;
+  BANG_CUDA(cudaEventCreate(&e0));
+  BANG_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  bang_model::Tuning best_t;
+  bool any = false;
+  for (int G : {1, 2, 4, 8}) {
+    for (int nb : bands) {
+      m->tuned[skey] = bang_model::Tuning{G, nb};
+      m->plans.clear();
+      Plan* p = nullptr;
+      if (get_plan(m, gal_idx, B, bang::kModeLogL, &p) != BANG_OK) continue;
+      if (p->G != G) continue;   // shared memory forced a smaller step
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        BANG_CUDA(cudaEventRecord(e0, st));
+        BANG_CUDA(enqueue_forward(m, p, m->stage_theta.as<float>(), bang::kModeLogL, m->stage_out.as<double>(), nullptr,
+                                  st));
+        BANG_CUDA(cudaEventRecord(e1, st));
+        BANG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BANG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) t_min = std::min(t_min, ms);
+      }
+      if (t_min < best) {
+        best = t_min;
+        best_t = bang_model::Tuning{G, nb};
+        any = true;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->plans.clear();
+  if (!any) {
+    m->tuned.erase(skey);
+    return fail(BANG_E_UNSUPPORTED, "no launch configuration fits this batch");
+  }
+  m->tuned[skey] = best_t;
   return BANG_OK;
 }
 

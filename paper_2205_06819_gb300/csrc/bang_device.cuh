@@ -235,10 +235,10 @@ __device__ __forceinline__ void bulge_projected(const ModelConst& m, float R, fl
   const float xp1 = x + 1.0f;
   const float w = x / xp1;
   const float lw = log2f(w);
-  const float i2 = 1.0f / (xp1 * xp1);
+  const float i2 = __frcp_rn(xp1 * xp1);
   const float ip4 = i2 * i2;
-  const float pS = exp2f(m.ngam * lw) * ip4;
-  const float pQ = exp2f(m.g3 * lw) * ip4;
+  const float pS = ex2_approx(m.ngam * lw) * ip4;
+  const float pQ = ex2_approx(m.g3 * lw) * ip4;
   float S = 0.f, Q = 0.f;
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
@@ -264,7 +264,7 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
   const float r2 = fmaf(xr, xr, yd * yd);
   const float R = sqrtf(fmaxf(R2, kR2Floor));
   const float r = sqrtf(fmaxf(r2, kR2Floor));
-  const float inv_r = 1.0f / r;
+  const float inv_r = __frcp_rn(r);
   const float cphi = xr * inv_r;
 
   float Sb, SbS2;
@@ -273,7 +273,7 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
   // circular velocities in the disc plane (Eq. 10)
   const float xa = r * m.inv_a;
   const float ub = xa / (xa + 1.0f);
-  float vint2 = m.vb_c * exp2f(m.three_mg * log2f(ub)) / xa;
+  float vint2 = __fdividef(m.vb_c * ex2_approx(m.three_mg * log2f(ub)), xa);
   vint2 += m.vh_c * nfw_m(r * m.inv_rs) * inv_r;
   float Sd[ND];
 #pragma unroll
@@ -294,8 +294,8 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
     Bs2 = fmaf(Bd, m.omk[j] * vint2, Bs2);
     Stot += Sd[j];
   }
-  const float iB = 1.0f / B;
-  return make_float4(B, Bv * iB, sqrtf(Bs2 * iB), B * 1e6f / Stot);
+  const float iB = __frcp_rn(B);
+  return make_float4(B, Bv * iB, sqrtf(Bs2 * iB), __fdividef(B * 1e6f, Stot));
 }
 
 }  // namespace bang

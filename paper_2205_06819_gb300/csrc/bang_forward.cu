@@ -28,6 +28,21 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Next work item: from the shared counter when the launch has one (dynamic scheduling),
+// otherwise the fixed grid stride.  Always a block-wide barrier, so that thread 0 may
+// overwrite the shared item state afterwards.
+#define BANG_NEXT_ITEM(it)                                                     \
+  do {                                                                         \
+    if (a.queue) {                                                             \
+      if (threadIdx.x == 0) next_item = atomicAdd(a.queue, 1) + (int)gridDim.x; \
+      __syncthreads();                                                         \
+      it = next_item;                                                          \
+    } else {                                                                   \
+      __syncthreads();                                                         \
+      it += (int)gridDim.x;                                                    \
+    }                                                                          \
+  } while (0)
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -59,14 +74,19 @@ __device__ __forceinline__ float finish_spaxel(const GalDev& g, const ModelConst
 }
 
 template <int NQ, int ND, int PSF, int MODE>
-__global__ void __launch_bounds__(kThreads) forward_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ModelConst mc;
   __shared__ GalDev gs;
   __shared__ double red[kThreads / 32];
 
   const int tid = threadIdx.x;
-  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+  __shared__ int next_item;
+  __shared__ int chunk_ctr[2];
+  const int lane = threadIdx.x & 31;
+  // first item by block index, then either the next one from the shared counter (dynamic
+  // scheduling, longest items first) or a fixed stride
+  for (int it = blockIdx.x; it < a.n_items;) {
     const int item_id = a.order ? a.order[it] : it;
     const WorkItem w = a.items[item_id];
     if (tid == 0) {
@@ -98,40 +118,63 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(FwdArgs a) {
         }
       }
       if (tid == 0) a.partial[item_id] = __longlong_as_double(0x7ff8000000000000ll);
-      __syncthreads();
+      BANG_NEXT_ITEM(it);
       continue;
     }
 
     for (int t = tid; t < ntaps; t += kThreads) taps[t] = __ldg(gs.taps + t);
     for (int t = tid; t < NA * nx; t += kThreads) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < 2) chunk_ctr[tid] = 0;
     __syncthreads();
 
     double chi_thread = 0.0;
     const int y_begin = w.j0 * os;
     const int y_end = (w.j1 - 1) * os + L;                   // exclusive
+    const int nchunks = (y_end - y_begin + a.G - 1) / a.G;
     const float pk = gs.pitch_kpa;
-    for (int y0 = y_begin; y0 < y_end; y0 += a.G) {
-      const int G = min(a.G, y_end - y0);
-      // 1. evaluate the chunk of G fine rows
-      const int npts = G * W;
-      for (int p = tid; p < npts; p += kThreads) {
-        const int gr = p / W;
-        const int qx = p - gr * W;
-        const float X = fmaf((float)qx, pk, mc.X0);
-        const float Y = fmaf((float)(y0 + gr), pk, mc.Y0);
-        stage[p] = eval_point<NQ, ND>(mc, X, Y);
+    const float inv_W = 1.0f / (float)W;
+
+    // Evaluation of chunk c (a.G fine rows) into stage buffer c & 1.  Warps take 32 points
+    // at a time from the chunk's shared counter, so warps that are busy with the stencil
+    // of the previous chunk simply take fewer points.
+    auto eval_chunk = [&](int c) {
+      const int y0 = y_begin + c * a.G;
+      const int npts = min(a.G, y_end - y0) * W;
+      float4* st = stage + (size_t)(c & 1) * a.G * W;
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&chunk_ctr[c & 1], 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= npts) break;
+        const int p = base + lane;
+        if (p < npts) {
+          const int gr = __float2int_rz(((float)p + 0.5f) * inv_W);   // p + 1/2 is never a multiple of W
+          const int qx = p - gr * W;
+          const float X = fmaf((float)qx, pk, mc.X0);
+          const float Y = fmaf((float)(y0 + gr), pk, mc.Y0);
+          st[p] = eval_point<NQ, ND>(mc, X, Y);
+        }
       }
-      __syncthreads();
-      // 2 + 3. filter into open spaxel rows; finish the rows that complete
+    };
+
+    eval_chunk(0);
+    __syncthreads();
+    for (int c = 0; c < nchunks; ++c) {
+      // stage c & 1 holds chunk c; its counter is free again (next used by chunk c + 2)
+      if (tid == 0) chunk_ctr[c & 1] = 0;
+      const int y0 = y_begin + c * a.G;
+      const int G = min(a.G, y_end - y0);
+      const float4* stage_c = stage + (size_t)(c & 1) * a.G * W;
+      // filter chunk c into the open spaxel rows; finish the rows that complete
       if (PSF == 0) {
         for (int i = tid; i < nx; i += kThreads) {
           for (int gr = 0; gr < G; ++gr) {
             const int y = y0 + gr;
-            const float4* srow = stage + gr * W + i * os;
+            const float4* srow = stage_c + gr * W + i * os;
             float4 hs = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int c = 0; c < L; ++c) {
-              const float tw = taps[c];
-              const float4 v = srow[c];
+            for (int k = 0; k < L; ++k) {
+              const float tw = taps[k];
+              const float4 v = srow[k];
               hs.x = fmaf(tw, v.x, hs.x); hs.y = fmaf(tw, v.y, hs.y);
               hs.z = fmaf(tw, v.z, hs.z); hs.w = fmaf(tw, v.w, hs.w);
             }
@@ -170,10 +213,10 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(FwdArgs a) {
           const int gb = min(G - 1, j * os + L - 1 - y0);
           for (int gr = ga; gr <= gb; ++gr) {
             const float* wrow = taps + (y0 + gr - j * os) * L;
-            const float4* srow = stage + gr * W + i * os;
-            for (int c = 0; c < L; ++c) {
-              const float tw = wrow[c];
-              const float4 v = srow[c];
+            const float4* srow = stage_c + gr * W + i * os;
+            for (int k = 0; k < L; ++k) {
+              const float tw = wrow[k];
+              const float4 v = srow[k];
               A.x = fmaf(tw, v.x, A.x); A.y = fmaf(tw, v.y, A.y);
               A.z = fmaf(tw, v.z, A.z); A.w = fmaf(tw, v.w, A.w);
             }
@@ -185,6 +228,8 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(FwdArgs a) {
           acc[(j % NA) * nx + i] = A;
         }
       }
+      // meanwhile (and after its share of the stencil) every warp evaluates chunk c + 1
+      if (c + 1 < nchunks) eval_chunk(c + 1);
       __syncthreads();
     }
 
@@ -197,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) forward_kernel(FwdArgs a) {
       for (int k = 0; k < kThreads / 32; ++k) s += red[k];
       a.partial[item_id] = s;
     }
-    __syncthreads();
+    BANG_NEXT_ITEM(it);
   }
 }
 
@@ -244,7 +289,7 @@ int forward_threads() { return kThreads; }
 size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d) {
   const int ntaps = psf2d ? L * L : L;
   const int NA = (L + os - 1) / os;
-  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)NA * nx * 16 + (size_t)G * W * 16;
+  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)NA * nx * 16 + 2 * (size_t)G * W * 16;
 }
 
 const void* forward_kernel_ptr(int n_quad, int n_discs, int psf2d, int mode) {

@@ -22,6 +22,7 @@ struct FwdArgs {
   const WorkItem* items;    // [n_items], items of one row contiguous, rows in order
   const int* order;         // execution order of items (NULL = table order)
   int n_items;
+  int* queue;               // dynamic item counter, zeroed before the launch (NULL = static striding)
   int G;                    // fine rows per block step
   double* partial;          // [n_items] chi^2 of each item (NaN for an out-of-domain row)
   float* maps;              // kModeMaps: model maps, row b at out_off[b]
@@ -37,6 +38,7 @@ struct AdjArgs {
   const WorkItem* items;    // fine-row bands (j0/j1 hold fine padded rows [y0, y1))
   const int* order;
   int n_items;
+  int* queue;               // dynamic item counter, zeroed before the launch (NULL = static striding)
   int G;                    // fine rows per block step
   const float* seed;        // d logL / dF at the spaxels, row b at out_off[b]
   const int64_t* out_off;

@@ -177,3 +177,15 @@ def test_full_size_workload_sampled_rows(lib, name):
     ref, ref_chi2 = ds.oracle_loglike(theta[pick])
     chi = chi2_of(ds, got[pick])
     assert (np.abs(chi - ref_chi2) / ref_chi2).max() < CHI2_RTOL
+
+
+def test_autotuner_keeps_results(lib):
+    ds = Dataset(synth.GalaxySpec(16, 12, 3, 2.0), TH1, seed=19)
+    theta = torch.from_numpy(theta_batch(1, TH1, 5, seed=20)).cuda()
+    m = lib(ds.model_galaxy())
+    before = m.loglike(theta).cpu().numpy()
+    m.tune(5)
+    after = m.loglike(theta).cpu().numpy()
+    np.testing.assert_allclose(after, before, rtol=1e-12)
+    l2, g2 = m.loglike_grad(theta)
+    np.testing.assert_allclose(l2.cpu().numpy(), before, rtol=1e-12)
