@@ -279,7 +279,7 @@ __device__ void constants_to_theta(const float* __restrict__ th, int nd, const d
 }
 
 template <int NQ, int ND, int PSF>
-__global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
+__global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
   constexpr int NACC = A_D0 + kPerDisc * ND;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ModelConst mc;
@@ -288,13 +288,14 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int next_item;
+  __shared__ int pt_ctr;
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
   for (int it = blockIdx.x; it < a.n_items;) {
     const WorkItem w = a.items[a.order ? a.order[it] : it];
     if (tid == 0) {
       gs = a.gals[w.g];
-      mc.valid = decode_model(a.theta + (size_t)w.b * a.P, ND, gs, mc);
+      mc = a.consts[w.b];
     }
     __syncthreads();
     if (!mc.valid) {
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
       const int jhi = min(ny - 1, (y0 + G - 1) / os);
       const int nj = jhi - jlo + 1;
       __syncthreads();   // taps loaded / previous chunk's lam and V no longer read
+      if (tid == 0) pt_ctr = 0;
       for (int t = tid; t < nj * nx; t += kAdjThreads) {
         const int s = (jlo + t / nx) * nx + (t % nx);
         lam[t] = make_float4(__ldg(seed + s), __ldg(seed + n + s), __ldg(seed + 2 * n + s), __ldg(seed + 3 * n + s));
@@ -347,8 +349,18 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
         }
         __syncthreads();
       }
-      for (int p = tid; p < G * W; p += kAdjThreads) {
-        const int gr = p / W, qx = p - gr * W;
+      // point VJPs, 32 points per grab from the shared counter (balances the warps)
+      const int npts = G * W;
+      const float inv_W = 1.0f / (float)W;
+      for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&pt_ctr, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= npts) break;
+        const int p = base + lane;
+        if (p >= npts) continue;
+        const int gr = __float2int_rz(((float)p + 0.5f) * inv_W);   // p + 1/2 is never a multiple of W
+        const int qx = p - gr * W;
         const int y = y0 + gr;
         int i0 = qx - L + 1 <= 0 ? 0 : (qx - L + os) / os;
         const int i1 = min(nx - 1, qx / os);
@@ -389,27 +401,30 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
       if (lane == 0) red[warp][NACC] = v;
     }
     __syncthreads();
-    if (tid == 0) {
-      double s[NACC + 1];
-      for (int k = 0; k <= NACC; ++k) {
-        s[k] = 0.0;
-        for (int q = 0; q < kAdjThreads / 32; ++q) s[k] += red[q][k];
-      }
-      double g[kMaxParams];
-      for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
-      constants_to_theta(a.theta + (size_t)w.b * a.P, ND, s, g);
-      g[14] = s[NACC];
-      double* dst = a.grad_acc + (size_t)w.b * a.P;
-      for (int p = 0; p < a.P; ++p)
-        if (g[p] != 0.0) atomicAdd(dst + p, g[p]);
+    if (tid <= NACC) {   // one thread per accumulator: sum over warps, add to the row's slot
+      double sum = 0.0;
+      for (int q = 0; q < kAdjThreads / 32; ++q) sum += red[q][tid];
+      if (sum != 0.0) atomicAdd(a.grad_acc + (size_t)w.b * kGradAccStride + (tid < NACC ? tid : 24), sum);
     }
     BANG_NEXT_ITEM(it);
   }
 }
 
-__global__ void grad_out_kernel(const double* __restrict__ acc, int n, float* __restrict__ grad) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) grad[i] = (float)acc[i];
+// One thread per row: the reduced constant adjoints -> d logL / d theta (float64), or zero
+// for a row outside the parameter domain.
+__global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, const double* __restrict__ acc,
+                                int B, float* __restrict__ grad) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float* th = theta + (size_t)b * P;
+  double g[kMaxParams];
+  for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
+  if (theta_in_domain(th, nd)) {
+    const double* s = acc + (size_t)b * kGradAccStride;
+    constants_to_theta(th, nd, s, g);
+    g[14] = s[24];
+  }
+  for (int p = 0; p < P; ++p) grad[(size_t)b * P + p] = (float)g[p];
 }
 
 template <int NQ, int ND>
@@ -444,8 +459,9 @@ cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d,
   return n_discs == 2 ? launch_nd<128, 2>(a, psf2d, grid, smem, st) : launch_nd<128, 1>(a, psf2d, grid, smem, st);
 }
 
-cudaError_t launch_grad_out(const double* acc, int n, float* grad, cudaStream_t st) {
-  grad_out_kernel<<<(n + 255) / 256, 256, 0, st>>>(acc, n, grad);
+cudaError_t launch_grad_out(const float* theta, int P, int n_discs, const double* acc, int B, float* grad,
+                            cudaStream_t st) {
+  grad_out_kernel<<<(B + 63) / 64, 64, 0, st>>>(theta, P, n_discs, acc, B, grad);
   return cudaGetLastError();
 }
 

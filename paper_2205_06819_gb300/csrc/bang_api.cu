@@ -195,7 +195,7 @@ struct Plan {
   std::vector<int> order, row_first, row_g;
   std::vector<int64_t> out_off;
   int64_t out_total = 0;
-  DevBuf d_items, d_order, d_row_first, d_row_g, d_out_off, d_partial, d_queue;
+  DevBuf d_items, d_order, d_row_first, d_row_g, d_out_off, d_partial, d_queue, d_consts;
   int bands = 1;
   // adjoint sweep (kModeSeed plans only): bands of fine rows
   int adj_items = 0, adj_G = 4, adj_grid = 0;
@@ -406,9 +406,10 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     // adjoint work items: bands of fine rows, sized for ~16 items per SM
     long long total_rows = 0;
     for (int b = 0; b < B; ++b) total_rows += m->gals[p->row_g[b]].H;
+    // one staging step per band: rows per band = rows per block step (at most 16)
     const long long target = 16LL * m->num_sms;
-    int rows = (int)std::min<long long>(64, std::max<long long>(p->adj_G, (total_rows + target - 1) / target));
-    rows = (rows + p->adj_G - 1) / p->adj_G * p->adj_G;
+    const int rows = (int)std::max<long long>(1, std::min<long long>(16, (total_rows + target - 1) / target));
+    p->adj_G = rows;
     std::vector<bang::WorkItem> ai;
     std::vector<double> acost;
     for (int b = 0; b < B; ++b) {
@@ -449,6 +450,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   BANG_CUDA(copy_vec(p->d_out_off, p->out_off));
   BANG_CUDA(p->d_partial.reserve(sizeof(double) * std::max(1, p->n_items)));
   BANG_CUDA(p->d_queue.reserve(2 * sizeof(int)));
+  BANG_CUDA(p->d_consts.reserve(bang::model_const_bytes() * (size_t)B));
   m->plans.push_front(std::move(p));
   while (m->plans.size() > 8) m->plans.pop_back();
   *out = m->plans.front().get();
@@ -472,7 +474,11 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.seed = mode == bang::kModeSeed ? out : nullptr;
   a.out_off = p->d_out_off.as<int64_t>();
   a.queue = p->d_queue.as<int>();
-  cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
+  a.consts = p->d_consts.as<bang::ModelConst>();
+  cudaError_t e = bang::launch_decode(theta, m->P, m->opts.n_discs, a.gals, p->d_row_g.as<int>(), p->B,
+                                      p->d_consts.as<bang::ModelConst>(), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
   if (e != cudaSuccess || !logL) return e;
@@ -481,7 +487,7 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
 
 cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* logL, float* seed, double* grad_acc,
                          float* grad, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->B * m->P, st);
+  cudaError_t e = cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->B * bang::kGradAccStride, st);
   if (e != cudaSuccess) return e;
   e = enqueue_forward(m, p, theta, bang::kModeSeed, logL, seed, st);
   if (e != cudaSuccess) return e;
@@ -489,6 +495,7 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   a.theta = theta;
   a.P = m->P;
   a.gals = m->d_gals.as<bang::GalDev>();
+  a.consts = p->d_consts.as<bang::ModelConst>();
   a.items = p->d_adj_items.as<bang::WorkItem>();
   a.order = p->d_adj_order.as<int>();
   a.n_items = p->adj_items;
@@ -501,7 +508,7 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   if (e != cudaSuccess) return e;
   e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
   if (e != cudaSuccess) return e;
-  return bang::launch_grad_out(grad_acc, p->B * m->P, grad, st);
+  return bang::launch_grad_out(theta, m->P, m->opts.n_discs, grad_acc, p->B, grad, st);
 }
 
 }  // namespace
@@ -756,7 +763,7 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
     if (!g_dev) d_grad = reinterpret_cast<float*>(m->stage_out.as<char>() + sizeof(double) * B);
   }
   BANG_CUDA(m->scratch_seed.reserve(sizeof(float) * (size_t)std::max<int64_t>(p->out_total, 4)));
-  BANG_CUDA(m->scratch_grad.reserve(sizeof(double) * (size_t)B * m->P));
+  BANG_CUDA(m->scratch_grad.reserve(sizeof(double) * (size_t)B * bang::kGradAccStride));
   BANG_CUDA(enqueue_grad(m, p, d_theta, d_logL, m->scratch_seed.as<float>(), m->scratch_grad.as<double>(), d_grad, st));
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   if (!g_dev) BANG_CUDA(cudaMemcpyAsync(grad, d_grad, th_bytes, cudaMemcpyDeviceToHost, st));

@@ -84,19 +84,25 @@ __device__ __forceinline__ float lg2_approx(float x) {
 // Decode row theta (float32) into per-model constants.  Returns 0 when the row is outside
 // the parameter domain (non-finite, i not in [0, pi/2), gamma not in [0, 3), |k| > 1,
 // c <= 0, M/L <= 0).
+__device__ inline bool theta_in_domain(const float* __restrict__ th, int nd) {
+  const int np = nd == 2 ? 19 : 15;
+  for (int i = 0; i < np; ++i)
+    if (!isfinite((double)th[i])) return false;
+  const double inc = th[3], gam = th[6];
+  if (!(inc >= 0.0 && inc < 0.5 * kPi)) return false;
+  if (!(gam >= 0.0 && gam < 3.0)) return false;
+  if (!(fabs((double)th[9]) <= 1.0)) return false;
+  if (!(th[10] > 0.f && th[11] > 0.f)) return false;
+  if (!(th[13] > 0.f)) return false;
+  if (nd == 2 && !(fabs((double)th[17]) <= 1.0 && th[18] > 0.f)) return false;
+  return true;
+}
+
 __device__ inline int decode_model(const float* __restrict__ th, int nd, const GalDev& g, ModelConst& m) {
   const int np = nd == 2 ? 19 : 15;
+  if (!theta_in_domain(th, nd)) return 0;
   double t[kMaxParams];
-  for (int i = 0; i < np; ++i) {
-    t[i] = (double)th[i];
-    if (!isfinite(t[i])) return 0;
-  }
-  if (!(t[3] >= 0.0 && t[3] < 0.5 * kPi)) return 0;
-  if (!(t[6] >= 0.0 && t[6] < 3.0)) return 0;
-  if (!(fabs(t[9]) <= 1.0)) return 0;
-  if (!(t[10] > 0.0 && t[11] > 0.0)) return 0;
-  if (!(t[13] > 0.0)) return 0;
-  if (nd == 2 && !(fabs(t[17]) <= 1.0 && t[18] > 0.0)) return 0;
+  for (int i = 0; i < np; ++i) t[i] = (double)th[i];
 
   const double ci = cos(t[3]), si = sin(t[3]);
   m.X0 = (float)(g.xoff_kpa - t[0]);

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     const WorkItem w = a.items[item_id];
     if (tid == 0) {
       gs = a.gals[w.g];
-      mc.valid = decode_model(a.theta + (size_t)w.b * a.P, ND, gs, mc);
+      if (a.consts) mc = a.consts[w.b];
+      else mc.valid = decode_model(a.theta + (size_t)w.b * a.P, ND, gs, mc);
     }
     __syncthreads();
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx;
@@ -246,6 +247,16 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
   }
 }
 
+// One thread per row: theta -> per-model constants (float64 decode), against the row's galaxy.
+__global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, const GalDev* __restrict__ gals,
+                              const int* __restrict__ row_g, int B, ModelConst* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  ModelConst m;
+  m.valid = decode_model(theta + (size_t)b * P, nd, gals[row_g[b]], m);
+  out[b] = m;
+}
+
 // logL[b] = -chi^2/2 - const from the per-item partial sums (items of row b are contiguous).
 __global__ void finalize_kernel(const double* __restrict__ partial, const int* __restrict__ row_first,
                                 const int* __restrict__ row_g, const GalDev* __restrict__ gals, int B,
@@ -313,6 +324,14 @@ cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d,
   }
   return n_discs == 2 ? launch_psf<128, 2>(a, psf2d, mode, grid, smem, st)
                       : launch_psf<128, 1>(a, psf2d, mode, grid, smem, st);
+}
+
+size_t model_const_bytes() { return sizeof(ModelConst); }
+
+cudaError_t launch_decode(const float* theta, int P, int n_discs, const GalDev* gals, const int* row_g, int B,
+                          ModelConst* out, cudaStream_t st) {
+  decode_kernel<<<(B + 63) / 64, 64, 0, st>>>(theta, P, n_discs, gals, row_g, B, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,

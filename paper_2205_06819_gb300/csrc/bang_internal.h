@@ -11,6 +11,11 @@ namespace bang {
 
 struct GalDev;
 struct WorkItem;
+struct ModelConst;
+
+// Gradient accumulator row: adjoints of the per-model constants (slots 0..23, the second
+// disc's unused for one-disc models) and d logL / d v_sys (slot 24).
+constexpr int kGradAccStride = 25;
 
 enum { kModeLogL = 0, kModeMaps = 1, kModeSeed = 2 };
 
@@ -19,6 +24,7 @@ struct FwdArgs {
   const float* theta;       // [B][P]
   int P;
   const GalDev* gals;
+  const ModelConst* consts; // [B] decoded rows (NULL: each block decodes its row itself)
   const WorkItem* items;    // [n_items], items of one row contiguous, rows in order
   const int* order;         // execution order of items (NULL = table order)
   int n_items;
@@ -35,6 +41,7 @@ struct AdjArgs {
   const float* theta;
   int P;
   const GalDev* gals;
+  const ModelConst* consts; // [B] decoded rows
   const WorkItem* items;    // fine-row bands (j0/j1 hold fine padded rows [y0, y1))
   const int* order;
   int n_items;
@@ -42,7 +49,7 @@ struct AdjArgs {
   int G;                    // fine rows per block step
   const float* seed;        // d logL / dF at the spaxels, row b at out_off[b]
   const int64_t* out_off;
-  double* grad_acc;         // [B][P] float64 accumulators (zeroed before the launch)
+  double* grad_acc;         // [B][kGradAccStride] float64 constant adjoints (zeroed before the launch)
 };
 
 // Read-only view of a model's immutable device state (for entry points defined outside
@@ -70,7 +77,11 @@ size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d);
 const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d);
 cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
                            cudaStream_t st);
-cudaError_t launch_grad_out(const double* acc, int n, float* grad, cudaStream_t st);
+cudaError_t launch_grad_out(const float* theta, int P, int n_discs, const double* acc, int B, float* grad,
+                            cudaStream_t st);
+size_t model_const_bytes();
+cudaError_t launch_decode(const float* theta, int P, int n_discs, const GalDev* gals, const int* row_g, int B,
+                          ModelConst* out, cudaStream_t st);
 cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq);
 
 size_t plain_scratch_bytes(int N, int n);
