@@ -159,7 +159,7 @@ def sfu_peak_ops_per_s(n_quad: int, mhz: float, sms: int) -> float:
 
 
 # ----------------------------------------------------------------------------- data
-def make_model(wl: synth.Workload, rank: int, torch):
+def make_model(wl: synth.Workload, rank: int, torch, bulge_table: int = 0):
     """Seeded synthetic galaxies: noise-free maps from the library at each galaxy's
     theta_true plus noise; the batch is rows_per_galaxy rows per galaxy."""
     from paper_2205_06819_gb300.model import Galaxy, Model
@@ -178,7 +178,7 @@ def make_model(wl: synth.Workload, rank: int, torch):
         data, err, mask = synth.noisy_data(true[g].cpu().numpy().astype(np.float64), seed=synth.dataset_seed(wid, g))
         gals.append(Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, data, err, mask,
                            psf_kind=s.psf_kind, moffat_beta=s.moffat_beta))
-    model = Model(gals, n_discs=wl.n_discs, n_quad=wl.n_quad)
+    model = Model(gals, n_discs=wl.n_discs, n_quad=wl.n_quad, bulge_table=bulge_table)
     seed = rank_batch_seed(wid, rank)
     theta = np.concatenate([synth.draw_theta_batch(box, tts[g], wl.rows_per_galaxy, seed + 7 * g)
                             for g in range(len(gals))]).astype(np.float32)

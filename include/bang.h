@@ -81,6 +81,13 @@ typedef struct {
   int halo_kind;   /* 0: NFW (M200, c); 1: Hernquist (paper's halo) -> BANG_E_UNSUPPORTED */
   int n_quad;      /* radial quadrature nodes: 64 or 128 */
   int psf_mode;    /* 0: convolve B, v, sigma and <L/M> each on its own (Sec. 3.1) */
+  int bulge_table; /* 0: the radial quadrature at every fine point (default).  N in [256, 4096]:
+                      per parameter vector, the same n_quad-node quadrature at N radii spaced
+                      uniformly in log R between the 1e-6 kpc floor and the farthest fine point,
+                      then 4-point Lagrange interpolation in log R of each fine point's bulge
+                      density and dispersion (of values and log-ratios, so float32 keeps ~1e-7);
+                      the interpolation error is ~1e-9 relative at N = 1024.  Not available to
+                      bang_loglike_batch_noalloc and bang_loglike_plain (BANG_E_UNSUPPORTED). */
 } bang_model_opts;
 
 /* Creates a model for n_gal galaxies on CUDA device `device`: copies data, errors, masks

@@ -36,7 +36,7 @@ class GalaxyDesc(ctypes.Structure):
 
 class ModelOpts(ctypes.Structure):
     _fields_ = [("n_discs", ctypes.c_int), ("bulge_kind", ctypes.c_int), ("halo_kind", ctypes.c_int),
-                ("n_quad", ctypes.c_int), ("psf_mode", ctypes.c_int)]
+                ("n_quad", ctypes.c_int), ("psf_mode", ctypes.c_int), ("bulge_table", ctypes.c_int)]
 
 
 _VP = ctypes.c_void_p

@@ -121,9 +121,31 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
   return o;
 }
 
+// The same derivatives from the row's radial table: Sigma = M a^-2 F(R/a, g) and
+// Q = M^2 a^-3 G(R/a, g) give a dSigma/da = -(2 + s_S) Sigma and a dQ/da = -(3 + s_Q) Q,
+// with s = R dln/dR the tabulated slopes; d/dgamma from the tabulated g = dln/dgamma.
+__device__ __forceinline__ BulgeDer bulge_table_vjp(const ModelConst& m, const float* __restrict__ tab, int T,
+                                                     float R) {
+  const TabPos p = table_pos(tab, T, R * m.inv_a);
+  BulgeDer o;
+  o.Sb = table_value(tab, T, TAB_VS, p);
+  o.Qb = table_value(tab, T, TAB_VQ, p);
+  const float sS = table_plain(tab, T, TAB_SS, p), sQ = table_plain(tab, T, TAB_SQ, p);
+  const float gS = table_plain(tab, T, TAB_GS, p), gQ = table_plain(tab, T, TAB_GQ, p);
+  const float iR = __frcp_rn(R);
+  o.dSb_dR = o.Sb * sS * iR;
+  o.dQb_dR = o.Qb * sQ * iR;
+  o.dSb_da = -o.Sb * (2.0f + sS) * m.inv_a;
+  o.dQb_da = -o.Qb * (3.0f + sQ) * m.inv_a;
+  o.dSb_dg = o.Sb * gS;
+  o.dQb_dg = o.Qb * gQ;
+  return o;
+}
+
 // Vector-Jacobian product of one fine point: adds sum_c a_c d f_c / d(constants) to acc.
 template <int NQ, int ND>
-__device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y, float4 a, float* acc) {
+__device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y, float4 a, float* acc,
+                                          const float* tab, int T) {
   // ---- forward (Sec. 2.1-2.4), keeping what the reverse sweep needs
   const float xr = fmaf(X, m.cpa, Y * m.spa);
   const float yr = fmaf(Y, m.cpa, -X * m.spa);
@@ -136,7 +158,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float inv_r = 1.0f / r;
   const float cphi = xr * inv_r;
 
-  const BulgeDer bd = bulge_projected_vjp<NQ>(m, R);
+  const BulgeDer bd = tab ? bulge_table_vjp(m, tab, T, R) : bulge_projected_vjp<NQ>(m, R);
 
   const float xa = r * m.inv_a;
   const float ub = xa / (xa + 1.0f);
@@ -309,7 +331,13 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
     float4* lam = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 4 + 15) / 16) * 16);
     const int nj_max = (a.G + L - 1) / os + 2;
     float4* V = lam + (size_t)nj_max * nx;
+    float* tab = a.tables ? reinterpret_cast<float*>(V + (PSF == 0 ? (size_t)a.G * nx : 0)) : nullptr;
     for (int t = tid; t < ntaps; t += kAdjThreads) taps[t] = __ldg(gs.taps + t);
+    if (tab) {
+      const float* src = a.tables + (size_t)w.b * a.table_stride;
+      const int nt = kTabHdr + 8 * a.table_T;
+      for (int t = tid; t < nt; t += kAdjThreads) tab[t] = __ldg(src + t);
+    }
 
     float acc[NACC];
 #pragma unroll
@@ -387,7 +415,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
         }
         const float X = fmaf((float)qx, pk, mc.X0);
         const float Y = fmaf((float)y, pk, mc.Y0);
-        point_vjp<NQ, ND>(mc, X, Y, s4, acc);
+        point_vjp<NQ, ND>(mc, X, Y, s4, acc, tab, a.table_T);
       }
     }
     // float64 block reduction of the adjoints, then theta-space gradient (one thread)
@@ -427,6 +455,72 @@ __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, 
   for (int p = 0; p < P; ++p) grad[(size_t)b * P + p] = (float)g[p];
 }
 
+// Radial table of one row per block: Sigma and Q (and, for the adjoint, their slopes in
+// ln R and ln-derivatives in gamma) by the radial quadrature at T radii, t = log2(R / a)
+// uniform from the 1e-6 kpc floor to 1% beyond the farthest fine point; then the
+// log-ratios of neighbouring values.  Node positions are formed in float64 so that the
+// lookup's t0 + k h holds to float32 rounding.
+template <int NQ>
+__global__ void table_kernel(const ModelConst* __restrict__ consts, const GalDev* __restrict__ gals,
+                             const int* __restrict__ row_g, int T, int derivs, float* __restrict__ tables,
+                             int64_t stride) {
+  const int b = blockIdx.x;
+  __shared__ ModelConst m;
+  __shared__ double t0h[2];
+  if (threadIdx.x == 0) {
+    m = consts[b];
+    const GalDev g = gals[row_g[b]];
+    const double xa = m.X0, xb = m.X0 + (double)(g.W - 1) * g.pitch_kpa;
+    const double ya = m.Y0, yb = m.Y0 + (double)(g.H - 1) * g.pitch_kpa;
+    const double rmax = sqrt(fmax(xa * xa, xb * xb) + fmax(ya * ya, yb * yb));
+    const double inv_a = m.inv_a;
+    const double t_lo = log2(1e-6 * inv_a);
+    double t_hi = log2(fmax(rmax * 1.01, 2e-6) * inv_a);
+    if (t_hi < t_lo + 1.0) t_hi = t_lo + 1.0;
+    const double h = (t_hi - t_lo) / (T - 4);
+    // the float32 header the lookup uses; node positions follow from it exactly
+    t0h[0] = (double)(float)(t_lo - h);
+    t0h[1] = (double)(float)(1.0 / h);
+  }
+  __syncthreads();
+  if (!m.valid) return;
+  float* tab = tables + (size_t)b * stride;
+  if (threadIdx.x == 0) {
+    tab[0] = (float)t0h[0];
+    tab[1] = (float)t0h[1];
+    tab[2] = 0.f;
+    tab[3] = 0.f;
+  }
+  float* VS = tab + kTabHdr + TAB_VS * T;
+  float* VQ = tab + kTabHdr + TAB_VQ * T;
+  for (int k = threadIdx.x; k < T; k += blockDim.x) {
+    // the lookup maps R to u = (log2(R / a) - t0) / h; node k sits at u = k
+    const double tk = t0h[0] + (double)k / t0h[1];
+    const float R = (float)(exp2(tk) / (double)m.inv_a);
+    if (derivs) {
+      const BulgeDer d = bulge_projected_vjp<NQ>(m, R);
+      VS[k] = d.Sb;
+      VQ[k] = d.Qb;
+      tab[kTabHdr + TAB_SS * T + k] = R * d.dSb_dR / d.Sb;
+      tab[kTabHdr + TAB_SQ * T + k] = R * d.dQb_dR / d.Qb;
+      tab[kTabHdr + TAB_GS * T + k] = d.dSb_dg / d.Sb;
+      tab[kTabHdr + TAB_GQ * T + k] = d.dQb_dg / d.Qb;
+    } else {
+      float S, Q;
+      bulge_projected<NQ>(m, R, S, Q);
+      VS[k] = S;
+      VQ[k] = Q;
+    }
+  }
+  __syncthreads();
+  float* DS = tab + kTabHdr + TAB_DS * T;
+  float* DQ = tab + kTabHdr + TAB_DQ * T;
+  for (int k = threadIdx.x; k < T; k += blockDim.x) {
+    DS[k] = k + 1 < T ? log2f(VS[k + 1] / VS[k]) : 0.f;
+    DQ[k] = k + 1 < T ? log2f(VQ[k + 1] / VQ[k]) : 0.f;
+  }
+}
+
 template <int NQ, int ND>
 cudaError_t launch_nd(const AdjArgs& a, int psf2d, int grid, size_t smem, cudaStream_t st) {
   if (psf2d) adjoint_kernel<NQ, ND, 1><<<grid, kAdjThreads, smem, st>>>(a);
@@ -438,11 +532,14 @@ cudaError_t launch_nd(const AdjArgs& a, int psf2d, int grid, size_t smem, cudaSt
 
 int adjoint_threads() { return kAdjThreads; }
 
-size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d) {
+size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d, int table_T) {
   const int ntaps = psf2d ? L * L : L;
   const int nj_max = (G + L - 1) / os + 2;
-  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)nj_max * nx * 16 + (psf2d ? 0 : (size_t)G * nx * 16);
+  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)nj_max * nx * 16 + (psf2d ? 0 : (size_t)G * nx * 16) +
+         (table_T > 0 ? sizeof(float) * (size_t)(kTabHdr + 8 * table_T) : 0);
 }
+
+int64_t table_row_floats(int T, int derivs) { return kTabHdr + (int64_t)(derivs ? 8 : 4) * T; }
 
 const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d) {
 #define BANG_PICK(NQ, ND, PSF) \
@@ -457,6 +554,13 @@ cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d,
                            cudaStream_t st) {
   if (n_quad == 64) return n_discs == 2 ? launch_nd<64, 2>(a, psf2d, grid, smem, st) : launch_nd<64, 1>(a, psf2d, grid, smem, st);
   return n_discs == 2 ? launch_nd<128, 2>(a, psf2d, grid, smem, st) : launch_nd<128, 1>(a, psf2d, grid, smem, st);
+}
+
+cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int B, int n_quad, int T,
+                          int derivs, float* tables, int64_t stride, cudaStream_t st) {
+  if (n_quad == 64) table_kernel<64><<<B, 256, 0, st>>>(consts, gals, row_g, T, derivs, tables, stride);
+  else table_kernel<128><<<B, 256, 0, st>>>(consts, gals, row_g, T, derivs, tables, stride);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_grad_out(const float* theta, int P, int n_discs, const double* acc, int B, float* grad,

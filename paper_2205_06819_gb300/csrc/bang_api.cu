@@ -195,7 +195,8 @@ struct Plan {
   std::vector<int> order, row_first, row_g;
   std::vector<int64_t> out_off;
   int64_t out_total = 0;
-  DevBuf d_items, d_order, d_row_first, d_row_g, d_out_off, d_partial, d_queue, d_consts;
+  DevBuf d_items, d_order, d_row_first, d_row_g, d_out_off, d_partial, d_queue, d_consts, d_tables;
+  int64_t table_stride = 0;   // floats per row of the radial tables (bulge_table option)
   int bands = 1;
   // adjoint sweep (kModeSeed plans only): bands of fine rows
   int adj_items = 0, adj_G = 4, adj_grid = 0;
@@ -377,14 +378,14 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   size_t smem = 0;
   for (int b = 0; b < B; ++b) {
     const bang::GalDev& G = m->gals[p->row_g[b]];
-    smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, p->G, psf2d));
+    smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, p->G, psf2d, m->opts.bulge_table));
   }
   if (smem > (size_t)m->smem_optin - 4096) {
     p->G = 1;
     smem = 0;
     for (int b = 0; b < B; ++b) {
       const bang::GalDev& G = m->gals[p->row_g[b]];
-      smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, 1, psf2d));
+      smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, 1, psf2d, m->opts.bulge_table));
     }
     if (smem > (size_t)m->smem_optin - 4096) return fail(BANG_E_UNSUPPORTED, "galaxy too large for one block's shared memory");
   }
@@ -426,7 +427,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     size_t asmem = 0;
     for (int b = 0; b < B; ++b) {
       const bang::GalDev& G = m->gals[p->row_g[b]];
-      asmem = std::max(asmem, bang::adjoint_smem_bytes(G.L, G.os, G.nx, p->adj_G, psf2d));
+      asmem = std::max(asmem, bang::adjoint_smem_bytes(G.L, G.os, G.nx, p->adj_G, psf2d, m->opts.bulge_table));
     }
     p->adj_smem = asmem;
     const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d);
@@ -451,6 +452,10 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   BANG_CUDA(p->d_partial.reserve(sizeof(double) * std::max(1, p->n_items)));
   BANG_CUDA(p->d_queue.reserve(2 * sizeof(int)));
   BANG_CUDA(p->d_consts.reserve(bang::model_const_bytes() * (size_t)B));
+  if (m->opts.bulge_table > 0) {
+    p->table_stride = bang::table_row_floats(m->opts.bulge_table, mode == bang::kModeSeed);
+    BANG_CUDA(p->d_tables.reserve(sizeof(float) * (size_t)p->table_stride * B));
+  }
   m->plans.push_front(std::move(p));
   while (m->plans.size() > 8) m->plans.pop_back();
   *out = m->plans.front().get();
@@ -478,6 +483,14 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   cudaError_t e = bang::launch_decode(theta, m->P, m->opts.n_discs, a.gals, p->d_row_g.as<int>(), p->B,
                                       p->d_consts.as<bang::ModelConst>(), st);
   if (e != cudaSuccess) return e;
+  if (m->opts.bulge_table > 0) {
+    a.tables = p->d_tables.as<float>();
+    a.table_T = m->opts.bulge_table;
+    a.table_stride = p->table_stride;
+    e = bang::launch_tables(a.consts, a.gals, p->d_row_g.as<int>(), p->B, m->opts.n_quad, a.table_T,
+                            mode == bang::kModeSeed, p->d_tables.as<float>(), p->table_stride, st);
+    if (e != cudaSuccess) return e;
+  }
   e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
@@ -503,6 +516,11 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   a.seed = seed;
   a.out_off = p->d_out_off.as<int64_t>();
   a.grad_acc = grad_acc;
+  if (m->opts.bulge_table > 0) {
+    a.tables = p->d_tables.as<float>();
+    a.table_T = m->opts.bulge_table;
+    a.table_stride = p->table_stride;
+  }
   a.queue = p->d_queue.as<int>() + 1;
   e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
@@ -524,6 +542,7 @@ bool model_view(const bang_model* m, ModelView* v) {
   v->P = m->P;
   v->num_sms = m->num_sms;
   v->smem_optin = m->smem_optin;
+  v->bulge_table = m->opts.bulge_table;
   v->h_gals = m->gals.data();
   v->d_gals = m->d_gals.as<GalDev>();
   return true;
@@ -555,6 +574,8 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
   if (opts->bulge_kind != 0) return fail(BANG_E_UNSUPPORTED, "bulge_kind %d not available", opts->bulge_kind);
   if (opts->halo_kind != 0) return fail(BANG_E_UNSUPPORTED, "halo_kind %d not available (NFW = 0)", opts->halo_kind);
   if (opts->psf_mode != 0) return fail(BANG_E_UNSUPPORTED, "psf_mode %d not available", opts->psf_mode);
+  if (opts->bulge_table != 0 && (opts->bulge_table < 256 || opts->bulge_table > 4096))
+    return fail(BANG_E_INVALID_ARG, "bulge_table must be 0 or in [256, 4096]");
   for (int g = 0; g < n_gal; ++g) {
     bang_status s = validate_desc(gal[g], g);
     if (s != BANG_OK) return s;
@@ -776,6 +797,7 @@ bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t*
   g_last_error.clear();
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
   if (!theta || !logL || B < 1) return fail(BANG_E_INVALID_ARG, "theta or logL is null, or B < 1");
+  if (m->opts.bulge_table) return fail(BANG_E_UNSUPPORTED, "bang_loglike_plain: no radial-table mode (bulge_table)");
   std::lock_guard<std::mutex> lock(m->mu);
   BANG_CUDA(cudaSetDevice(m->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -240,7 +240,7 @@ __device__ __forceinline__ void bulge_projected(const ModelConst& m, float R, fl
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
   const float w = x / xp1;
-  const float lw = log2f(w);
+  const float lw = lg2_approx(w);
   const float i2 = __frcp_rn(xp1 * xp1);
   const float ip4 = i2 * i2;
   const float pS = ex2_approx(m.ngam * lw) * ip4;
@@ -259,9 +259,61 @@ __device__ __forceinline__ void bulge_projected(const ModelConst& m, float R, fl
   SigS2 = m.cQ * pQ * Q;
 }
 
+// ---------------------------------------------------------------- radial table (option)
+// Per parameter vector, the projected density Sigma and Q = Sigma sigma^2 of the bulge are
+// computed by the same radial quadrature at T radii uniformly spaced in t = log2(R / a),
+// node k at t0 + k h, covering the 1e-6 kpc floor to the farthest fine point.  A fine point
+// then interpolates with the 4-point Lagrange rule in t.  To keep float32 precision the
+// table holds the values V_k and the log-ratios D_k = log2(V_{k+1} / V_k) (|D_k| < 1): the
+// interpolant is V_i 2^d with d = -w0 D_{i-1} + (w2 + w3) D_i + w3 D_{i+1}, all small.
+// For the adjoint the table also holds the logarithmic slopes s = R dln/dR and
+// g = dln/dgamma of both quantities (O(1) values, interpolated directly).
+// Layout of one row's table (floats): [t0, 1/h, -, -][V_S][D_S][V_Q][D_Q][s_S][s_Q][g_S][g_Q].
+constexpr int kTabHdr = 4;
+enum { TAB_VS = 0, TAB_DS, TAB_VQ, TAB_DQ, TAB_SS, TAB_SQ, TAB_GS, TAB_GQ };
+
+struct TabPos {
+  int i;
+  float w0, w2, w3, wv[4];
+};
+
+__device__ __forceinline__ TabPos table_pos(const float* __restrict__ tab, int T, float x) {
+  const float t = log2f(x);
+  const float u = (t - tab[0]) * tab[1];
+  int i = (int)floorf(u);
+  i = i < 1 ? 1 : (i > T - 3 ? T - 3 : i);
+  const float f = u - (float)i;
+  TabPos p;
+  p.i = i;
+  const float fm1 = f - 1.0f, fm2 = f - 2.0f, fp1 = f + 1.0f;
+  p.w0 = -f * fm1 * fm2 * (1.0f / 6.0f);
+  p.w2 = -fp1 * f * fm2 * 0.5f;
+  p.w3 = fp1 * f * fm1 * (1.0f / 6.0f);
+  p.wv[0] = p.w0;
+  p.wv[1] = fp1 * fm1 * fm2 * 0.5f;
+  p.wv[2] = p.w2;
+  p.wv[3] = p.w3;
+  return p;
+}
+
+// value of table q (V_S or V_Q with its log-ratios in the next table) at position p
+__device__ __forceinline__ float table_value(const float* __restrict__ tab, int T, int q, const TabPos& p) {
+  const float* V = tab + kTabHdr + q * T;
+  const float* D = V + T;
+  const float d = fmaf(-p.w0, D[p.i - 1], fmaf(p.w2 + p.w3, D[p.i], p.w3 * D[p.i + 1]));
+  return V[p.i] * ex2_approx(d);
+}
+
+// plain 4-point interpolation of an O(1) table (slopes)
+__device__ __forceinline__ float table_plain(const float* __restrict__ tab, int T, int q, const TabPos& p) {
+  const float* Y = tab + kTabHdr + q * T + p.i - 1;
+  return fmaf(p.wv[0], Y[0], fmaf(p.wv[1], Y[1], fmaf(p.wv[2], Y[2], p.wv[3] * Y[3])));
+}
+
 // The four observables at one padded fine grid point: (B, v_los, sigma_los, <L/M>).
 template <int NQ, int ND>
-__device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float Y) {
+__device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float Y, const float* tab = nullptr,
+                                             int T = 0) {
   // Sec. 2.1: rotate the major axis onto x; deproject the razor-thin discs by 1 / cos i
   const float xr = fmaf(X, m.cpa, Y * m.spa);
   const float yr = fmaf(Y, m.cpa, -X * m.spa);
@@ -274,12 +326,18 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
   const float cphi = xr * inv_r;
 
   float Sb, SbS2;
-  bulge_projected<NQ>(m, R, Sb, SbS2);
+  if (tab) {
+    const TabPos tp = table_pos(tab, T, R * m.inv_a);
+    Sb = table_value(tab, T, TAB_VS, tp);
+    SbS2 = table_value(tab, T, TAB_VQ, tp);
+  } else {
+    bulge_projected<NQ>(m, R, Sb, SbS2);
+  }
 
   // circular velocities in the disc plane (Eq. 10)
   const float xa = r * m.inv_a;
   const float ub = xa / (xa + 1.0f);
-  float vint2 = __fdividef(m.vb_c * ex2_approx(m.three_mg * log2f(ub)), xa);
+  float vint2 = __fdividef(m.vb_c * ex2_approx(m.three_mg * lg2_approx(ub)), xa);
   vint2 += m.vh_c * nfw_m(r * m.inv_rs) * inv_r;
   float Sd[ND];
 #pragma unroll

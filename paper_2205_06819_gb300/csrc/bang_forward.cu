@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     const int ntaps = PSF == 0 ? L : L * L;
     float4* acc = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 4 + 15) / 16) * 16);
     float4* stage = acc + (size_t)NA * nx;
+    float* tab = a.tables ? reinterpret_cast<float*>(stage + 2 * (size_t)a.G * W) : nullptr;
     float* out = nullptr;
     if (MODE == kModeMaps) out = a.maps + a.out_off[w.b];
     if (MODE == kModeSeed) out = a.seed + a.out_off[w.b];
@@ -125,6 +126,11 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
 
     for (int t = tid; t < ntaps; t += kThreads) taps[t] = __ldg(gs.taps + t);
     for (int t = tid; t < NA * nx; t += kThreads) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tab) {   // this row's radial table: header, values and log-ratios of Sigma and Q
+      const float* src = a.tables + (size_t)w.b * a.table_stride;
+      const int nt = kTabHdr + 4 * a.table_T;
+      for (int t = tid; t < nt; t += kThreads) tab[t] = __ldg(src + t);
+    }
     if (tid < 2) chunk_ctr[tid] = 0;
     __syncthreads();
 
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           const int qx = p - gr * W;
           const float X = fmaf((float)qx, pk, mc.X0);
           const float Y = fmaf((float)(y0 + gr), pk, mc.Y0);
-          st[p] = eval_point<NQ, ND>(mc, X, Y);
+          st[p] = eval_point<NQ, ND>(mc, X, Y, tab, a.table_T);
         }
       }
     };
@@ -297,10 +303,11 @@ cudaError_t launch_psf(const FwdArgs& a, int psf2d, int mode, int grid, size_t s
 
 int forward_threads() { return kThreads; }
 
-size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d) {
+size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d, int table_T) {
   const int ntaps = psf2d ? L * L : L;
   const int NA = (L + os - 1) / os;
-  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)NA * nx * 16 + 2 * (size_t)G * W * 16;
+  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)NA * nx * 16 + 2 * (size_t)G * W * 16 +
+         (table_T > 0 ? sizeof(float) * (size_t)(kTabHdr + 4 * table_T) : 0);
 }
 
 const void* forward_kernel_ptr(int n_quad, int n_discs, int psf2d, int mode) {
@@ -399,6 +406,8 @@ extern "C" bang_status bang_loglike_batch_noalloc(bang_model* m, const float* th
   using namespace bang;
   ModelView v;
   if (!model_view(m, &v)) return set_error(BANG_E_INVALID_ARG, "null model");
+  if (v.bulge_table)
+    return set_error(BANG_E_UNSUPPORTED, "bang_loglike_batch_noalloc: no radial-table mode (bulge_table)");
   if (!theta || !logL) return set_error(BANG_E_INVALID_ARG, "theta or logL is null");
   if (B < 1 || B > kNoAllocMaxRows)
     return set_error(BANG_E_INVALID_ARG, "bang_loglike_batch_noalloc: B = %d outside [1, %d] (fixed scratch of %zu bytes)",

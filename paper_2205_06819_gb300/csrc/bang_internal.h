@@ -34,6 +34,9 @@ struct FwdArgs {
   float* maps;              // kModeMaps: model maps, row b at out_off[b]
   float* seed;              // kModeSeed: d logL / dF per spaxel, row b at out_off[b]
   const int64_t* out_off;   // [B] float offsets of each row's [4][ny][nx] block
+  const float* tables;      // radial tables, row b at b * table_stride (NULL: quadrature per point)
+  int table_T;              // radii per table
+  int64_t table_stride;     // floats per row's table
 };
 
 // Arguments of the adjoint sweep.
@@ -50,12 +53,15 @@ struct AdjArgs {
   const float* seed;        // d logL / dF at the spaxels, row b at out_off[b]
   const int64_t* out_off;
   double* grad_acc;         // [B][kGradAccStride] float64 constant adjoints (zeroed before the launch)
+  const float* tables;      // radial tables with slopes, row b at b * table_stride (NULL: quadrature)
+  int table_T;
+  int64_t table_stride;
 };
 
 // Read-only view of a model's immutable device state (for entry points defined outside
 // bang_api.cu).
 struct ModelView {
-  int device, n_gal, n_quad, n_discs, P, num_sms, smem_optin;
+  int device, n_gal, n_quad, n_discs, P, num_sms, smem_optin, bulge_table;
   const GalDev* h_gals;   // host copies (device pointers inside)
   const GalDev* d_gals;   // device array [n_gal]
 };
@@ -64,7 +70,7 @@ bool model_view(const bang_model* m, ModelView* v);
 bang_status set_error(bang_status s, const char* fmt, ...);
 
 int forward_threads();
-size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d);
+size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d, int table_T = 0);
 const void* forward_kernel_ptr(int n_quad, int n_discs, int psf2d, int mode);
 cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d, int mode, int grid, size_t smem,
                            cudaStream_t st);
@@ -73,7 +79,12 @@ cudaError_t launch_finalize(const double* partial, const int* row_first, const i
 cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float* ws, const float* wq);
 
 int adjoint_threads();
-size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d);
+size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d, int table_T = 0);
+// Radial tables of the bulge (see bang_device.cuh): floats per row, and the table kernel
+// (one block per row; slopes only when `derivs`).
+int64_t table_row_floats(int T, int derivs);
+cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int B, int n_quad, int T,
+                          int derivs, float* tables, int64_t stride, cudaStream_t st);
 const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d);
 cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
                            cudaStream_t st);
