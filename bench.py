@@ -227,6 +227,44 @@ def time_plain(model, theta, logL, B):
             "form": "one kernel per task per parameter vector, 64 threads/block, intermediates in HBM"}
 
 
+def time_table(wl, torch, T=1024, steps=20):
+    """The same workload with the radial-table option (bulge_table = T): logL and
+    logL + gradient, device-timed, with the largest chi^2 difference to the default mode."""
+    model, _, theta_np, gal_idx = make_model(wl, 0, torch, bulge_table=T)
+    exact, _, _, _ = make_model(wl, 0, torch)
+    theta = torch.from_numpy(theta_np).cuda()
+    B = theta.shape[0]
+    model.tune(B, gal_idx)
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        model.loglike(theta, gal_idx, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        model.loglike(theta, gal_idx, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    model.loglike_grad(theta, gal_idx)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        model.loglike_grad(theta, gal_idx)
+    e1.record()
+    torch.cuda.synchronize()
+    gms = e0.elapsed_time(e1) / 3
+    ref = exact.loglike(theta, gal_idx)
+    fin = torch.isfinite(ref)
+    rel = ((out[fin] - ref[fin]).abs() / ref[fin].abs()).max().item()
+    model.close()
+    exact.close()
+    return {"value": B / ms * 1e3, "unit": "logL evals/s", "ms_per_batch": ms, "table_radii": T,
+            "fwd_adjoint_evals_s": B / gms * 1e3, "max_rel_logL_vs_per_point_quadrature": rel,
+            "form": "bulge Sigma and sigma^2 from a per-row table of the same radial quadrature, "
+                    "4-point Lagrange interpolation in log R"}
+
+
 def time_adjoint(torch, steps=10):
     """logL + gradient for the 256-row adjoint workload (80x80, os 5), device-timed."""
     wl = synth.workload("adjoint")
@@ -406,6 +444,7 @@ def run_ours(args):
     if ws == 1 and not args.no_extras and len(wl.galaxies) == 1:
         line["plain_gpu"] = time_plain(model, theta, logL, B)
         line["fwd_adjoint"] = time_adjoint(torch)
+        line["radial_table"] = time_table(wl, torch)
         line["cpu_baseline"] = cpu_oracle_sample(wl, gal, theta_np, args.cpu_seconds)
     elif ws == 1:
         line["cpu_baseline"] = None

@@ -7,7 +7,7 @@ relative error of chi^2 (the theta-dependent part of logL) and of logL, per-map 
 errors (B, sigma, M/L relative; v relative to the map's largest |v|), and for the
 gradient workloads the gradient error relative to the oracle gradient's norm.
 
-    python tests/parity_report.py [--rows N] [--grad-rows N] [--out file.json]
+    python tests/parity_report.py [--rows N] [--grad-rows N] [--bulge-table T] [--out file.json]
 
 Prints one JSON object per workload.  Needs a GPU; the oracle uses all host cores.
 """
@@ -39,7 +39,7 @@ def map_errors(got, ref):
     return out
 
 
-def report(name, rows, grad_rows, torch, Model):
+def report(name, rows, grad_rows, torch, Model, bulge_table=0):
     wl = synth.workload(name)
     wid = synth.workload_id(name)
     box = synth.prior_box(wl.n_discs, wl.gamma_fixed)
@@ -51,14 +51,15 @@ def report(name, rows, grad_rows, torch, Model):
     gal_idx = np.repeat(np.arange(len(dss), dtype=np.int32), wl.rows_per_galaxy)
     theta = np.concatenate([synth.draw_theta_batch(box, d.theta_true, wl.rows_per_galaxy, synth.batch_seed(wid) + 7 * g)
                             for g, d in enumerate(dss)]).astype(np.float32)
-    m = Model([d.model_galaxy() for d in dss], n_discs=wl.n_discs, n_quad=wl.n_quad)
+    m = Model([d.model_galaxy() for d in dss], n_discs=wl.n_discs, n_quad=wl.n_quad, bulge_table=bulge_table)
     tt_ = torch.from_numpy(theta).cuda()
     gi = gal_idx if len(dss) > 1 else None
     logL = m.loglike(tt_, gi).cpu().numpy()
     rng = np.random.default_rng(wid)
     nb = theta.shape[0]
     pick = np.unique(np.concatenate([[0, nb - 1], rng.choice(nb, min(rows, nb), replace=False)]))[:max(1, min(rows, nb))]
-    res = {"workload": name, "rows_total": int(theta.shape[0]), "rows_checked": [int(b) for b in pick]}
+    res = {"workload": name, "bulge_table": bulge_table, "rows_total": int(theta.shape[0]),
+           "rows_checked": [int(b) for b in pick]}
     chi_rel, logl_rel, maps_err = [], [], {"B": 0.0, "v": 0.0, "sigma": 0.0, "ML": 0.0}
     maps = m.maps(torch.from_numpy(theta[pick]).cuda(), gal_idx[pick] if gi is not None else None)
     for k, b in enumerate(pick):
@@ -99,6 +100,7 @@ def main():
     ap.add_argument("--grad-rows", type=int, default=2)
     ap.add_argument("--workloads", default=",".join(synth.WORKLOADS))
     ap.add_argument("--out", default=None)
+    ap.add_argument("--bulge-table", type=int, default=0, help="radial-table option of the library (0: off)")
     args = ap.parse_args()
     import torch
     oracle.build()
@@ -107,7 +109,7 @@ def main():
     from paper_2205_06819_gb300.model import Model
     out = []
     for name in args.workloads.split(","):
-        r = report(name, args.rows, args.grad_rows, torch, Model)
+        r = report(name, args.rows, args.grad_rows, torch, Model, args.bulge_table)
         print(json.dumps(r), flush=True)
         out.append(r)
     if args.out:
