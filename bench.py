@@ -193,16 +193,31 @@ def cpu_oracle_sample(wl, gal, theta, seconds: float):
     og = oracle.Galaxy(gal.nx, gal.ny, gal.oversample, gal.psf_fwhm_arcsec, gal.kpc_per_arcsec,
                        psf_kind=gal.psf_kind, moffat_beta=gal.moffat_beta,
                        data=np.asarray(gal.data, np.float64), err=np.asarray(gal.err, np.float64), mask=gal.mask)
+    cores = oracle.max_threads()
     t0 = time.perf_counter()
     n = 0
-    while n < theta.shape[0]:
-        oracle.loglike(og, theta[n:n + 1].astype(np.float64), n_discs=wl.n_discs, n_quad=wl.n_quad)
+    B = theta.shape[0]
+    while n < max(B, 1 << 30):
+        oracle.loglike(og, theta[n % B:n % B + 1].astype(np.float64), n_discs=wl.n_discs, n_quad=wl.n_quad)
         n += 1
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "logL evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"first {n} of the {theta.shape[0]} rows, one oracle call per row (OpenMP over fine-grid rows), "
+    # the same oracle on one thread, a few rows (about a third of the budget)
+    t1 = time.perf_counter()
+    n1 = 0
+    while True:
+        oracle.loglike(og, theta[n1 % B:n1 % B + 1].astype(np.float64), n_discs=wl.n_discs, n_quad=wl.n_quad,
+                       nthreads=1)
+        n1 += 1
+        if time.perf_counter() - t1 > seconds / 3:
+            break
+    dt1 = time.perf_counter() - t1
+    oracle.loglike(og, theta[:1].astype(np.float64), n_discs=wl.n_discs, n_quad=wl.n_quad,
+                   nthreads=cores)   # restore the thread count
+    return {"value": n / dt, "unit": "logL evals/s", "cores": cores, "kind": "oracle",
+            "single_thread_value": n1 / dt1, "single_thread_sample": f"{n1} rows, {dt1:.1f} s",
+            "sample": f"{n} oracle calls on consecutive rows of the {B}-row batch (OpenMP over fine-grid rows), "
                       f"{dt:.1f} s"}
 
 

@@ -99,6 +99,16 @@ bang_status bang_model_create(const bang_galaxy_desc *gal, int n_gal, const bang
 /* Frees all device and host state of the model.  NULL is accepted.  Synchronises. */
 bang_status bang_model_destroy(bang_model *m);
 
+/* Caps the device memory the model may allocate while serving calls (work-item tables,
+ * staging of host arrays, gradient and table scratch), beyond the resident data copied by
+ * bang_model_create; bytes = 0 removes the cap.  A call that would go over the cap
+ * returns BANG_E_OOM before launching anything and leaves the buffers it already had.
+ * Also the host-side way to test allocation failure. */
+bang_status bang_model_set_scratch_limit(bang_model *m, int64_t bytes);
+
+/* Device bytes the model currently holds as call scratch; -1 for a NULL model. */
+int64_t bang_model_scratch_bytes(const bang_model *m);
+
 /* Parameters per row: 15 (one disc) or 19 (two discs); -1 for a NULL model. */
 int bang_model_nparams(const bang_model *m);
 

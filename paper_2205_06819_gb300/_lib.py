@@ -45,6 +45,8 @@ _SIGNATURES = {
                                          ctypes.c_int, ctypes.POINTER(_VP)]),
     "bang_model_destroy": (ctypes.c_int, [_VP]),
     "bang_model_nparams": (ctypes.c_int, [_VP]),
+    "bang_model_set_scratch_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "bang_model_scratch_bytes": (ctypes.c_int64, [_VP]),
     "bang_model_ngalaxies": (ctypes.c_int, [_VP]),
     "bang_model_psf_halfwidth": (ctypes.c_int, [_VP, ctypes.c_int]),
     "bang_loglike_batch": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),

@@ -167,19 +167,47 @@ std::vector<float> make_taps(int kind, double fwhm, double beta, int os, int h, 
   return W2;
 }
 
+// Device memory the library allocates while serving calls (plans, staging, scratch), with
+// an optional cap set by bang_model_set_scratch_limit.  Entry points that may allocate
+// install the model's budget for the calling thread (ScratchScope).
+struct ScratchBudget {
+  size_t limit = 0;   // 0: no cap
+  size_t used = 0;
+};
+thread_local ScratchBudget* tl_budget = nullptr;
+
+struct ScratchScope {
+  ScratchBudget* prev;
+  explicit ScratchScope(ScratchBudget* b) : prev(tl_budget) { tl_budget = b; }
+  ~ScratchScope() { tl_budget = prev; }
+};
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
-  ~DevBuf() {
+  ScratchBudget* charged = nullptr;
+  ~DevBuf() { release(); }
+  void release() {
     if (p) cudaFree(p);
+    if (charged) charged->used -= bytes;
+    p = nullptr;
+    bytes = 0;
+    charged = nullptr;
   }
   cudaError_t reserve(size_t b) {
     if (b <= bytes) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
+    ScratchBudget* bud = tl_budget;
+    if (bud && bud->limit && bud->used - (charged == bud ? bytes : 0) + b > bud->limit)
+      return cudaErrorMemoryAllocation;   // over the caller's cap: nothing is freed or allocated
+    release();
     cudaError_t e = cudaMalloc(&p, b);
-    if (e == cudaSuccess) bytes = b;
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = b;
+    charged = bud;
+    if (bud) bud->used += b;
     return e;
   }
   template <class T> T* as() const { return reinterpret_cast<T*>(p); }
@@ -251,6 +279,7 @@ struct bang_model {
   };
   std::map<uint64_t, Tuning> tuned;         // batch-shape key -> launch parameters
   std::mutex mu;
+  ScratchBudget budget;
   cudaStream_t capture_stream = nullptr;
   bool use_graphs = true;
 };
@@ -653,6 +682,17 @@ bang_status bang_model_destroy(bang_model* m) {
   return BANG_OK;
 }
 
+bang_status bang_model_set_scratch_limit(bang_model* m, int64_t bytes) {
+  g_last_error.clear();
+  if (!m) return fail(BANG_E_INVALID_ARG, "null model");
+  if (bytes < 0) return fail(BANG_E_INVALID_ARG, "negative scratch limit");
+  std::lock_guard<std::mutex> lock(m->mu);
+  m->budget.limit = (size_t)bytes;
+  return BANG_OK;
+}
+
+int64_t bang_model_scratch_bytes(const bang_model* m) { return m ? (int64_t)m->budget.used : -1; }
+
 int bang_model_nparams(const bang_model* m) { return m ? m->P : -1; }
 int bang_model_ngalaxies(const bang_model* m) { return m ? (int)m->gals.size() : -1; }
 int bang_model_psf_halfwidth(const bang_model* m, int g) {
@@ -685,6 +725,7 @@ bang_status run_forward(bang_model* m, const float* theta, const int32_t* gal_id
   if (mode == bang::kModeLogL && !logL) return fail(BANG_E_INVALID_ARG, "logL is null");
   if (mode == bang::kModeMaps && !maps) return fail(BANG_E_INVALID_ARG, "maps is null");
   std::lock_guard<std::mutex> lock(m->mu);
+  ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Plan* p = nullptr;
@@ -763,6 +804,7 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
   if (!theta || !logL || !grad || B < 1) return fail(BANG_E_INVALID_ARG, "theta, logL or grad is null, or B < 1");
   std::lock_guard<std::mutex> lock(m->mu);
+  ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Plan* p = nullptr;
@@ -799,6 +841,7 @@ bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t*
   if (!theta || !logL || B < 1) return fail(BANG_E_INVALID_ARG, "theta or logL is null, or B < 1");
   if (m->opts.bulge_table) return fail(BANG_E_UNSUPPORTED, "bang_loglike_plain: no radial-table mode (bulge_table)");
   std::lock_guard<std::mutex> lock(m->mu);
+  ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   size_t need = 0;
@@ -839,6 +882,7 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
   if (B < 1) return fail(BANG_E_INVALID_ARG, "B < 1");
   std::lock_guard<std::mutex> lock(m->mu);
+  ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
   int ny_max = 1;
   for (int b = 0; b < B; ++b) {
