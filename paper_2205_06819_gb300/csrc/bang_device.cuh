@@ -310,10 +310,51 @@ __device__ __forceinline__ float table_plain(const float* __restrict__ tab, int 
   return fmaf(p.wv[0], Y[0], fmaf(p.wv[1], Y[1], fmaf(p.wv[2], Y[2], p.wv[3] * Y[3])));
 }
 
+// The same sums with the per-model node factors folded into weights staged in shared
+// memory: nw[k] = (w_k cosh t_k c_k^-g, w_k tanh^2 t_k c_k^(3-2g)), so a node needs one
+// 64-bit shared load instead of two multiplications, and its exponents (g - 4) d and
+// (2g - 7) d are smaller.
+template <int NQ>
+__device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const float2* __restrict__ nw, float R,
+                                                  float& Sigma, float& SigS2) {
+  constexpr int base = NodeBase<NQ>::value;
+  const float x = R * m.inv_a;
+  const float xp1 = x + 1.0f;
+  const float w = x / xp1;
+  const float lw = lg2_approx(w);
+  const float i2 = __frcp_rn(xp1 * xp1);
+  const float ip4 = i2 * i2;
+  const float pS = ex2_approx(m.ngam * lw) * ip4;
+  const float pQ = ex2_approx(m.g3 * lw) * ip4;
+  float S = 0.f, Q = 0.f;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const float d = lg2_approx(fmaf(w, kNodeCm1[base + k], 1.0f));
+    float2 wk;   // kept in the loop: hoisting 2 NQ invariant weights would exhaust the registers
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                 : "=f"(wk.x), "=f"(wk.y)
+                 : "r"((unsigned)__cvta_generic_to_shared(nw + k)));
+    S = fmaf(wk.x, ex2_approx(m.g4 * d), S);
+    Q = fmaf(wk.y, ex2_approx(m.g7 * d), Q);
+  }
+  Sigma = m.cS * x * pS * S;
+  SigS2 = m.cQ * pQ * Q;
+}
+
+// Per-model node weights for bulge_projected_w (threads of a block fill them together).
+template <int NQ>
+__device__ __forceinline__ void fill_node_weights(const ModelConst& m, float2* nw, int tid, int nthreads) {
+  constexpr int base = NodeBase<NQ>::value;
+  for (int k = tid; k < NQ; k += nthreads) {
+    const float lc = kNodeLc[base + k];
+    nw[k] = make_float2(kNodeWs[base + k] * exp2f(m.ngam * lc), kNodeWq[base + k] * exp2f(m.g3 * lc));
+  }
+}
+
 // The four observables at one padded fine grid point: (B, v_los, sigma_los, <L/M>).
 template <int NQ, int ND>
 __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float Y, const float* tab = nullptr,
-                                             int T = 0) {
+                                             int T = 0, const float2* nodew = nullptr) {
   // Sec. 2.1: rotate the major axis onto x; deproject the razor-thin discs by 1 / cos i
   const float xr = fmaf(X, m.cpa, Y * m.spa);
   const float yr = fmaf(Y, m.cpa, -X * m.spa);
@@ -330,6 +371,8 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
     const TabPos tp = table_pos(tab, T, R * m.inv_a);
     Sb = table_value(tab, T, TAB_VS, tp);
     SbS2 = table_value(tab, T, TAB_VQ, tp);
+  } else if (nodew) {
+    bulge_projected_w<NQ>(m, nodew, R, Sb, SbS2);
   } else {
     bulge_projected<NQ>(m, R, Sb, SbS2);
   }

@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
   const int tid = threadIdx.x;
   __shared__ int next_item;
   __shared__ int chunk_ctr[2];
+  __shared__ float2 nodew[NQ];
   const int lane = threadIdx.x & 31;
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       for (int t = tid; t < nt; t += kThreads) tab[t] = __ldg(src + t);
     }
     if (tid < 2) chunk_ctr[tid] = 0;
+    if (!tab) fill_node_weights<NQ>(mc, nodew, tid, kThreads);
     __syncthreads();
 
     double chi_thread = 0.0;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           const int qx = p - gr * W;
           const float X = fmaf((float)qx, pk, mc.X0);
           const float Y = fmaf((float)(y0 + gr), pk, mc.Y0);
-          st[p] = eval_point<NQ, ND>(mc, X, Y, tab, a.table_T);
+          st[p] = eval_point<NQ, ND>(mc, X, Y, tab, a.table_T, nodew);
         }
       }
     };
