@@ -77,7 +77,7 @@ struct BulgeDer {
 };
 
 template <int NQ>
-__device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, float R) {
+__device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, float R, const float2* nw = nullptr) {
   constexpr int base = NodeBase<NQ>::value;
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
@@ -93,8 +93,18 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
     const float lc = kNodeLc[base + k];
     const float q = fmaf(w, kNodeCm1[base + k], 1.0f);
     const float d = lg2_approx(q);
-    const float t1 = kNodeWs[base + k] * ex2_approx(fmaf(m.g4, d, m.ngam * lc));
-    const float t2 = kNodeWq[base + k] * ex2_approx(fmaf(m.g7, d, m.g3 * lc));
+    float t1, t2;
+    if (nw) {   // per-model node factors folded into shared-memory weights (see bulge_projected_w)
+      float2 wk;
+      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                   : "=f"(wk.x), "=f"(wk.y)
+                   : "r"((unsigned)__cvta_generic_to_shared(nw + k)));
+      t1 = wk.x * ex2_approx(m.g4 * d);
+      t2 = wk.y * ex2_approx(m.g7 * d);
+    } else {
+      t1 = kNodeWs[base + k] * ex2_approx(fmaf(m.g4, d, m.ngam * lc));
+      t2 = kNodeWq[base + k] * ex2_approx(fmaf(m.g7, d, m.g3 * lc));
+    }
     const float lu = (lw + lc) - d;                  // log2 u_k, u_k = r_k / (r_k + a)
     const float u = ex2_approx(lu);
     S += t1;
@@ -145,7 +155,7 @@ __device__ __forceinline__ BulgeDer bulge_table_vjp(const ModelConst& m, const f
 // Vector-Jacobian product of one fine point: adds sum_c a_c d f_c / d(constants) to acc.
 template <int NQ, int ND>
 __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y, float4 a, float* acc,
-                                          const float* tab, int T) {
+                                          const float* tab, int T, const float2* nodew) {
   // ---- forward (Sec. 2.1-2.4), keeping what the reverse sweep needs
   const float xr = fmaf(X, m.cpa, Y * m.spa);
   const float yr = fmaf(Y, m.cpa, -X * m.spa);
@@ -158,7 +168,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float inv_r = 1.0f / r;
   const float cphi = xr * inv_r;
 
-  const BulgeDer bd = tab ? bulge_table_vjp(m, tab, T, R) : bulge_projected_vjp<NQ>(m, R);
+  const BulgeDer bd = tab ? bulge_table_vjp(m, tab, T, R) : bulge_projected_vjp<NQ>(m, R, nodew);
 
   const float xa = r * m.inv_a;
   const float ub = xa / (xa + 1.0f);
@@ -311,6 +321,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int next_item;
   __shared__ int pt_ctr;
+  __shared__ float2 nodew[NQ];
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
   for (int it = blockIdx.x; it < a.n_items;) {
@@ -337,6 +348,8 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
       const float* src = a.tables + (size_t)w.b * a.table_stride;
       const int nt = kTabHdr + 8 * a.table_T;
       for (int t = tid; t < nt; t += kAdjThreads) tab[t] = __ldg(src + t);
+    } else {
+      fill_node_weights<NQ>(mc, nodew, tid, kAdjThreads);
     }
 
     float acc[NACC];
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
         }
         const float X = fmaf((float)qx, pk, mc.X0);
         const float Y = fmaf((float)y, pk, mc.Y0);
-        point_vjp<NQ, ND>(mc, X, Y, s4, acc, tab, a.table_T);
+        point_vjp<NQ, ND>(mc, X, Y, s4, acc, tab, a.table_T, nodew);
       }
     }
     // float64 block reduction of the adjoints, then theta-space gradient (one thread)
