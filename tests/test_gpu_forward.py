@@ -189,3 +189,30 @@ def test_autotuner_keeps_results(lib):
     np.testing.assert_allclose(after, before, rtol=1e-12)
     l2, g2 = m.loglike_grad(theta)
     np.testing.assert_allclose(l2.cpu().numpy(), before, rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_large_grid_wide_psf(lib, kind):
+    """A large grid near the shared-memory limits: 150x110 spaxels, os 6, FWHM 3.5" (h = 26,
+    padded rows of 952 fine points, 58-tap window), Gaussian and Moffat; sampled rows."""
+    spec = synth.GalaxySpec(150, 110, 6, 3.5, psf_kind=kind)
+    ds = Dataset(spec, TH1, seed=120 + kind)
+    theta = theta_batch(1, TH1, 3, seed=122)
+    check_rows(ds, lib, theta)
+
+
+def test_large_batch_indexing(lib):
+    """20000 rows in one launch (work-item table, per-row offsets) on a small grid; rows
+    sampled across the batch against the oracle, and the batch equal to a split of it."""
+    spec = synth.GalaxySpec(9, 8, 2, 1.6)
+    ds = Dataset(spec, TH1, seed=123)
+    theta = theta_batch(1, TH1, 20000, seed=124)
+    m = lib(ds.model_galaxy())
+    t = torch.from_numpy(theta).cuda()
+    got = m.loglike(t).cpu().numpy()
+    pick = np.array([0, 7777, 12345, 19999])
+    ref, ref_chi2 = ds.oracle_loglike(theta[pick])
+    chi = chi2_of(ds, got[pick])
+    assert (np.abs(chi - ref_chi2) / ref_chi2).max() < CHI2_RTOL
+    part = m.loglike(t[12000:12100]).cpu().numpy()
+    np.testing.assert_allclose(part, got[12000:12100], rtol=1e-12)
