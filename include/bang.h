@@ -21,7 +21,8 @@
  *   0 x0, 1 y0 [kpc], 2 P.A. [rad], 3 i [rad, 0 <= i < pi/2],
  *   4 log10 Mb [Msun], 5 log10 Rb [kpc], 6 gamma [0 <= gamma < 3],
  *   7 log10 Md1, 8 log10 Rd1, 9 k1 [|k| <= 1], 10 (M/L)b, 11 (M/L)d1 [> 0],
- *   12 log10 M200, 13 c [> 0], 14 v_sys [km/s],
+ *   12 log10 M200 (NFW) or log10 M_h (Hernquist halo), 13 c [> 0] (NFW) or log10 R_h [kpc]
+ *   (Hernquist halo), 14 v_sys [km/s],
  *   15 log10 Md2, 16 log10 Rd2, 17 k2, 18 (M/L)d2   (two-disc models only).
  * A row that is not finite or lies outside those ranges gets logL = -INFINITY and a zero
  * gradient; that is not an error (samplers propose such points).
@@ -78,7 +79,8 @@ typedef struct {
 typedef struct {
   int n_discs;     /* 1 or 2 */
   int bulge_kind;  /* 0: Dehnen gamma family (the only kind) */
-  int halo_kind;   /* 0: NFW (M200, c); 1: Hernquist (paper's halo) -> BANG_E_UNSUPPORTED */
+  int halo_kind;   /* 0: NFW (M200, c); 1: Hernquist (M_h, R_h), the paper's halo (Sec. 2.2):
+                      v^2 = G M_h r / (r + R_h)^2, Eq. 2 with the halo's mass and radius */
   int n_quad;      /* radial quadrature nodes: 64 or 128 */
   int psf_mode;    /* 0: convolve B, v, sigma and <L/M> each on its own (Sec. 3.1) */
   int bulge_table; /* 0: the radial quadrature at every fine point (default).  N in [256, 4096]:

@@ -189,6 +189,15 @@ template <class T> T nfw_vc2(const T& r, const T& M200, const T& c) {
   return kG * M200 * nfw_m(r / rs) / (nfw_m(c) * r);
 }
 
+// Hernquist halo (the paper's, Sec. 2.2): v^2 = G M r / (r + R)^2, Eq. 2 with the halo's
+// mass and scale radius.
+template <class T> T hernquist_vc2(const T& r, const T& M, const T& Rh) {
+  return kG * M * r / ((r + Rh) * (r + Rh));
+}
+template <class T> T halo_vc2(const T& r, const T& M, const T& p, int halo) {
+  return halo == 0 ? nfw_vc2(r, M, p) : hernquist_vc2(r, M, p);
+}
+
 // Razor-thin exponential disc: circular velocity squared (Eq. 9, Binney & Tremaine form).
 template <class T> T freeman_vc2(const T& r, const T& Md, const T& Rd) {
   const T y = r / (2.0 * Rd);
@@ -205,10 +214,11 @@ template <class T> struct Model {
   T x0, y0, cpa, spa, ci, si;
   T a, g, Mb, MLb;
   T Md[2], Rd[2], k[2], MLd[2];
-  T M200, c, vsys;
+  int halo;             // 0: NFW (M200, c); 1: Hernquist (M_h, R_h), the paper's halo
+  T M200, c, vsys;      // for the Hernquist halo M200 holds M_h and c holds R_h
 };
 
-template <class T> Model<T> decode(const T* th, int nd) {
+template <class T> Model<T> decode(const T* th, int nd, int halo) {
   Model<T> m;
   m.nd = nd;
   m.x0 = th[0]; m.y0 = th[1];
@@ -217,18 +227,20 @@ template <class T> Model<T> decode(const T* th, int nd) {
   m.Mb = pow(10.0, th[4]); m.a = pow(10.0, th[5]); m.g = th[6];
   m.Md[0] = pow(10.0, th[7]); m.Rd[0] = pow(10.0, th[8]); m.k[0] = th[9];
   m.MLb = th[10]; m.MLd[0] = th[11];
-  m.M200 = pow(10.0, th[12]); m.c = th[13]; m.vsys = th[14];
+  m.halo = halo;
+  m.M200 = pow(10.0, th[12]); m.vsys = th[14];
+  m.c = halo == 0 ? th[13] : pow(10.0, th[13]);
   if (nd == 2) { m.Md[1] = pow(10.0, th[15]); m.Rd[1] = pow(10.0, th[16]); m.k[1] = th[17]; m.MLd[1] = th[18]; }
   return m;
 }
 
-bool in_domain(const double* th, int np) {
+bool in_domain(const double* th, int np, int halo) {
   for (int i = 0; i < np; ++i) if (!std::isfinite(th[i])) return false;
   if (!(th[3] >= 0.0 && th[3] < 0.5 * kPi)) return false;   // inclination
   if (!(th[6] >= 0.0 && th[6] < 3.0)) return false;         // Dehnen inner slope
   if (!(std::fabs(th[9]) <= 1.0)) return false;             // Satoh k
   if (!(th[10] > 0.0 && th[11] > 0.0)) return false;        // M/L
-  if (!(th[13] > 0.0)) return false;                        // concentration
+  if (halo == 0 && !(th[13] > 0.0)) return false;           // NFW concentration
   if (np == 19 && !(std::fabs(th[17]) <= 1.0 && th[18] > 0.0)) return false;
   return true;
 }
@@ -252,7 +264,7 @@ void eval_point(const Model<T>& m, double xs, double ys, double kpa, const Radia
   bulge_projected(R, m.a, m.g, m.Mb, q, &Sb, &s2b);
 
   // Eq. 10: every component's circular velocity adds in quadrature
-  T vint2 = bulge_vc2(r, m.a, m.g, m.Mb) + nfw_vc2(r, m.M200, m.c);
+  T vint2 = bulge_vc2(r, m.a, m.g, m.Mb) + halo_vc2(r, m.M200, m.c, m.halo);
   T Sd[2], vd[2], s2d[2];
   for (int j = 0; j < m.nd; ++j) vint2 += freeman_vc2(r, m.Md[j], m.Rd[j]);
   const T vint = sqrt(vint2);
@@ -409,7 +421,7 @@ typedef struct {
   const uint8_t* mask;     // [4][ny][nx] or NULL
 } bang_oracle_galaxy;
 
-typedef struct { int n_discs; int n_quad; } bang_oracle_opts;
+typedef struct { int n_discs; int n_quad; int halo_kind; } bang_oracle_opts;
 
 static Galaxy make_galaxy(const bang_oracle_galaxy* d) {
   Galaxy g;
@@ -458,6 +470,7 @@ double bang_oracle_bulge_vc2(double r, double a, double gamma, double M) { retur
 double bang_oracle_dehnen_rho(double r, double a, double gamma, double M) { return dehnen_rho(r, a, gamma, M); }
 double bang_oracle_dehnen_mass(double r, double a, double gamma, double M) { return dehnen_mass(r, a, gamma, M); }
 double bang_oracle_nfw_vc2(double r, double M200, double c) { return nfw_vc2(r, M200, c); }
+double bang_oracle_hernquist_halo_vc2(double r, double Mh, double Rh) { return hernquist_vc2(r, Mh, Rh); }
 double bang_oracle_nfw_r200(double M200) { return std::pow(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit), 1.0 / 3.0); }
 double bang_oracle_freeman_vc2(double r, double Md, double Rd) { return freeman_vc2(r, Md, Rd); }
 double bang_oracle_bessel_diff(double y) { return bessel_diff(y); }
@@ -468,9 +481,9 @@ double bang_oracle_rho_crit(void) { return kRhoCrit; }
 int bang_oracle_points(const bang_oracle_opts* o, const double* theta, const double* xs, const double* ys, int n,
                        double kpa, double* out) {
   const int np = bang_oracle_nparams(o->n_discs);
-  if (!in_domain(theta, np)) return 1;
+  if (!in_domain(theta, np, o->halo_kind)) return 1;
   const RadialRule q(o->n_quad);
-  const Model<double> m = decode(theta, o->n_discs);
+  const Model<double> m = decode(theta, o->n_discs, o->halo_kind);
   for (int p = 0; p < n; ++p) {
     double v[4];
     eval_point(m, xs[p], ys[p], kpa, q, v);
@@ -485,10 +498,10 @@ int bang_oracle_fine_field(const bang_oracle_galaxy* d, const bang_oracle_opts* 
   set_threads(nthreads);
   const Galaxy g = make_galaxy(d);
   const int np = bang_oracle_nparams(o->n_discs);
-  if (!in_domain(theta, np)) return 1;
+  if (!in_domain(theta, np, o->halo_kind)) return 1;
   const RadialRule q(o->n_quad);
   std::vector<double> f;
-  fine_field(g, decode(theta, o->n_discs), q, f);
+  fine_field(g, decode(theta, o->n_discs, o->halo_kind), q, f);
   std::memcpy(field, f.data(), f.size() * sizeof(double));
   return 0;
 }
@@ -509,10 +522,10 @@ int bang_oracle_maps(const bang_oracle_galaxy* d, const bang_oracle_opts* o, con
   set_threads(nthreads);
   const Galaxy g = make_galaxy(d);
   const int np = bang_oracle_nparams(o->n_discs);
-  if (!in_domain(theta, np)) return 1;
+  if (!in_domain(theta, np, o->halo_kind)) return 1;
   const RadialRule q(o->n_quad);
   std::vector<double> out;
-  model_maps(g, decode(theta, o->n_discs), q, out);
+  model_maps(g, decode(theta, o->n_discs, o->halo_kind), q, out);
   std::memcpy(maps, out.data(), out.size() * sizeof(double));
   return 0;
 }
@@ -530,13 +543,13 @@ int bang_oracle_loglike(const bang_oracle_galaxy* d, const bang_oracle_opts* o, 
   const double cst = norm_const(g);
   for (int b = 0; b < B; ++b) {
     const double* th = theta + (size_t)b * np;
-    if (!in_domain(th, np)) {
+    if (!in_domain(th, np, o->halo_kind)) {
       logL[b] = -INFINITY;
       if (chi2) chi2[b] = INFINITY;
       continue;
     }
     std::vector<double> maps;
-    model_maps(g, decode(th, o->n_discs), q, maps);
+    model_maps(g, decode(th, o->n_discs, o->halo_kind), q, maps);
     const double c2 = chi2_of(g, maps);
     logL[b] = -0.5 * c2 - cst;
     if (chi2) chi2[b] = c2;
@@ -555,7 +568,7 @@ int bang_oracle_loglike_grad(const bang_oracle_galaxy* d, const bang_oracle_opts
   const double cst = norm_const(g);
   for (int b = 0; b < B; ++b) {
     const double* th = theta + (size_t)b * np;
-    if (!in_domain(th, np)) {
+    if (!in_domain(th, np, o->halo_kind)) {
       logL[b] = -INFINITY;
       for (int p = 0; p < np; ++p) grad[(size_t)b * np + p] = 0.0;
       continue;
@@ -563,7 +576,7 @@ int bang_oracle_loglike_grad(const bang_oracle_galaxy* d, const bang_oracle_opts
     Dual td[PMAX];
     for (int p = 0; p < np; ++p) { td[p] = Dual(th[p]); td[p].d[p] = 1.0; }
     std::vector<Dual> maps;
-    model_maps(g, decode(td, o->n_discs), q, maps);
+    model_maps(g, decode(td, o->n_discs, o->halo_kind), q, maps);
     const Dual c2 = chi2_of(g, maps);
     logL[b] = -0.5 * c2.v - cst;
     for (int p = 0; p < np; ++p) grad[(size_t)b * np + p] = -0.5 * c2.d[p];

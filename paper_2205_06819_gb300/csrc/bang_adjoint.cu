@@ -175,8 +175,10 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float lub = log2f(ub);
   const float vb2 = m.vb_c * exp2f(m.three_mg * lub) / xa;
   const float xh = r * m.inv_rs;
-  const float mh = nfw_m(xh);
-  const float vh2 = m.vh_c * mh * inv_r;
+  const float ixh1 = __frcp_rn(1.0f + xh);
+  // NFW: vh2 = vh_c m(x) / r; Hernquist: vh2 = vh_c h(x), h = x / (1 + x)^2
+  const float mh = m.hern ? xh * ixh1 * ixh1 : nfw_m(xh);
+  const float vh2 = m.hern ? m.vh_c * mh : m.vh_c * mh * inv_r;
   float vint2 = vb2 + vh2;
   float Fd[ND], dFd[ND], ex[ND], Sd[ND];
 #pragma unroll
@@ -236,12 +238,19 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
     gr = fmaf(gy, m.half_inv_Rd[j], gr);
     dj[D_HIRD] += gy * r;
   }
-  // NFW halo: vh2 = vh_c m(x) / r, x = r / rs, m'(x) = x / (1 + x)^2
-  acc[A_VHC] += gvint2 * mh * inv_r;
-  const float xh1 = 1.0f + xh;
-  const float gxh = gvint2 * m.vh_c * (xh / (xh1 * xh1)) * inv_r;
-  gr += gxh * m.inv_rs - gvint2 * vh2 * inv_r;
-  acc[A_IRS] += gxh * r;
+  if (m.hern) {
+    // Hernquist halo: vh2 = vh_c h(x), x = r / R_h, h'(x) = (1 - x) / (1 + x)^3
+    acc[A_VHC] += gvint2 * mh;
+    const float gxh = gvint2 * m.vh_c * (1.0f - xh) * ixh1 * ixh1 * ixh1;
+    gr += gxh * m.inv_rs;
+    acc[A_IRS] += gxh * r;
+  } else {
+    // NFW halo: vh2 = vh_c m(x) / r, x = r / rs, m'(x) = x / (1 + x)^2
+    acc[A_VHC] += gvint2 * mh * inv_r;
+    const float gxh = gvint2 * m.vh_c * (xh * ixh1 * ixh1) * inv_r;
+    gr += gxh * m.inv_rs - gvint2 * vh2 * inv_r;
+    acc[A_IRS] += gxh * r;
+  }
   // bulge circular velocity: vb2 = G Mb u^(3-g) / r, u = r / (r + a)
   const float omu = 1.0f - ub;
   gr += gvint2 * vb2 * inv_r * (m.three_mg * omu - 1.0f);
@@ -276,7 +285,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
 }
 
 // d logL / d theta from the reduced constant adjoints (float64, one thread).
-__device__ void constants_to_theta(const float* __restrict__ th, int nd, const double* s, double* g) {
+__device__ void constants_to_theta(const float* __restrict__ th, int nd, int halo_kind, const double* s, double* g) {
   const double ln10 = 2.302585092994045684;
   const double ci = cos((double)th[3]), si = sin((double)th[3]);
   const double a = pow(10.0, (double)th[5]);
@@ -288,13 +297,19 @@ __device__ void constants_to_theta(const float* __restrict__ th, int nd, const d
   g[5] = ln10 * a * s[A_A];
   g[6] = s[A_G];
   g[10] = -s[A_LB] * (1e-6 / th[10]) / th[10];
-  // NFW
-  const double M200 = pow(10.0, (double)th[12]), c = th[13];
-  const double r200 = cbrt(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit));
-  const double mc = log1p(c) - c / (1.0 + c), dmc = c / ((1.0 + c) * (1.0 + c));
-  const double vh_c = kG * M200 / mc, inv_rs = c / r200;
-  g[12] = ln10 * (s[A_VHC] * vh_c - s[A_IRS] * inv_rs / 3.0);
-  g[13] = -s[A_VHC] * vh_c * dmc / mc + s[A_IRS] * inv_rs / c;
+  if (halo_kind == 0) {   // NFW: vh_c = G M200 / m(c), 1/rs = c / r200(M200)
+    const double M200 = pow(10.0, (double)th[12]), c = th[13];
+    const double r200 = cbrt(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit));
+    const double mc = log1p(c) - c / (1.0 + c), dmc = c / ((1.0 + c) * (1.0 + c));
+    const double vh_c = kG * M200 / mc, inv_rs = c / r200;
+    g[12] = ln10 * (s[A_VHC] * vh_c - s[A_IRS] * inv_rs / 3.0);
+    g[13] = -s[A_VHC] * vh_c * dmc / mc + s[A_IRS] * inv_rs / c;
+  } else {                // Hernquist: vh_c = G M_h / R_h, 1/rs = 1 / R_h
+    const double Mh = pow(10.0, (double)th[12]), Rh = pow(10.0, (double)th[13]);
+    const double vh_c = kG * Mh / Rh, inv_rs = 1.0 / Rh;
+    g[12] = ln10 * s[A_VHC] * vh_c;
+    g[13] = -ln10 * (s[A_VHC] * vh_c + s[A_IRS] * inv_rs);
+  }
   for (int j = 0; j < nd; ++j) {
     const double* dj = s + A_D0 + kPerDisc * j;
     const int o = j == 0 ? 7 : 15;
@@ -453,16 +468,16 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
 
 // One thread per row: the reduced constant adjoints -> d logL / d theta (float64), or zero
 // for a row outside the parameter domain.
-__global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, const double* __restrict__ acc,
-                                int B, float* __restrict__ grad) {
+__global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind,
+                                const double* __restrict__ acc, int B, float* __restrict__ grad) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const float* th = theta + (size_t)b * P;
   double g[kMaxParams];
   for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
-  if (theta_in_domain(th, nd)) {
+  if (theta_in_domain(th, nd, halo_kind)) {
     const double* s = acc + (size_t)b * kGradAccStride;
-    constants_to_theta(th, nd, s, g);
+    constants_to_theta(th, nd, halo_kind, s, g);
     g[14] = s[24];
   }
   for (int p = 0; p < P; ++p) grad[(size_t)b * P + p] = (float)g[p];
@@ -576,9 +591,9 @@ cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const in
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_out(const float* theta, int P, int n_discs, const double* acc, int B, float* grad,
-                            cudaStream_t st) {
-  grad_out_kernel<<<(B + 63) / 64, 64, 0, st>>>(theta, P, n_discs, acc, B, grad);
+cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, const double* acc, int B,
+                            float* grad, cudaStream_t st) {
+  grad_out_kernel<<<(B + 63) / 64, 64, 0, st>>>(theta, P, n_discs, halo_kind, acc, B, grad);
   return cudaGetLastError();
 }
 

@@ -509,7 +509,9 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.out_off = p->d_out_off.as<int64_t>();
   a.queue = p->d_queue.as<int>();
   a.consts = p->d_consts.as<bang::ModelConst>();
-  cudaError_t e = bang::launch_decode(theta, m->P, m->opts.n_discs, a.gals, p->d_row_g.as<int>(), p->B,
+  a.halo_kind = m->opts.halo_kind;
+  cudaError_t e = bang::launch_decode(theta, m->P, m->opts.n_discs, m->opts.halo_kind, a.gals, p->d_row_g.as<int>(),
+                                      p->B,
                                       p->d_consts.as<bang::ModelConst>(), st);
   if (e != cudaSuccess) return e;
   if (m->opts.bulge_table > 0) {
@@ -555,7 +557,7 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   if (e != cudaSuccess) return e;
   e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
   if (e != cudaSuccess) return e;
-  return bang::launch_grad_out(theta, m->P, m->opts.n_discs, grad_acc, p->B, grad, st);
+  return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, grad_acc, p->B, grad, st);
 }
 
 }  // namespace
@@ -568,6 +570,7 @@ bool model_view(const bang_model* m, ModelView* v) {
   v->n_gal = (int)m->gals.size();
   v->n_quad = m->opts.n_quad;
   v->n_discs = m->opts.n_discs;
+  v->halo_kind = m->opts.halo_kind;
   v->P = m->P;
   v->num_sms = m->num_sms;
   v->smem_optin = m->smem_optin;
@@ -601,7 +604,8 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
   if (opts->n_discs != 1 && opts->n_discs != 2) return fail(BANG_E_INVALID_ARG, "n_discs must be 1 or 2");
   if (opts->n_quad != 64 && opts->n_quad != 128) return fail(BANG_E_INVALID_ARG, "n_quad must be 64 or 128");
   if (opts->bulge_kind != 0) return fail(BANG_E_UNSUPPORTED, "bulge_kind %d not available", opts->bulge_kind);
-  if (opts->halo_kind != 0) return fail(BANG_E_UNSUPPORTED, "halo_kind %d not available (NFW = 0)", opts->halo_kind);
+  if (opts->halo_kind != 0 && opts->halo_kind != 1)
+    return fail(BANG_E_UNSUPPORTED, "halo_kind %d not available (0 NFW, 1 Hernquist)", opts->halo_kind);
   if (opts->psf_mode != 0) return fail(BANG_E_UNSUPPORTED, "psf_mode %d not available", opts->psf_mode);
   if (opts->bulge_table != 0 && (opts->bulge_table < 256 || opts->bulge_table > 4096))
     return fail(BANG_E_INVALID_ARG, "bulge_table must be 0 or in [256, 4096]");
@@ -867,7 +871,7 @@ bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t*
   }
   for (int b = 0; b < B; ++b) {
     const int g = gal_idx ? gal_idx[b] : 0;
-    BANG_CUDA(bang::launch_plain_row(d_theta + (size_t)b * m->P, m->P, m->opts.n_quad, m->opts.n_discs,
+    BANG_CUDA(bang::launch_plain_row(d_theta + (size_t)b * m->P, m->P, m->opts.n_quad, m->opts.n_discs, m->opts.halo_kind,
                                      m->d_gals.as<bang::GalDev>() + g, m->gals[g], m->scratch_plain.p, d_logL + b, st));
   }
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));

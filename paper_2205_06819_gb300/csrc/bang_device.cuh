@@ -63,7 +63,8 @@ struct ModelConst {
   float cS, cQ, vb_c;      // Sigma = cS x pS S; Sigma sigma^2 = cQ pQ Q; vb^2 = vb_c u^(3-g) / (r/a)
   float Lb;                // 1e-6 / (M/L)_b
   // halo (NFW)
-  float inv_rs, vh_c;      // x = r / rs; vh^2 = vh_c m(x) / r
+  float inv_rs, vh_c;      // x = r / rs; NFW vh^2 = vh_c m(x) / r; Hernquist vh^2 = vh_c x / (1 + x)^2
+  int hern;                // halo kind: 0 NFW, 1 Hernquist
   // discs
   float inv_Rd[2], half_inv_Rd[2], vd_c[2], Sd_c[2], Ld[2], ks[2], omk[2];
   float vsys;
@@ -83,8 +84,9 @@ __device__ __forceinline__ float lg2_approx(float x) {
 
 // Decode row theta (float32) into per-model constants.  Returns 0 when the row is outside
 // the parameter domain (non-finite, i not in [0, pi/2), gamma not in [0, 3), |k| > 1,
-// c <= 0, M/L <= 0).
-__device__ inline bool theta_in_domain(const float* __restrict__ th, int nd) {
+// M/L <= 0, and for the NFW halo c <= 0).  halo_kind 0: NFW (slot 13 = c); 1: Hernquist
+// (slot 13 = log10 R_h, the paper's halo).
+__device__ inline bool theta_in_domain(const float* __restrict__ th, int nd, int halo_kind) {
   const int np = nd == 2 ? 19 : 15;
   for (int i = 0; i < np; ++i)
     if (!isfinite((double)th[i])) return false;
@@ -93,14 +95,15 @@ __device__ inline bool theta_in_domain(const float* __restrict__ th, int nd) {
   if (!(gam >= 0.0 && gam < 3.0)) return false;
   if (!(fabs((double)th[9]) <= 1.0)) return false;
   if (!(th[10] > 0.f && th[11] > 0.f)) return false;
-  if (!(th[13] > 0.f)) return false;
+  if (halo_kind == 0 && !(th[13] > 0.f)) return false;
   if (nd == 2 && !(fabs((double)th[17]) <= 1.0 && th[18] > 0.f)) return false;
   return true;
 }
 
-__device__ inline int decode_model(const float* __restrict__ th, int nd, const GalDev& g, ModelConst& m) {
+__device__ inline int decode_model(const float* __restrict__ th, int nd, int halo_kind, const GalDev& g,
+                                   ModelConst& m) {
   const int np = nd == 2 ? 19 : 15;
-  if (!theta_in_domain(th, nd)) return 0;
+  if (!theta_in_domain(th, nd, halo_kind)) return 0;
   double t[kMaxParams];
   for (int i = 0; i < np; ++i) t[i] = (double)th[i];
 
@@ -124,11 +127,18 @@ __device__ inline int decode_model(const float* __restrict__ th, int nd, const G
   m.vb_c = (float)(kG * Mb / a);
   m.Lb = (float)(1e-6 / t[10]);
   // halo
-  const double M200 = pow(10.0, t[12]), c = t[13];
-  const double r200 = cbrt(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit));
-  const double mc = log1p(c) - c / (1.0 + c);
-  m.inv_rs = (float)(c / r200);
-  m.vh_c = (float)(kG * M200 / mc);
+  m.hern = halo_kind;
+  if (halo_kind == 0) {   // NFW: vh^2 = vh_c m(r/rs) / r
+    const double M200 = pow(10.0, t[12]), c = t[13];
+    const double r200 = cbrt(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit));
+    const double mc = log1p(c) - c / (1.0 + c);
+    m.inv_rs = (float)(c / r200);
+    m.vh_c = (float)(kG * M200 / mc);
+  } else {                // Hernquist (Eq. 2 with M_h, R_h): vh^2 = vh_c x / (1 + x)^2, x = r / R_h
+    const double Mh = pow(10.0, t[12]), Rh = pow(10.0, t[13]);
+    m.inv_rs = (float)(1.0 / Rh);
+    m.vh_c = (float)(kG * Mh / Rh);
+  }
   // discs
   for (int j = 0; j < 2; ++j) {
     if (j >= nd) {
@@ -226,6 +236,16 @@ __device__ __forceinline__ float nfw_m(float x) {
     return 2.0f * z2 / (1.0f + z) + 2.0f * z2 * z * s;
   }
   return log1pf(x) - x / (1.0f + x);
+}
+
+// Circular velocity squared of the halo at in-plane radius r.
+__device__ __forceinline__ float halo_v2(const ModelConst& m, float r, float inv_r) {
+  const float x = r * m.inv_rs;
+  if (m.hern) {
+    const float ix = __frcp_rn(1.0f + x);
+    return m.vh_c * x * ix * ix;
+  }
+  return m.vh_c * nfw_m(x) * inv_r;
 }
 
 // Projected density and Sigma sigma^2 of the bulge at sky radius R (kpc).
@@ -381,7 +401,7 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
   const float xa = r * m.inv_a;
   const float ub = xa / (xa + 1.0f);
   float vint2 = __fdividef(m.vb_c * ex2_approx(m.three_mg * lg2_approx(ub)), xa);
-  vint2 += m.vh_c * nfw_m(r * m.inv_rs) * inv_r;
+  vint2 += halo_v2(m, r, inv_r);
   float Sd[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {

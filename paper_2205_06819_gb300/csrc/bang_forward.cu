@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     if (tid == 0) {
       gs = a.gals[w.g];
       if (a.consts) mc = a.consts[w.b];
-      else mc.valid = decode_model(a.theta + (size_t)w.b * a.P, ND, gs, mc);
+      else mc.valid = decode_model(a.theta + (size_t)w.b * a.P, ND, a.halo_kind, gs, mc);
     }
     __syncthreads();
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx;
@@ -256,12 +256,13 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
 }
 
 // One thread per row: theta -> per-model constants (float64 decode), against the row's galaxy.
-__global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, const GalDev* __restrict__ gals,
-                              const int* __restrict__ row_g, int B, ModelConst* __restrict__ out) {
+__global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind,
+                              const GalDev* __restrict__ gals, const int* __restrict__ row_g, int B,
+                              ModelConst* __restrict__ out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   ModelConst m;
-  m.valid = decode_model(theta + (size_t)b * P, nd, gals[row_g[b]], m);
+  m.valid = decode_model(theta + (size_t)b * P, nd, halo_kind, gals[row_g[b]], m);
   out[b] = m;
 }
 
@@ -337,9 +338,9 @@ cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d,
 
 size_t model_const_bytes() { return sizeof(ModelConst); }
 
-cudaError_t launch_decode(const float* theta, int P, int n_discs, const GalDev* gals, const int* row_g, int B,
-                          ModelConst* out, cudaStream_t st) {
-  decode_kernel<<<(B + 63) / 64, 64, 0, st>>>(theta, P, n_discs, gals, row_g, B, out);
+cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
+                          int B, ModelConst* out, cudaStream_t st) {
+  decode_kernel<<<(B + 63) / 64, 64, 0, st>>>(theta, P, n_discs, halo_kind, gals, row_g, B, out);
   return cudaGetLastError();
 }
 
@@ -489,6 +490,7 @@ extern "C" bang_status bang_loglike_batch_noalloc(bang_model* m, const float* th
   FwdArgs a{};
   a.theta = theta;
   a.P = v.P;
+  a.halo_kind = v.halo_kind;
   a.gals = v.d_gals;
   a.items = items;
   a.order = nullptr;

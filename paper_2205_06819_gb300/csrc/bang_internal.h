@@ -23,6 +23,7 @@ enum { kModeLogL = 0, kModeMaps = 1, kModeSeed = 2 };
 struct FwdArgs {
   const float* theta;       // [B][P]
   int P;
+  int halo_kind;            // 0 NFW, 1 Hernquist (used when consts is NULL)
   const GalDev* gals;
   const ModelConst* consts; // [B] decoded rows (NULL: each block decodes its row itself)
   const WorkItem* items;    // [n_items], items of one row contiguous, rows in order
@@ -61,7 +62,7 @@ struct AdjArgs {
 // Read-only view of a model's immutable device state (for entry points defined outside
 // bang_api.cu).
 struct ModelView {
-  int device, n_gal, n_quad, n_discs, P, num_sms, smem_optin, bulge_table;
+  int device, n_gal, n_quad, n_discs, halo_kind, P, num_sms, smem_optin, bulge_table;
   const GalDev* h_gals;   // host copies (device pointers inside)
   const GalDev* d_gals;   // device array [n_gal]
 };
@@ -88,16 +89,16 @@ cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const in
 const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d);
 cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
                            cudaStream_t st);
-cudaError_t launch_grad_out(const float* theta, int P, int n_discs, const double* acc, int B, float* grad,
-                            cudaStream_t st);
+cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, const double* acc, int B,
+                            float* grad, cudaStream_t st);
 size_t model_const_bytes();
-cudaError_t launch_decode(const float* theta, int P, int n_discs, const GalDev* gals, const int* row_g, int B,
-                          ModelConst* out, cudaStream_t st);
+cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
+                          int B, ModelConst* out, cudaStream_t st);
 cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq);
 
 size_t plain_scratch_bytes(int N, int n);
 int plain_launches_per_row();
-cudaError_t launch_plain_row(const float* theta, int P, int n_quad, int n_discs, const GalDev* d_gal,
+cudaError_t launch_plain_row(const float* theta, int P, int n_quad, int n_discs, int halo_kind, const GalDev* d_gal,
                              const GalDev& h_gal, void* scratch, double* logL, cudaStream_t st);
 cudaError_t upload_nodes_plain(const float* cm1, const float* lc, const float* ws, const float* wq);
 

@@ -22,10 +22,10 @@ struct PlainBufs {
   ModelConst* mc;                                           // [1]
 };
 
-__global__ void plain_decode(const float* __restrict__ theta, int nd, const GalDev* __restrict__ gal,
+__global__ void plain_decode(const float* __restrict__ theta, int nd, int halo_kind, const GalDev* __restrict__ gal,
                              ModelConst* __restrict__ mc, double* __restrict__ chi) {
   ModelConst m;
-  m.valid = decode_model(theta, nd, *gal, m);
+  m.valid = decode_model(theta, nd, halo_kind, *gal, m);
   *mc = m;
   *chi = 0.0;
 }
@@ -71,7 +71,7 @@ __global__ void plain_velocity(const GalDev* __restrict__ gal, const ModelConst*
   const float xa = r * m.inv_a;
   const float ub = xa / (xa + 1.0f);
   float v2 = m.vb_c * exp2f(m.three_mg * log2f(ub)) / xa;
-  v2 += m.vh_c * nfw_m(r * m.inv_rs) * (1.0f / r);
+  v2 += halo_v2(m, r, 1.0f / r);
 #pragma unroll
   for (int j = 0; j < ND; ++j) v2 += m.vd_c[j] * disc_F(r * m.half_inv_Rd[j]);
   b.vint2[p] = v2;
@@ -179,10 +179,10 @@ __global__ void plain_logl(const GalDev* __restrict__ gal, const ModelConst* __r
 inline int blocks_for(int n) { return (n + kPlainThreads - 1) / kPlainThreads; }
 
 template <int NQ, int ND, int PSF>
-cudaError_t chain(const float* theta, int P, const GalDev* d_gal, const GalDev& h_gal, PlainBufs bufs, double* logL,
-                  cudaStream_t st) {
+cudaError_t chain(const float* theta, int P, int halo_kind, const GalDev* d_gal, const GalDev& h_gal, PlainBufs bufs,
+                  double* logL, cudaStream_t st) {
   const int N = h_gal.W * h_gal.H, n = h_gal.nx * h_gal.ny;
-  plain_decode<<<1, 1, 0, st>>>(theta, ND, d_gal, bufs.mc, bufs.chi);
+  plain_decode<<<1, 1, 0, st>>>(theta, ND, halo_kind, d_gal, bufs.mc, bufs.chi);
   plain_coords<<<blocks_for(N), kPlainThreads, 0, st>>>(d_gal, bufs.mc, bufs);
   plain_bulge<NQ><<<blocks_for(N), kPlainThreads, 0, st>>>(d_gal, bufs.mc, bufs);
   plain_velocity<ND><<<blocks_for(N), kPlainThreads, 0, st>>>(d_gal, bufs.mc, bufs);
@@ -203,7 +203,7 @@ size_t plain_scratch_bytes(int N, int n) {
 
 int plain_launches_per_row() { return 9; }
 
-cudaError_t launch_plain_row(const float* theta, int P, int n_quad, int n_discs, const GalDev* d_gal,
+cudaError_t launch_plain_row(const float* theta, int P, int n_quad, int n_discs, int halo_kind, const GalDev* d_gal,
                              const GalDev& h_gal, void* scratch, double* logL, cudaStream_t st) {
   const int N = h_gal.W * h_gal.H, n = h_gal.nx * h_gal.ny;
   float* base = static_cast<float*>(scratch);
@@ -225,8 +225,8 @@ cudaError_t launch_plain_row(const float* theta, int P, int n_quad, int n_discs,
   const int psf2d = h_gal.psf_kind;
 #define BANG_CHAIN(NQ, ND)                                                                    \
   if (n_quad == NQ && n_discs == ND)                                                          \
-    return psf2d ? chain<NQ, ND, 1>(theta, P, d_gal, h_gal, b, logL, st)                      \
-                 : chain<NQ, ND, 0>(theta, P, d_gal, h_gal, b, logL, st);
+    return psf2d ? chain<NQ, ND, 1>(theta, P, halo_kind, d_gal, h_gal, b, logL, st)           \
+                 : chain<NQ, ND, 0>(theta, P, halo_kind, d_gal, h_gal, b, logL, st);
   BANG_CHAIN(64, 1) BANG_CHAIN(64, 2) BANG_CHAIN(128, 1) BANG_CHAIN(128, 2)
 #undef BANG_CHAIN
   return cudaErrorInvalidValue;

@@ -29,7 +29,7 @@ PARAM_NAMES_2 = PARAM_NAMES_1 + ["logMd2", "logRd2", "k2", "MLd2"]
 DEG = math.pi / 180.0
 
 
-def prior_box(n_discs: int, gamma_fixed: float | None = None) -> np.ndarray:
+def prior_box(n_discs: int, gamma_fixed: float | None = None, halo_kind: int = 0) -> np.ndarray:
     """[P, 2] lower/upper bounds of the uniform prior box.
 
     Inclination 30-70 deg, bulge scale 0.5-2 kpc, disc scale 2-5 kpc, log bulge/disc mass
@@ -51,6 +51,8 @@ def prior_box(n_discs: int, gamma_fixed: float | None = None) -> np.ndarray:
     if n_discs == 2:
         box += [(9.0, 11.0), (math.log10(2.0), math.log10(5.0)), (0.0, 1.0), (0.1, 100.0)]
     b = np.array(box, dtype=np.float64)
+    if halo_kind == 1:                               # Hernquist halo: slot 13 = log10 R_h, prior [1, 3]
+        b[13] = (1.0, 3.0)
     if gamma_fixed is not None:
         b[6] = (gamma_fixed, gamma_fixed)
     return b

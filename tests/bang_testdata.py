@@ -7,11 +7,12 @@ from paper_2205_06819_gb300 import synth
 
 
 class Dataset:
-    def __init__(self, spec: synth.GalaxySpec, theta_true, n_discs=1, n_quad=64, seed=1, noise=True, mask=None):
-        self.spec, self.n_discs, self.n_quad = spec, n_discs, n_quad
+    def __init__(self, spec: synth.GalaxySpec, theta_true, n_discs=1, n_quad=64, seed=1, noise=True, mask=None,
+                 halo_kind=0):
+        self.spec, self.n_discs, self.n_quad, self.halo_kind = spec, n_discs, n_quad, halo_kind
         self.theta_true = np.asarray(theta_true, dtype=np.float64)
         g0 = self.oracle_galaxy(None, None, None)
-        true = oracle.maps(g0, self.theta_true, n_discs=n_discs, n_quad=n_quad)
+        true = oracle.maps(g0, self.theta_true, n_discs=n_discs, n_quad=n_quad, halo_kind=halo_kind)
         self.data, self.err, m = synth.noisy_data(true, seed=seed, noise=noise)
         self.mask = m if mask is None else np.asarray(mask, dtype=np.uint8)
         self.og = self.oracle_galaxy(self.data.astype(np.float64), self.err.astype(np.float64), self.mask)
@@ -30,13 +31,14 @@ class Dataset:
 
     def oracle_loglike(self, theta32, nthreads=0):
         th = np.asarray(theta32, dtype=np.float32).astype(np.float64)
-        return oracle.loglike(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad, nthreads=nthreads)
+        return oracle.loglike(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad, nthreads=nthreads,
+                              halo_kind=self.halo_kind)
 
     def oracle_maps(self, theta32):
         th = np.asarray(theta32, dtype=np.float32).astype(np.float64)
-        return oracle.maps(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad)
+        return oracle.maps(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad, halo_kind=self.halo_kind)
 
 
-def theta_batch(n_discs, theta_true, B, seed, gamma_fixed=None):
-    box = synth.prior_box(n_discs, gamma_fixed)
+def theta_batch(n_discs, theta_true, B, seed, gamma_fixed=None, halo_kind=0):
+    box = synth.prior_box(n_discs, gamma_fixed, halo_kind)
     return synth.draw_theta_batch(box, np.asarray(theta_true), B, seed).astype(np.float32)

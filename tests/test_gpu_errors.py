@@ -58,7 +58,7 @@ def test_invalid_arguments(env):
     assert L.bang_loglike_batch(m.handle, None, None, 1, ctypes.c_void_p(out.data_ptr()), None) == 1
 
 
-@pytest.mark.parametrize("case", ["bad_err", "bad_quad", "hernquist_halo", "bad_table", "bad_grid"])
+@pytest.mark.parametrize("case", ["bad_err", "bad_quad", "unknown_halo", "bad_table", "bad_grid"])
 def test_invalid_model_descriptions(env, case):
     _lib, Galaxy, Model, ones = env
     err = ones.copy()
@@ -72,14 +72,14 @@ def test_invalid_model_descriptions(env, case):
         kw["bulge_table"] = 100
     elif case == "bad_grid":
         os_ = 0
-    if case == "hernquist_halo":
+    if case == "unknown_halo":
         L = _lib.lib()
         d = (_lib.GalaxyDesc * 1)()
         data = ones * 50.0
         d[0].nx, d[0].ny, d[0].oversample = 11, 9, 3
         d[0].spaxel_arcsec, d[0].kpc_per_arcsec, d[0].psf_fwhm_arcsec = 1.0, 0.25695, 2.0
         d[0].data, d[0].err = data.ctypes.data, err.ctypes.data
-        opts = _lib.ModelOpts(1, 0, 1, 64, 0, 0)
+        opts = _lib.ModelOpts(1, 0, 2, 64, 0, 0)
         h = ctypes.c_void_p()
         assert L.bang_model_create(d, 1, ctypes.byref(opts), 0, ctypes.byref(h)) == 4   # BANG_E_UNSUPPORTED
         assert b"halo" in L.bang_last_error()

@@ -101,3 +101,14 @@ def test_nfw_enclosed_mass_integral(oracle_mod, x):
     r = x * rs
     num, _ = integrate.quad(lambda t: 4 * math.pi * t * t * rho(t), 0, r, epsabs=0, epsrel=1e-12)
     assert oracle_mod.nfw_vc2(r, M200, c) * r / G == pytest.approx(num, rel=1e-9)
+
+
+@pytest.mark.parametrize("x", [0.05, 0.5, 2.0, 8.0])
+def test_hernquist_halo_is_the_enclosed_mass_of_eq1(oracle_mod, x):
+    """The paper's halo: Eq. 2 with the halo's mass and scale radius, i.e. G M(<r) / r for
+    the density of Eq. 1, integrated here numerically."""
+    Mh, Rh = 10 ** 12.2, 25.0
+    r = x * Rh
+    rho = lambda t: Mh / (2 * math.pi) * Rh / (t * (t + Rh) ** 3)
+    num, _ = integrate.quad(lambda t: 4 * math.pi * t * t * rho(t), 0, r, epsabs=0, epsrel=1e-12)
+    assert oracle_mod.hernquist_halo_vc2(r, Mh, Rh) * r / G == pytest.approx(num, rel=1e-10)

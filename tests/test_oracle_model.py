@@ -290,3 +290,31 @@ def test_dual_gradient_matches_central_differences(oracle_mod, n_discs):
         fd[p] = (4.0 * central(p, h / 2) - central(p, h)) / 3.0
     scale = np.abs(grad).max()
     np.testing.assert_allclose(grad[0], fd, rtol=1e-6, atol=1e-8 * scale)
+
+
+def test_hernquist_halo_gradient_and_domain(oracle_mod):
+    """halo_kind 1 (slot 13 = log10 R_h): dual gradient vs Richardson differences; c <= 0 is
+    no longer a domain limit."""
+    th = THETA.copy()
+    th[13] = 1.4                                    # log10 R_h = 1.4 (25 kpc)
+    g0 = gal_of(oracle_mod)
+    true = oracle_mod.maps(g0, th, halo_kind=1)
+    data, err, mask = synth.noisy_data(true, seed=12)
+    g = gal_of(oracle_mod, data=data.astype(np.float64), err=err.astype(np.float64), mask=mask)
+    t = th + np.random.default_rng(6).normal(size=th.size) * 0.02
+    logL, grad = oracle_mod.loglike_grad(g, t, halo_kind=1)
+    assert np.isfinite(logL[0])
+
+    def central(p, h):
+        tp, tm = t.copy(), t.copy()
+        tp[p] += h
+        tm[p] -= h
+        return (oracle_mod.loglike(g, tp, halo_kind=1)[0][0] - oracle_mod.loglike(g, tm, halo_kind=1)[0][0]) / (2 * h)
+
+    fd = np.array([(4 * central(p, 5e-5 * max(abs(t[p]), 1)) - central(p, 1e-4 * max(abs(t[p]), 1))) / 3
+                   for p in range(t.size)])
+    np.testing.assert_allclose(grad[0], fd, rtol=1e-6, atol=1e-8 * np.abs(grad).max())
+    neg = t.copy()
+    neg[13] = -0.5                                  # R_h = 0.3 kpc: valid for the Hernquist halo
+    assert np.isfinite(oracle_mod.loglike(g, neg, halo_kind=1)[0][0])
+    assert np.isneginf(oracle_mod.loglike(g, neg, halo_kind=0)[0][0])
