@@ -1,0 +1,144 @@
+"""Parameter estimation and model selection with the batched likelihood (Sec. 2.5, Sec. 3.1).
+
+The paper fits three models to one galaxy with nested sampling and compares their
+evidences: bulge + inner disc + outer disc ("B+D1+D2"), bulge + one disc ("B+D"), and
+bulge + one disc with priors that force a rotation-dominated disc (k > 0.7, (M/L)_d > 2.5,
+log10 M_b < 11.1).  All three share the dark halo.  This module runs that comparison on
+synthetic maps: the maps come from a B+D1+D2 galaxy and the noise follows the error model
+of Sec. 3.1.  The paper's galaxy data are not available.
+
+    python -m paper_2205_06819_gb300.fit [--nx 30 --oversample 3 --n-live 300 ...]
+
+prints one JSON line per model (ln Z, its error, the information H, likelihood calls,
+wall time, posterior medians and 16th / 84th percentiles) and the log Bayes factors.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import synth
+from .nested import BoxPrior, NestedSampler, gpu_loglike
+
+#: slots of the parameter vector (layout in synth)
+SLOT = {n: i for i, n in enumerate(synth.PARAM_NAMES_2)}
+
+
+def truth_two_discs() -> np.ndarray:
+    """A B+D1+D2 galaxy close to the paper's NGC 7683 posterior medians (inner disc of
+    scale ~1 kpc, outer disc ~4 kpc), centred in the field, Hernquist-limit bulge."""
+    th = synth.NGC7683_LIKE.copy()
+    th[0], th[1] = 0.05, -0.03
+    th[5] = math.log10(0.5)
+    return th
+
+
+def selection_box(model: str, truth: np.ndarray, free_geometry: bool = False) -> np.ndarray:
+    """[P, 2] prior box of one model: 'BD1D2' (19 slots), 'BD' or 'BD_rot' (15 slots).
+
+    Free: bulge mass, scale and M/L; each disc's mass, scale, k and M/L; with
+    ``free_geometry`` also P.A. and inclination.  Fixed at the truth: centre, gamma,
+    halo and systemic velocity (lo == hi).  The inner disc's scale is bounded above by the
+    outer disc's lower bound so that the two discs cannot swap.
+    """
+    P = 19 if model == "BD1D2" else 15
+    box = np.repeat(truth[:P, None], 2, axis=1).astype(np.float64)
+    box[SLOT["logMb"]] = (9.0, 11.5)
+    box[SLOT["logRb"]] = (-1.0, 0.5)
+    box[SLOT["MLb"]] = (0.5, 20.0)
+    box[SLOT["logMd1"]] = (9.0, 11.5)
+    box[SLOT["k1"]] = (0.0, 1.0)
+    box[SLOT["MLd1"]] = (0.1, 20.0)
+    if model == "BD1D2":
+        box[SLOT["logRd1"]] = (-0.5, 0.3)
+        box[SLOT["logMd2"]] = (9.0, 11.5)
+        box[SLOT["logRd2"]] = (0.3, 1.0)
+        box[SLOT["k2"]] = (0.0, 1.0)
+        box[SLOT["MLd2"]] = (0.1, 20.0)
+    else:
+        box[SLOT["logRd1"]] = (-0.5, 1.0)
+    if model == "BD_rot":                      # the paper's rotation-dominated priors
+        box[SLOT["k1"]] = (0.7, 1.0)
+        box[SLOT["MLd1"]] = (2.5, 20.0)
+        box[SLOT["logMb"]] = (9.0, 11.1)
+    if free_geometry:
+        box[SLOT["PA"]] = (truth[2] - 0.5, truth[2] + 0.5)
+        box[SLOT["inc"]] = (30 * synth.DEG, 70 * synth.DEG)
+    return box
+
+
+def make_galaxy(spec: synth.GalaxySpec, data, err, mask=None):
+    from .model import Galaxy
+    return Galaxy(spec.nx, spec.ny, spec.oversample, spec.psf_fwhm_arcsec, spec.kpc_per_arcsec, data, err, mask,
+                  spaxel_arcsec=spec.spaxel_arcsec, psf_kind=spec.psf_kind, moffat_beta=spec.moffat_beta)
+
+
+def synthetic_data(spec: synth.GalaxySpec, truth: np.ndarray, seed: int, n_quad: int = 64):
+    """Noisy [4, ny, nx] maps of a B+D1+D2 galaxy: noise-free maps from the CUDA forward
+    model (bang_model_maps), noise from synth.noisy_data."""
+    import torch
+    from .model import Model
+    ones = np.ones((4, spec.ny, spec.nx), np.float32)
+    m = Model(make_galaxy(spec, ones, ones), n_discs=2, n_quad=n_quad)
+    try:
+        true = m.maps(torch.from_numpy(truth[None, :].astype(np.float32)))[0].numpy().astype(np.float64)
+    finally:
+        m.close()
+    return synth.noisy_data(true, seed=seed)
+
+
+def run_model(model_name: str, spec, data, err, truth, n_live: int, batch: int, seed: int,
+              free_geometry: bool = False, frac: float = 0.01, n_quad: int = 64, slice_steps=None):
+    from .model import Model
+    box = selection_box(model_name, truth, free_geometry)
+    prior = BoxPrior(box, sin_slot=SLOT["inc"] if free_geometry else None)
+    m = Model(make_galaxy(spec, data, err), n_discs=2 if model_name == "BD1D2" else 1, n_quad=n_quad)
+    try:
+        t0 = time.perf_counter()
+        res = NestedSampler(gpu_loglike(m), prior, n_live=n_live, batch=batch, seed=seed, frac=frac,
+                            slice_steps=slice_steps).run()
+        wall = time.perf_counter() - t0
+    finally:
+        m.close()
+    q = res.quantiles([0.16, 0.5, 0.84])
+    names = synth.PARAM_NAMES_2 if model_name == "BD1D2" else synth.PARAM_NAMES_1
+    post = {names[j]: [round(float(q[1, j]), 4), round(float(q[2, j] - q[1, j]), 4),
+                       round(float(q[1, j] - q[0, j]), 4)] for j in prior.free}
+    return res, {"model": model_name, "logZ": res.logz, "logZ_err": res.logz_err, "H": res.information,
+                 "n_free": int(prior.ndim), "n_iter": res.n_iter, "n_like": res.n_like, "wall_s": wall,
+                 "evals_per_s": res.n_like / wall, "max_logL": float(res.log_l.max()),
+                 "posterior_median_plus_minus": post}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--nx", type=int, default=30)
+    ap.add_argument("--oversample", type=int, default=3)
+    ap.add_argument("--psf-fwhm", type=float, default=2.5)
+    ap.add_argument("--n-live", type=int, default=300)
+    ap.add_argument("--batch", type=int, default=30)
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--frac", type=float, default=0.01)
+    ap.add_argument("--free-geometry", action="store_true")
+    ap.add_argument("--models", default="BD1D2,BD,BD_rot")
+    a = ap.parse_args(argv)
+    spec = synth.GalaxySpec(a.nx, a.nx, a.oversample, a.psf_fwhm)
+    truth = truth_two_discs()
+    data, err, _ = synthetic_data(spec, truth, seed=a.seed)
+    out = {}
+    for name in a.models.split(","):
+        _, row = run_model(name, spec, data, err, truth, a.n_live, a.batch, a.seed, a.free_geometry, a.frac)
+        out[name] = row
+        print(json.dumps(row), flush=True)
+    if "BD1D2" in out:
+        print(json.dumps({"ln_bayes_factor_vs_BD1D2": {k: out["BD1D2"]["logZ"] - v["logZ"]
+                                                       for k, v in out.items() if k != "BD1D2"},
+                          "truth": {n: float(truth[i]) for i, n in enumerate(synth.PARAM_NAMES_2)}}))
+
+
+if __name__ == "__main__":
+    main()
