@@ -37,8 +37,8 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT_NOMINAL = 152
 SM_MAX_MHZ_NOMINAL = 2070.0
-# Per-SM issue rates measured on this GB300 (sm_103a) by a clock64 microbenchmark of
-# dependent-free chains of the PTX instructions ("Roofline").
+# Per-SM issue rates measured on GB300 (sm_103a) by a microbenchmark of independent
+# chains of each PTX instruction (ex2.approx issues at twice the rate of lg2.approx).
 MUFU_EX2_PER_CLK_SM = 32.0
 MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 128.0
@@ -65,6 +65,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain-form and adjoint side measurements")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (bang_model_tune) before timing")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="time only the first R rows of the workload's batch (small cases for ncu captures; "
+                         "not a headline number)")
+    ap.add_argument("--grad", action="store_true",
+                    help="time logL + gradient (bang_loglike_grad_batch) instead of logL")
+    ap.add_argument("--bulge-table", type=int, default=0,
+                    help="radial-table option with T radii (0: per-point quadrature, the method as defined)")
     return ap.parse_args()
 
 
@@ -127,13 +134,18 @@ def points_per_eval(spec: synth.GalaxySpec) -> int:
     return (spec.oversample * spec.nx + 2 * h) * (spec.oversample * spec.ny + 2 * h)
 
 
-def algorithmic_sfu_ops(wl: synth.Workload) -> float:
-    """Transcendental (SFU) operations of one batch: per padded fine point, one log2 and two
-    exp2 per radial quadrature node, plus 16 for the rest of the point (two square roots of
-    the radii, one of the velocity, the bulge, halo and disc powers, logarithms and
-    exponentials, and the reciprocals of the light weighting)."""
-    pts = sum(points_per_eval(g) for g in wl.galaxies) * wl.rows_per_galaxy
-    return float(pts) * (3 * wl.n_quad + 16)
+def algorithmic_sfu_ops(wl: synth.Workload, gal_idx=None, rows: int | None = None) -> float:
+    """Transcendental (SFU) operations of one batch: per padded fine point, one log2 and one
+    exp2 per radial quadrature node (q^(g-4) by lg2 + ex2; q^(2g-7) = (q^(g-4))^2 q by
+    multiplications), plus 16 for the rest of the point (two square roots of the radii, one
+    of the velocity, the bulge, halo and disc powers, logarithms and exponentials, and the
+    reciprocals of the light weighting)."""
+    if rows is None:
+        pts = sum(points_per_eval(g) for g in wl.galaxies) * wl.rows_per_galaxy
+    else:
+        per = [points_per_eval(g) for g in wl.galaxies]
+        pts = sum(per[0 if gal_idx is None else int(gal_idx[b])] for b in range(rows))
+    return float(pts) * (2 * wl.n_quad + 16)
 
 
 def combine_max(local: float, dist, device) -> float:
@@ -153,8 +165,8 @@ def rank_batch_seed(workload_id: int, rank: int) -> int:
 
 
 def sfu_peak_ops_per_s(n_quad: int, mhz: float, sms: int) -> float:
-    """Peak transcendental rate for the radial-rule mix (one lg2 per two ex2)."""
-    per_op_clk = (1.0 / MUFU_LG2_PER_CLK_SM + 2.0 / MUFU_EX2_PER_CLK_SM) / 3.0   # SM-clocks per op
+    """Peak transcendental rate for the radial-rule mix (one lg2 per ex2)."""
+    per_op_clk = (1.0 / MUFU_LG2_PER_CLK_SM + 1.0 / MUFU_EX2_PER_CLK_SM) / 2.0   # SM-clocks per op
     return sms * mhz * 1e6 / per_op_clk
 
 
@@ -366,11 +378,24 @@ def run_ours(args):
     from paper_2205_06819_gb300 import build as bmod
     bmod.build()
     wl = synth.workload(args.workload)
-    model, gals, theta_np, gal_idx = make_model(wl, rank, torch)
+    model, gals, theta_np, gal_idx = make_model(wl, rank, torch, bulge_table=args.bulge_table)
     gal = gals[0]
+    B_full = theta_np.shape[0]
+    if args.rows:
+        theta_np = np.ascontiguousarray(theta_np[:args.rows])
+        gal_idx = None if gal_idx is None else np.ascontiguousarray(gal_idx[:args.rows])
     if not args.no_tune:
         model.tune(theta_np.shape[0], gal_idx)
     B, P = theta_np.shape
+    if args.grad:
+        def call(th, out):
+            return model.loglike_grad(th, gal_idx)
+    else:
+        def call(th, out):
+            return model.loglike(th, gal_idx, out=out)
+    # kernels per step: decode, forward, finalize (+ the table kernel; + adjoint and gradient map)
+    launches_per_step = 3 + (1 if args.bulge_table else 0) + (2 if args.grad else 0)
+    headline = not (args.rows or args.grad or args.bulge_table)
     theta = torch.from_numpy(theta_np).cuda()
     logL = torch.empty(B, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -381,7 +406,7 @@ def run_ours(args):
             dist.barrier()
 
     for _ in range(args.warmup):
-        model.loglike(theta, gal_idx, out=logL)
+        call(theta, logL)
     torch.cuda.synchronize()
 
     # device-timed steps (L2 flushed between steps, outside the events)
@@ -396,7 +421,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         starts[k].record(stream)
-        model.loglike(theta, gal_idx, out=logL)
+        res = call(theta, logL)
         ends[k].record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -405,20 +430,20 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_s = combine_max(sum(step_ms) / 1e3, dist, "cuda")
     value = ws * B * args.steps / dev_s
-    assert np.isfinite(logL.cpu().numpy()).any()
+    assert np.isfinite((res[0] if args.grad else logL).cpu().numpy()).any()
 
     # end to end through the C ABI with pinned host buffers
     th_host = torch.from_numpy(theta_np).pin_memory()
     out_host = torch.empty(B, dtype=torch.float64).pin_memory()
     for _ in range(2):
-        model.loglike(th_host, gal_idx, out=out_host)
+        call(th_host, out_host)
     e2e_t = []
     barrier()
     for k in range(max(3, args.steps // 4)):
         flush.fill_(k & 0xff)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        model.loglike(th_host, gal_idx, out=out_host)
+        call(th_host, out_host)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = combine_max(sum(e2e_t), dist, "cuda")
     e2e_value = ws * B * len(e2e_t) / e2e_s
@@ -432,31 +457,38 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL))
     step_s = dev_s / args.steps
-    ops = algorithmic_sfu_ops(wl)
+    ops = algorithmic_sfu_ops(wl, gal_idx, B)
     achieved = ops / step_s / 1e9
     peak = sfu_peak_ops_per_s(wl.n_quad, mhz, sms) / 1e9
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["stamp"] == kernel_stamp() else None
 
+    metric = "logL+gradient evals/s" if args.grad else "logL evals/s"
     line = {
-        "metric": "logL evals/s", "value": value, "unit": "logL evals/s", "n_gpus": ws, "steps": args.steps,
+        "metric": metric, "value": value, "unit": metric, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{wl.name}: {wl.description}", "rows": B,
+        "config": {"workload": f"{wl.name}: {wl.description}", "rows": B, "rows_of_workload": B_full,
+                   "path": ("logL + gradient" if args.grad else "logL")
+                   + (f", radial table T={args.bulge_table}" if args.bulge_table else ""),
                    "padded_fine_points_per_row": points_per_eval(wl.galaxies[0]) if len(wl.galaxies) == 1 else
                    "per galaxy", "n_quad": wl.n_quad, "galaxies": len(wl.galaxies),
                    "l2": "flushed between steps (256 MiB write outside the timed events)"},
-        "e2e": {"value": e2e_value, "unit": "logL evals/s", "h2d_bytes_per_step": int(B * P * 4),
-                "d2h_bytes_per_step": int(B * 8)},
-        "gpu_launches": 2 * args.steps,
+        "e2e": {"value": e2e_value, "unit": metric, "h2d_bytes_per_step": int(B * P * 4),
+                "d2h_bytes_per_step": int(B * 8 + (B * P * 4 if args.grad else 0))},
+        "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SFU op/s", "frac": achieved / peak,
                      "traffic": traffic,
                      "peak_basis": f"{sms} SMs x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz) x measured per-SM rates "
                                    f"lg2 {MUFU_LG2_PER_CLK_SM:.0f}/clk, ex2 {MUFU_EX2_PER_CLK_SM:.0f}/clk for the "
-                                   "radial-rule mix (1 lg2 : 2 ex2)"},
+                                   "radial-rule mix (1 lg2 : 1 ex2)"},
         "clocks": clk,
         "wall_s_timed": wall,
     }
-    if ws == 1 and not args.no_extras and len(wl.galaxies) == 1:
+    if not headline:
+        line["note"] = "profiling case (--rows / --grad / --bulge-table), not the headline configuration"
+        if args.grad or args.bulge_table:
+            line["roofline"] = None        # the SFU count above is the forward per-point quadrature's
+    if ws == 1 and headline and not args.no_extras and len(wl.galaxies) == 1:
         line["plain_gpu"] = time_plain(model, theta, logL, B)
         line["fwd_adjoint"] = time_adjoint(torch)
         line["radial_table"] = time_table(wl, torch)

@@ -99,11 +99,14 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
       asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
                    : "=f"(wk.x), "=f"(wk.y)
                    : "r"((unsigned)__cvta_generic_to_shared(nw + k)));
-      t1 = wk.x * ex2_approx(m.g4 * d);
-      t2 = wk.y * ex2_approx(m.g7 * d);
+      const float e = ex2_approx(m.g4 * d);          // q^(g-4); q^(2g-7) = e^2 q
+      t1 = wk.x * e;
+      t2 = (wk.y * e) * (e * q);
     } else {
-      t1 = kNodeWs[base + k] * ex2_approx(fmaf(m.g4, d, m.ngam * lc));
-      t2 = kNodeWq[base + k] * ex2_approx(fmaf(m.g7, d, m.g3 * lc));
+      const float E = ex2_approx(fmaf(m.g4, d, m.ngam * lc));   // c^-g q^(g-4)
+      const float c = kNodeCm1[base + k] + 1.0f;
+      t1 = kNodeWs[base + k] * E;
+      t2 = (kNodeWq[base + k] * E) * (E * (c * c) * (c * q));
     }
     const float lu = (lw + lc) - d;                  // log2 u_k, u_k = r_k / (r_k + a)
     const float u = ex2_approx(lu);

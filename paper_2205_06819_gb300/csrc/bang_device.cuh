@@ -59,7 +59,7 @@ struct ModelConst {
   float cpa, spa;          // cos, sin of the position angle
   float inv_ci, si;        // 1 / cos i, sin i
   // bulge (Dehnen): a, gamma
-  float inv_a, ngam, g4, g7, g3, three_mg;
+  float inv_a, ngam, g4, g3, three_mg;
   float cS, cQ, vb_c;      // Sigma = cS x pS S; Sigma sigma^2 = cQ pQ Q; vb^2 = vb_c u^(3-g) / (r/a)
   float Lb;                // 1e-6 / (M/L)_b
   // halo (NFW)
@@ -119,7 +119,6 @@ __device__ inline int decode_model(const float* __restrict__ th, int nd, int hal
   m.inv_a = (float)(1.0 / a);
   m.ngam = (float)(-gam);
   m.g4 = (float)(gam - 4.0);
-  m.g7 = (float)(2.0 * gam - 7.0);
   m.g3 = (float)(3.0 - 2.0 * gam);
   m.three_mg = (float)(3.0 - gam);
   m.cS = (float)((3.0 - gam) * Mb / (2.0 * kPi * a * a));
@@ -252,8 +251,10 @@ __device__ __forceinline__ float halo_v2(const ModelConst& m, float r, float inv
 // With x = R / a, w = x / (x + 1) and node k at r = R cosh t_k:
 //   rho(r) r^-1-part:  (x c)^-g (x c + 1)^(g-4) = x^-g (x+1)^(g-4) * c^-g q^(g-4),  q = 1 + w (c - 1)
 //   rho M part:        (x c)^(3-2g) (x c + 1)^(2g-7) = x^(3-2g) (x+1)^(2g-7) * c^(3-2g) q^(2g-7)
-// so each node costs one lg2 and two ex2 of small arguments; the large per-point powers are
-// taken once, accurately, outside the sum.
+// and q^(2g-7) = (q^(g-4))^2 q, so each node costs one lg2 and one ex2 of small arguments
+// plus multiplications; the large per-point powers are taken once, accurately, outside the
+// sum.  The products are grouped as (W E)(E c^3 q) so that no intermediate leaves the float
+// range while its term still matters.
 template <int NQ>
 __device__ __forceinline__ void bulge_projected(const ModelConst& m, float R, float& Sigma, float& SigS2) {
   constexpr int base = NodeBase<NQ>::value;
@@ -268,12 +269,13 @@ __device__ __forceinline__ void bulge_projected(const ModelConst& m, float R, fl
   float S = 0.f, Q = 0.f;
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
-    const float q = fmaf(w, kNodeCm1[base + k], 1.0f);
+    const float cm1 = kNodeCm1[base + k];
+    const float q = fmaf(w, cm1, 1.0f);
     const float d = lg2_approx(q);
-    const float e1 = fmaf(m.g4, d, m.ngam * kNodeLc[base + k]);
-    const float e2 = fmaf(m.g7, d, m.g3 * kNodeLc[base + k]);
-    S = fmaf(kNodeWs[base + k], ex2_approx(e1), S);
-    Q = fmaf(kNodeWq[base + k], ex2_approx(e2), Q);
+    const float E = ex2_approx(fmaf(m.g4, d, m.ngam * kNodeLc[base + k]));   // c^-g q^(g-4)
+    const float c = cm1 + 1.0f;
+    S = fmaf(kNodeWs[base + k], E, S);
+    Q = fmaf(kNodeWq[base + k] * E, E * (c * c) * (c * q), Q);
   }
   Sigma = m.cS * x * pS * S;
   SigS2 = m.cQ * pQ * Q;
@@ -332,8 +334,8 @@ __device__ __forceinline__ float table_plain(const float* __restrict__ tab, int 
 
 // The same sums with the per-model node factors folded into weights staged in shared
 // memory: nw[k] = (w_k cosh t_k c_k^-g, w_k tanh^2 t_k c_k^(3-2g)), so a node needs one
-// 64-bit shared load instead of two multiplications, and its exponents (g - 4) d and
-// (2g - 7) d are smaller.
+// 64-bit shared load, one lg2 and one ex2: e = q^(g-4) gives both q^(g-4) and
+// q^(2g-7) = e^2 q.
 template <int NQ>
 __device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const float2* __restrict__ nw, float R,
                                                   float& Sigma, float& SigS2) {
@@ -349,13 +351,15 @@ __device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const flo
   float S = 0.f, Q = 0.f;
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
-    const float d = lg2_approx(fmaf(w, kNodeCm1[base + k], 1.0f));
+    const float q = fmaf(w, kNodeCm1[base + k], 1.0f);
+    const float d = lg2_approx(q);
     float2 wk;   // kept in the loop: hoisting 2 NQ invariant weights would exhaust the registers
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
                  : "=f"(wk.x), "=f"(wk.y)
                  : "r"((unsigned)__cvta_generic_to_shared(nw + k)));
-    S = fmaf(wk.x, ex2_approx(m.g4 * d), S);
-    Q = fmaf(wk.y, ex2_approx(m.g7 * d), Q);
+    const float e = ex2_approx(m.g4 * d);
+    S = fmaf(wk.x, e, S);
+    Q = fmaf(wk.y * e, e * q, Q);
   }
   Sigma = m.cS * x * pS * S;
   SigS2 = m.cQ * pQ * Q;
