@@ -25,6 +25,8 @@
 // float64 accumulators; the per-model constants are mapped to theta in float64.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "bang_device.cuh"
 #include "bang_internal.h"
 
@@ -287,11 +289,13 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   acc[A_PA] += gxr * yr - gyr * xr;
 }
 
-// d logL / d theta from the reduced constant adjoints (float64, one thread).
-__device__ void constants_to_theta(const float* __restrict__ th, int nd, int halo_kind, const double* s, double* g) {
+// d logL / d theta from the reduced constant adjoints and the row's decode terms T
+// (float64, one thread).
+__device__ void constants_to_theta(const float* __restrict__ th, const double* T, int nd, int halo_kind,
+                                   const double* s, double* g) {
   const double ln10 = 2.302585092994045684;
-  const double ci = cos((double)th[3]), si = sin((double)th[3]);
-  const double a = pow(10.0, (double)th[5]);
+  const double ci = T[0], si = T[1];
+  const double a = T[5];
   g[0] = -s[A_X0];
   g[1] = -s[A_Y0];
   g[2] = s[A_PA];
@@ -301,14 +305,13 @@ __device__ void constants_to_theta(const float* __restrict__ th, int nd, int hal
   g[6] = s[A_G];
   g[10] = -s[A_LB] * (1e-6 / th[10]) / th[10];
   if (halo_kind == 0) {   // NFW: vh_c = G M200 / m(c), 1/rs = c / r200(M200)
-    const double M200 = pow(10.0, (double)th[12]), c = th[13];
-    const double r200 = cbrt(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit));
-    const double mc = log1p(c) - c / (1.0 + c), dmc = c / ((1.0 + c) * (1.0 + c));
+    const double M200 = T[6], c = th[13], r200 = T[7], mc = T[8];
+    const double dmc = c / ((1.0 + c) * (1.0 + c));
     const double vh_c = kG * M200 / mc, inv_rs = c / r200;
     g[12] = ln10 * (s[A_VHC] * vh_c - s[A_IRS] * inv_rs / 3.0);
     g[13] = -s[A_VHC] * vh_c * dmc / mc + s[A_IRS] * inv_rs / c;
   } else {                // Hernquist: vh_c = G M_h / R_h, 1/rs = 1 / R_h
-    const double Mh = pow(10.0, (double)th[12]), Rh = pow(10.0, (double)th[13]);
+    const double Mh = T[6], Rh = T[7];
     const double vh_c = kG * Mh / Rh, inv_rs = 1.0 / Rh;
     g[12] = ln10 * s[A_VHC] * vh_c;
     g[13] = -ln10 * (s[A_VHC] * vh_c + s[A_IRS] * inv_rs);
@@ -316,7 +319,7 @@ __device__ void constants_to_theta(const float* __restrict__ th, int nd, int hal
   for (int j = 0; j < nd; ++j) {
     const double* dj = s + A_D0 + kPerDisc * j;
     const int o = j == 0 ? 7 : 15;
-    const double Md = pow(10.0, (double)th[o]), Rd = pow(10.0, (double)th[o + 1]), k = th[o + 2];
+    const double Md = T[9 + 2 * j], Rd = T[10 + 2 * j], k = th[o + 2];
     const double ml = j == 0 ? th[11] : th[18];
     const double Sd_c = Md / (2.0 * kPi * Rd * Rd * ci), vd_c = 2.0 * kG * Md / Rd;
     g[o] = ln10 * (dj[D_SDC] * Sd_c + dj[D_VDC] * vd_c);
@@ -469,18 +472,26 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
   }
 }
 
-// One thread per row: the reduced constant adjoints -> d logL / d theta (float64), or zero
-// for a row outside the parameter domain.
+// One warp per row: the reduced constant adjoints -> d logL / d theta (float64), or zero
+// for a row outside the parameter domain.  As in decode_kernel, lane i < kDecodeTerms
+// evaluates decode term i and lane 0 does the rest.
 __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind,
-                                const double* __restrict__ acc, int B, float* __restrict__ grad) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+                                const double* __restrict__ acc, int B, double l10k, float* __restrict__ grad) {
+  const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;   // whole warps
   const float* th = theta + (size_t)b * P;
+  const bool ok = theta_in_domain(th, nd, halo_kind);
+  const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
+  double T[kDecodeTerms];
+#pragma unroll
+  for (int i = 0; i < kDecodeTerms; ++i) T[i] = __shfl_sync(0xffffffffu, v, i);
+  if (lane != 0) return;
   double g[kMaxParams];
   for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
-  if (theta_in_domain(th, nd, halo_kind)) {
+  if (ok) {
     const double* s = acc + (size_t)b * kGradAccStride;
-    constants_to_theta(th, nd, halo_kind, s, g);
+    constants_to_theta(th, T, nd, halo_kind, s, g);
     g[14] = s[24];
   }
   for (int p = 0; p < P; ++p) grad[(size_t)b * P + p] = (float)g[p];
@@ -596,7 +607,11 @@ cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const in
 
 cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, const double* acc, int B,
                             float* grad, cudaStream_t st) {
-  grad_out_kernel<<<(B + 63) / 64, 64, 0, st>>>(theta, P, n_discs, halo_kind, acc, B, grad);
+  constexpr int kRowsPerBlock = 4;   // 4 warps, one row each
+  const double l10k = std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit));
+  grad_out_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(theta, P, n_discs,
+                                                                                          halo_kind, acc, B, l10k,
+                                                                                          grad);
   return cudaGetLastError();
 }
 

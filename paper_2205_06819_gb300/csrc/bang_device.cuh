@@ -100,22 +100,56 @@ __device__ inline bool theta_in_domain(const float* __restrict__ th, int nd, int
   return true;
 }
 
-__device__ inline int decode_model(const float* __restrict__ th, int nd, int halo_kind, const GalDev& g,
-                                   ModelConst& m) {
-  const int np = nd == 2 ? 19 : 15;
-  if (!theta_in_domain(th, nd, halo_kind)) return 0;
-  double t[kMaxParams];
-  for (int i = 0; i < np; ++i) t[i] = (double)th[i];
+// The transcendental parts of the decode, independent of one another, so that a warp can
+// take one per lane (decode_kernel) or one thread all of them in turn (decode_model):
+//   0 cos i, 1 sin i, 2 cos PA, 3 sin PA, 4 M_b, 5 a, 6 M_200 (or M_h),
+//   7 r_200 = (3 M_200 / (4 pi 200 rho_c))^(1/3) (or R_h), 8 m(c) = ln(1 + c) - c / (1 + c)
+//   (NFW only), 9 M_d1, 10 R_d1, 11 M_d2, 12 R_d2.
+// They reduce to three functions so that the lanes of a warp diverge into three paths, not
+// thirteen: sin (cos x = sin(x + pi/2)), 10^x (r_200 = 10^((log10 M_200 + l10k) / 3) with
+// l10k = log10(3 / (4 pi 200 rho_c))) and ln(1 + c).
+constexpr int kDecodeTerms = 13;
 
-  const double ci = cos(t[3]), si = sin(t[3]);
-  m.X0 = (float)(g.xoff_kpa - t[0]);
-  m.Y0 = (float)(g.yoff_kpa - t[1]);
-  m.cpa = (float)cos(t[2]);
-  m.spa = (float)sin(t[2]);
+__device__ inline double decode_l10k() { return log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit)); }
+
+__device__ inline double decode_term(int i, const float* __restrict__ th, int nd, int halo_kind, double l10k) {
+  int kind = 1;   // 0 sin, 1 10^x, 2 ln(1 + x) - x / (1 + x), 3 unused
+  double x = 0.0;
+  switch (i) {
+    case 0: kind = 0; x = (double)th[3] + 0.5 * kPi; break;
+    case 1: kind = 0; x = th[3]; break;
+    case 2: kind = 0; x = (double)th[2] + 0.5 * kPi; break;
+    case 3: kind = 0; x = th[2]; break;
+    case 4: x = th[4]; break;
+    case 5: x = th[5]; break;
+    case 6: x = th[12]; break;
+    case 7: x = halo_kind == 0 ? ((double)th[12] + l10k) / 3.0 : (double)th[13]; break;
+    case 8: kind = halo_kind == 0 ? 2 : 3; x = th[13]; break;
+    case 9: x = th[7]; break;
+    case 10: x = th[8]; break;
+    case 11: kind = nd == 2 ? 1 : 3; x = th[15]; break;
+    case 12: kind = nd == 2 ? 1 : 3; x = th[16]; break;
+    default: kind = 3;
+  }
+  if (kind == 0) return sin(x);
+  if (kind == 1) return exp10(x);
+  if (kind == 2) return log1p(x) - x / (1.0 + x);
+  return 0.0;
+}
+
+// The per-model constants from theta and its decode terms T[kDecodeTerms] (float64
+// arithmetic, rounded to float32 once).
+__device__ inline void decode_finish(const float* __restrict__ th, const double* T, int nd, int halo_kind,
+                                     const GalDev& g, ModelConst& m) {
+  const double ci = T[0], si = T[1];
+  m.X0 = (float)(g.xoff_kpa - (double)th[0]);
+  m.Y0 = (float)(g.yoff_kpa - (double)th[1]);
+  m.cpa = (float)T[2];
+  m.spa = (float)T[3];
   m.inv_ci = (float)(1.0 / ci);
   m.si = (float)si;
   // bulge
-  const double Mb = pow(10.0, t[4]), a = pow(10.0, t[5]), gam = t[6];
+  const double Mb = T[4], a = T[5], gam = th[6];
   m.inv_a = (float)(1.0 / a);
   m.ngam = (float)(-gam);
   m.g4 = (float)(gam - 4.0);
@@ -124,17 +158,15 @@ __device__ inline int decode_model(const float* __restrict__ th, int nd, int hal
   m.cS = (float)((3.0 - gam) * Mb / (2.0 * kPi * a * a));
   m.cQ = (float)(kG * (3.0 - gam) * Mb * Mb / (2.0 * kPi * a * a * a));
   m.vb_c = (float)(kG * Mb / a);
-  m.Lb = (float)(1e-6 / t[10]);
+  m.Lb = (float)(1e-6 / (double)th[10]);
   // halo
   m.hern = halo_kind;
   if (halo_kind == 0) {   // NFW: vh^2 = vh_c m(r/rs) / r
-    const double M200 = pow(10.0, t[12]), c = t[13];
-    const double r200 = cbrt(3.0 * M200 / (4.0 * kPi * 200.0 * kRhoCrit));
-    const double mc = log1p(c) - c / (1.0 + c);
+    const double M200 = T[6], c = th[13], r200 = T[7], mc = T[8];
     m.inv_rs = (float)(c / r200);
     m.vh_c = (float)(kG * M200 / mc);
   } else {                // Hernquist (Eq. 2 with M_h, R_h): vh^2 = vh_c x / (1 + x)^2, x = r / R_h
-    const double Mh = pow(10.0, t[12]), Rh = pow(10.0, t[13]);
+    const double Mh = T[6], Rh = T[7];
     m.inv_rs = (float)(1.0 / Rh);
     m.vh_c = (float)(kG * Mh / Rh);
   }
@@ -145,8 +177,8 @@ __device__ inline int decode_model(const float* __restrict__ th, int nd, int hal
       continue;
     }
     const int o = j == 0 ? 7 : 15;
-    const double Md = pow(10.0, t[o]), Rd = pow(10.0, t[o + 1]), k = t[o + 2];
-    const double ml = j == 0 ? t[11] : t[18];
+    const double Md = T[9 + 2 * j], Rd = T[10 + 2 * j], k = th[o + 2];
+    const double ml = j == 0 ? th[11] : th[18];
     m.inv_Rd[j] = (float)(1.0 / Rd);
     m.half_inv_Rd[j] = (float)(0.5 / Rd);
     m.vd_c[j] = (float)(2.0 * kG * Md / Rd);
@@ -155,7 +187,17 @@ __device__ inline int decode_model(const float* __restrict__ th, int nd, int hal
     m.ks[j] = (float)(-k * si);
     m.omk[j] = (float)((1.0 - k * k) / 3.0);
   }
-  m.vsys = (float)t[14];
+  m.vsys = th[14];
+}
+
+// theta -> per-model constants by one thread; 0 for a row outside the domain.
+__device__ inline int decode_model(const float* __restrict__ th, int nd, int halo_kind, const GalDev& g,
+                                   ModelConst& m) {
+  if (!theta_in_domain(th, nd, halo_kind)) return 0;
+  double T[kDecodeTerms];
+  const double l10k = decode_l10k();
+  for (int i = 0; i < kDecodeTerms; ++i) T[i] = decode_term(i, th, nd, halo_kind, l10k);
+  decode_finish(th, T, nd, halo_kind, g, m);
   return 1;
 }
 

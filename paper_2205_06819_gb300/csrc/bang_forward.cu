@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "bang_device.cuh"
@@ -256,13 +257,28 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
 }
 
 // One thread per row: theta -> per-model constants (float64 decode), against the row's galaxy.
+// One warp per row: lane i < kDecodeTerms evaluates decode term i (the float64
+// transcendentals are independent), lane 0 gathers them and finishes the row, so a row
+// costs the latency of one transcendental instead of thirteen in a chain.
 __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind,
                               const GalDev* __restrict__ gals, const int* __restrict__ row_g, int B,
-                              ModelConst* __restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+                              double l10k, ModelConst* __restrict__ out) {
+  const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;   // whole warps: b is uniform across the warp
+  const float* th = theta + (size_t)b * P;
+  const bool ok = theta_in_domain(th, nd, halo_kind);
+  const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
+  double T[kDecodeTerms];
+#pragma unroll
+  for (int i = 0; i < kDecodeTerms; ++i) T[i] = __shfl_sync(0xffffffffu, v, i);
+  if (lane != 0) return;
   ModelConst m;
-  m.valid = decode_model(theta + (size_t)b * P, nd, halo_kind, gals[row_g[b]], m);
+  m.valid = 0;
+  if (ok) {
+    decode_finish(th, T, nd, halo_kind, gals[row_g[b]], m);
+    m.valid = 1;
+  }
   out[b] = m;
 }
 
@@ -340,7 +356,10 @@ size_t model_const_bytes() { return sizeof(ModelConst); }
 
 cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
                           int B, ModelConst* out, cudaStream_t st) {
-  decode_kernel<<<(B + 63) / 64, 64, 0, st>>>(theta, P, n_discs, halo_kind, gals, row_g, B, out);
+  constexpr int kRowsPerBlock = 4;   // 4 warps of 32 lanes, one row each
+  const double l10k = std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit));
+  decode_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(theta, P, n_discs, halo_kind,
+                                                                                       gals, row_g, B, l10k, out);
   return cudaGetLastError();
 }
 
