@@ -44,7 +44,7 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 128.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "f00e17775df1cf07", "bytes_per_launch": 458240}
+NCU_TRAFFIC = {"stamp": "f3c01e63c21af6cf", "bytes_per_launch": 562688}
 
 
 def kernel_stamp() -> str:

@@ -84,11 +84,11 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
   const float w = x / xp1;
-  const float lw = log2f(w);
-  const float i2 = 1.0f / (xp1 * xp1);
+  const float lw = lg2_approx(w);
+  const float i2 = rcp_approx(xp1 * xp1);
   const float ip4 = i2 * i2;
-  const float pS = exp2f(m.ngam * lw) * ip4;
-  const float pQ = exp2f(m.g3 * lw) * ip4;
+  const float pS = ex2_approx(m.ngam * lw) * ip4;
+  const float pQ = ex2_approx(m.g3 * lw) * ip4;
   float S = 0.f, Su = 0.f, Sl = 0.f, Q = 0.f, Qu = 0.f, Ql = 0.f;
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
@@ -121,12 +121,12 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
   }
   const float fS = m.cS * x * pS, fQ = m.cQ * pQ;
   const float g = -m.ngam;
-  const float inv3g = 1.0f / m.three_mg;
+  const float inv3g = rcp_approx(m.three_mg);
   BulgeDer o;
   o.Sb = fS * S;
   o.Qb = fQ * Q;
   const float SU = fS * Su, SL = fS * Sl * kLn2, QU = fQ * Qu, QL = fQ * Ql * kLn2;
-  const float iR = 1.0f / R;
+  const float iR = rcp_approx(R);
   o.dSb_dR = ((1.0f - g) * o.Sb + (g - 4.0f) * SU) * iR;
   o.dSb_da = ((g - 3.0f) * o.Sb + (4.0f - g) * SU) * m.inv_a;
   o.dSb_dg = -o.Sb * inv3g - SL;
@@ -168,19 +168,19 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float yd = yr * m.inv_ci;
   const float r2 = fmaf(xr, xr, yd * yd);
   const bool Rfree = R2 > kR2Floor, rfree = r2 > kR2Floor;
-  const float R = sqrtf(fmaxf(R2, kR2Floor));
-  const float r = sqrtf(fmaxf(r2, kR2Floor));
-  const float inv_r = 1.0f / r;
+  const float R = sqrt_approx(fmaxf(R2, kR2Floor));
+  const float r = sqrt_approx(fmaxf(r2, kR2Floor));
+  const float inv_r = rcp_approx(r);
   const float cphi = xr * inv_r;
 
   const BulgeDer bd = tab ? bulge_table_vjp(m, tab, T, R) : bulge_projected_vjp<NQ>(m, R, nodew);
 
   const float xa = r * m.inv_a;
-  const float ub = xa / (xa + 1.0f);
-  const float lub = log2f(ub);
-  const float vb2 = m.vb_c * exp2f(m.three_mg * lub) / xa;
+  const float ub = xa * rcp_approx(xa + 1.0f);
+  const float lub = lg2_approx(ub);
+  const float vb2 = __fdividef(m.vb_c * ex2_approx(m.three_mg * lub), xa);
   const float xh = r * m.inv_rs;
-  const float ixh1 = __frcp_rn(1.0f + xh);
+  const float ixh1 = rcp_approx(1.0f + xh);
   // NFW: vh2 = vh_c m(x) / r; Hernquist: vh2 = vh_c h(x), h = x / (1 + x)^2
   const float mh = m.hern ? xh * ixh1 * ixh1 : nfw_m(xh);
   const float vh2 = m.hern ? m.vh_c * mh : m.vh_c * mh * inv_r;
@@ -190,10 +190,10 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   for (int j = 0; j < ND; ++j) {
     disc_F_d(r * m.half_inv_Rd[j], Fd[j], dFd[j]);
     vint2 = fmaf(m.vd_c[j], Fd[j], vint2);
-    ex[j] = expf(-r * m.inv_Rd[j]);
+    ex[j] = ex2_approx(-r * m.inv_Rd[j] * 1.44269504f);
     Sd[j] = m.Sd_c[j] * ex[j];
   }
-  const float vint = sqrtf(vint2);
+  const float vint = sqrt_approx(vint2);
   float B = bd.Sb * m.Lb, Bv = 0.f, Bs2 = bd.Qb * m.Lb, Stot = bd.Sb;
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
@@ -203,16 +203,16 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
     Bs2 = fmaf(Bd, m.omk[j] * vint2, Bs2);
     Stot += Sd[j];
   }
-  const float iB = 1.0f / B;
+  const float iB = rcp_approx(B);
   const float f1 = Bv * iB;
-  const float f2 = sqrtf(Bs2 * iB);
-  const float iS = 1.0f / Stot;
+  const float f2 = sqrt_approx(Bs2 * iB);
+  const float iS = rcp_approx(Stot);
   const float f3 = B * 1e6f * iS;
 
   // ---- reverse
   const float gB = a.x - a.y * f1 * iB - 0.5f * a.z * f2 * iB + a.w * f3 * iB;
   const float gBv = a.y * iB;
-  const float gBs2 = f2 > 0.f ? 0.5f * a.z / (f2 * B) : 0.f;
+  const float gBs2 = f2 > 0.f ? __fdividef(0.5f * a.z, f2 * B) : 0.f;
   const float gStot = -a.w * f3 * iS;
   const float gSb = fmaf(gB, m.Lb, gStot);
   const float gQb = gBs2 * m.Lb;
@@ -234,7 +234,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
     gr -= gSd * Sd[j] * m.inv_Rd[j];
     dj[D_IRD] -= gSd * Sd[j] * r;
   }
-  gvint2 += 0.5f * gvint / vint;
+  gvint2 += __fdividef(0.5f * gvint, vint);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     float* dj = acc + A_D0 + kPerDisc * j;
@@ -280,7 +280,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   float gX = gxr * m.cpa - gyr * m.spa;
   float gY = gxr * m.spa + gyr * m.cpa;
   if (Rfree) {
-    const float iR = 1.0f / R;
+    const float iR = rcp_approx(R);
     gX = fmaf(gR * iR, X, gX);
     gY = fmaf(gR * iR, Y, gY);
   }

@@ -81,6 +81,20 @@ __device__ __forceinline__ float lg2_approx(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// SFU reciprocal and square root (about 1 ulp, flush-to-zero).  The forward model's
+// per-point reciprocals, divisions, square roots, exp and log use these single MUFU
+// operations instead of the correctly rounded sequences: the node loop leaves the SFU room
+// while instruction issue is the limit, and the change moves logL by < 2e-7 relative.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Decode row theta (float32) into per-model constants.  Returns 0 when the row is outside
 // the parameter domain (non-finite, i not in [0, pi/2), gamma not in [0, 3), |k| > 1,
@@ -211,9 +225,9 @@ __device__ __forceinline__ float disc_F(float y) {
       P = fmaf(P, s, kDiscP[k]);
       Q = fmaf(Q, s, kDiscQ[k]);
     }
-    return s * (P - logf(y) * Q);
+    return s * (P - lg2_approx(y) * 0.693147181f * Q);
   }
-  const float u = __frcp_rn(y);
+  const float u = rcp_approx(y);
   const int e = (int)((__float_as_uint(u) >> 23) & 0xff) - 127;   // u in [2^e, 2^(e+1))
   int k = -e - 1;
   k = k < 0 ? 0 : (k > BANG_DISC_NPIECE_B - 1 ? BANG_DISC_NPIECE_B - 1 : k);
@@ -238,12 +252,12 @@ __device__ __forceinline__ void disc_F_d(float y, float& F, float& dF) {
       P = fmaf(P, s, kDiscP[k]);
       Q = fmaf(Q, s, kDiscQ[k]);
     }
-    const float ly = logf(y);
+    const float ly = lg2_approx(y) * 0.693147181f;
     F = s * (P - ly * Q);
     dF = 2.0f * y * (P + s * dP - ly * (Q + s * dQ) - 0.5f * Q);
     return;
   }
-  const float u = __frcp_rn(y);
+  const float u = rcp_approx(y);
   const int e = (int)((__float_as_uint(u) >> 23) & 0xff) - 127;
   int k = -e - 1;
   k = k < 0 ? 0 : (k > BANG_DISC_NPIECE_B - 1 ? BANG_DISC_NPIECE_B - 1 : k);
@@ -263,7 +277,7 @@ __device__ __forceinline__ void disc_F_d(float y, float& F, float& dF) {
 // m = 2 z^2 / (1 + z) + 2 z^3 (1/3 + z^2/5 + z^4/7 + ...), free of the cancellation at small x.
 __device__ __forceinline__ float nfw_m(float x) {
   if (x <= 1.0f) {
-    const float z = x / (2.0f + x);
+    const float z = __fdividef(x, 2.0f + x);
     const float z2 = z * z;
     float s = 1.0f / 19.0f;
     s = fmaf(s, z2, 1.0f / 17.0f);
@@ -274,16 +288,16 @@ __device__ __forceinline__ float nfw_m(float x) {
     s = fmaf(s, z2, 1.0f / 7.0f);
     s = fmaf(s, z2, 1.0f / 5.0f);
     s = fmaf(s, z2, 1.0f / 3.0f);
-    return 2.0f * z2 / (1.0f + z) + 2.0f * z2 * z * s;
+    return __fdividef(2.0f * z2, 1.0f + z) + 2.0f * z2 * z * s;
   }
-  return log1pf(x) - x / (1.0f + x);
+  return lg2_approx(1.0f + x) * 0.693147181f - __fdividef(x, 1.0f + x);
 }
 
 // Circular velocity squared of the halo at in-plane radius r.
 __device__ __forceinline__ float halo_v2(const ModelConst& m, float r, float inv_r) {
   const float x = r * m.inv_rs;
   if (m.hern) {
-    const float ix = __frcp_rn(1.0f + x);
+    const float ix = rcp_approx(1.0f + x);
     return m.vh_c * x * ix * ix;
   }
   return m.vh_c * nfw_m(x) * inv_r;
@@ -302,9 +316,10 @@ __device__ __forceinline__ void bulge_projected(const ModelConst& m, float R, fl
   constexpr int base = NodeBase<NQ>::value;
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
-  const float w = x / xp1;
+  const float ix1 = rcp_approx(xp1);
+  const float w = x * ix1;
   const float lw = lg2_approx(w);
-  const float i2 = __frcp_rn(xp1 * xp1);
+  const float i2 = ix1 * ix1;
   const float ip4 = i2 * i2;
   const float pS = ex2_approx(m.ngam * lw) * ip4;
   const float pQ = ex2_approx(m.g3 * lw) * ip4;
@@ -384,9 +399,10 @@ __device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const flo
   constexpr int base = NodeBase<NQ>::value;
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
-  const float w = x / xp1;
+  const float ix1 = rcp_approx(xp1);
+  const float w = x * ix1;
   const float lw = lg2_approx(w);
-  const float i2 = __frcp_rn(xp1 * xp1);
+  const float i2 = ix1 * ix1;
   const float ip4 = i2 * i2;
   const float pS = ex2_approx(m.ngam * lw) * ip4;
   const float pQ = ex2_approx(m.g3 * lw) * ip4;
@@ -427,9 +443,9 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
   const float R2 = fmaf(X, X, Y * Y);
   const float yd = yr * m.inv_ci;
   const float r2 = fmaf(xr, xr, yd * yd);
-  const float R = sqrtf(fmaxf(R2, kR2Floor));
-  const float r = sqrtf(fmaxf(r2, kR2Floor));
-  const float inv_r = __frcp_rn(r);
+  const float R = sqrt_approx(fmaxf(R2, kR2Floor));
+  const float r = sqrt_approx(fmaxf(r2, kR2Floor));
+  const float inv_r = rcp_approx(r);
   const float cphi = xr * inv_r;
 
   float Sb, SbS2;
@@ -445,16 +461,16 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
 
   // circular velocities in the disc plane (Eq. 10)
   const float xa = r * m.inv_a;
-  const float ub = xa / (xa + 1.0f);
+  const float ub = xa * rcp_approx(xa + 1.0f);
   float vint2 = __fdividef(m.vb_c * ex2_approx(m.three_mg * lg2_approx(ub)), xa);
   vint2 += halo_v2(m, r, inv_r);
   float Sd[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     vint2 += m.vd_c[j] * disc_F(r * m.half_inv_Rd[j]);
-    Sd[j] = m.Sd_c[j] * expf(-r * m.inv_Rd[j]);
+    Sd[j] = m.Sd_c[j] * ex2_approx(-r * m.inv_Rd[j] * 1.44269504f);
   }
-  const float vint = sqrtf(vint2);
+  const float vint = sqrt_approx(vint2);
 
   // light weighting (Eqs. 13-15, 19)
   const float Bb = Sb * m.Lb;
@@ -467,8 +483,8 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
     Bs2 = fmaf(Bd, m.omk[j] * vint2, Bs2);
     Stot += Sd[j];
   }
-  const float iB = __frcp_rn(B);
-  return make_float4(B, Bv * iB, sqrtf(Bs2 * iB), __fdividef(B * 1e6f, Stot));
+  const float iB = rcp_approx(B);
+  return make_float4(B, Bv * iB, sqrt_approx(Bs2 * iB), __fdividef(B * 1e6f, Stot));
 }
 
 }  // namespace bang
