@@ -42,7 +42,7 @@ class _Galaxy(ctypes.Structure):
         ("spaxel_arcsec", ctypes.c_double), ("kpc_per_arcsec", ctypes.c_double),
         ("psf_kind", ctypes.c_int), ("psf_fwhm_arcsec", ctypes.c_double), ("moffat_beta", ctypes.c_double),
         ("data", ctypes.POINTER(ctypes.c_double)), ("err", ctypes.POINTER(ctypes.c_double)),
-        ("mask", ctypes.POINTER(ctypes.c_uint8)),
+        ("mask", ctypes.POINTER(ctypes.c_uint8)), ("psf_mode", ctypes.c_int),
     ]
 
 
@@ -105,7 +105,7 @@ class Galaxy:
     """
 
     def __init__(self, nx, ny, oversample, psf_fwhm_arcsec, kpc_per_arcsec,
-                 spaxel_arcsec=1.0, psf_kind=0, moffat_beta=3.0, data=None, err=None, mask=None):
+                 spaxel_arcsec=1.0, psf_kind=0, moffat_beta=3.0, data=None, err=None, mask=None, psf_mode=0):
         self.nx, self.ny, self.os = int(nx), int(ny), int(oversample)
         self.data = None if data is None else np.ascontiguousarray(data, dtype=np.float64).reshape(4, ny, nx)
         self.err = None if err is None else np.ascontiguousarray(err, dtype=np.float64).reshape(4, ny, nx)
@@ -114,7 +114,9 @@ class Galaxy:
                           int(psf_kind), float(psf_fwhm_arcsec), float(moffat_beta),
                           None if self.data is None else _dptr(self.data),
                           None if self.err is None else _dptr(self.err),
-                          None if self.mask is None else self.mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+                          None if self.mask is None else self.mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                          int(psf_mode))
+        self.psf_mode = int(psf_mode)
         self.h = _load().bang_oracle_psf_halfwidth(ctypes.byref(self._c))
 
     @property

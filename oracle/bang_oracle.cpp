@@ -29,6 +29,11 @@
 //    convolved on their own; the model M/L is 1/<L/M> (footnote to Eq. 19).
 //  * Oversampling: an os x os fine grid per spaxel, padded by h fine pixels on every side,
 //    convolved then averaged per spaxel.
+//  * PSF modes (bits of psf_mode): 1 - the window is the circle of radius 3 sigma that
+//    Eq. 21 names instead of the square; 2 - App. A's centre sampling: each spaxel's value
+//    is the PSF-weighted mean of the fine points around its centre (no average over its
+//    sub-points); 4 - flux-weighted moments: B, B v, B (sigma^2 + v^2) and the surface
+//    mass are convolved, and v, sigma and M/L are formed from them per spaxel.
 //  * Likelihood (Eq. 18): each term is Gaussian, logL = -chi^2/2 - sum ln(sqrt(2 pi) delta).
 #include <cmath>
 #include <cstdint>
@@ -248,8 +253,12 @@ bool in_domain(const double* th, int np, int halo) {
 // ------------------------------------------------------------------ one sky point
 // The four light-weighted observables at one sky point (arcsec): B_tot (Eq. 13, Lsun/pc^2),
 // v_los (Eq. 14), sigma_los (Eq. 15) and <L/M> (Eq. 19).
+// With flux = true the four outputs are instead the quantities a flux-weighted PSF
+// convolves: B, B v_los, B (sigma_los^2 + v_los^2) and the surface mass (1e-6 Sigma, so
+// that M/L = its convolution over B's).
 template <class T>
-void eval_point(const Model<T>& m, double xs, double ys, double kpa, const RadialRule& q, T out[4]) {
+void eval_point(const Model<T>& m, double xs, double ys, double kpa, const RadialRule& q, T out[4],
+                bool flux = false) {
   // Sec. 2.1: move the centre to the origin, rotate the major axis onto x (footnote on P.A.).
   const T X = xs * kpa - m.x0, Y = ys * kpa - m.y0;
   const T xr = X * m.cpa + Y * m.spa;
@@ -280,6 +289,13 @@ void eval_point(const Model<T>& m, double xs, double ys, double kpa, const Radia
     const T Bd = Sd[j] * 1e-6 / m.MLd[j];
     B += Bd; Bv += Bd * vd[j]; Bs2 += Bd * s2d[j]; Stot += Sd[j];
   }
+  if (flux) {
+    out[0] = B;
+    out[1] = Bv;
+    out[2] = Bs2 + Bv * Bv / B;       // B (sigma^2 + v^2)
+    out[3] = 1e-6 * Stot;
+    return;
+  }
   out[0] = B;
   out[1] = Bv / B;                    // Eq. 14
   out[2] = sqrt(Bs2 / B);             // Eq. 15
@@ -287,10 +303,14 @@ void eval_point(const Model<T>& m, double xs, double ys, double kpa, const Radia
 }
 
 // ------------------------------------------------------------------ grid and PSF
+enum { kPsfCircle = 1, kPsfCentre = 2, kPsfFlux = 4 };
+
 struct Galaxy {
   int nx, ny, os, h;
   double dpix, kpa, pitch;
   int psf_kind; double fwhm, beta;
+  int psf_mode;   // bits kPsfCircle, kPsfCentre, kPsfFlux
+  double rho;     // window radius 3 sigma in fine pixels (0 without a PSF)
   const double* data; const double* err; const uint8_t* mask;
   int W() const { return os * nx + 2 * h; }
   int H() const { return os * ny + 2 * h; }
@@ -306,20 +326,34 @@ int psf_halfwidth(double fwhm, double pitch) {
   return (int)std::floor(3.0 * sig / pitch);
 }
 
+// Unnormalised PSF value at a fine-pixel offset (dx, dy) (Eq. 21's Gaussian, or Moffat).
+double psf_value(const Galaxy& g, double dx, double dy) {
+  const double d2 = (dx * dx + dy * dy) * g.pitch * g.pitch;
+  if (g.psf_kind == 0) {
+    const double sig = g.fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    return std::exp(-d2 / (2.0 * sig * sig));
+  }
+  const double alpha = g.fwhm / (2.0 * std::sqrt(std::pow(2.0, 1.0 / g.beta) - 1.0));
+  return std::pow(1.0 + d2 / (alpha * alpha), -g.beta);
+}
+
+// Is the offset (dx, dy) (fine pixels) inside the PSF window: the square |dx|, |dy| <=
+// 3 sigma, or with kPsfCircle the circle of radius 3 sigma.
+bool in_window(const Galaxy& g, double dx, double dy) {
+  if (g.psf_mode & kPsfCircle) return dx * dx + dy * dy <= g.rho * g.rho;
+  return std::fabs(dx) <= g.rho && std::fabs(dy) <= g.rho;
+}
+
 // Normalised 2-D PSF weights W[(dy + h) * (2h+1) + (dx + h)] (Eq. 21).
 std::vector<double> psf_weights(const Galaxy& g) {
   const int n = 2 * g.h + 1;
-  std::vector<double> w(n * n);
+  std::vector<double> w(n * n, 0.0);
   if (g.h == 0) { w[0] = 1.0; return w; }                  // no PSF: the identity
   double tot = 0.0;
-  const double sig = g.fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
-  const double alpha = g.fwhm / (2.0 * std::sqrt(std::pow(2.0, 1.0 / g.beta) - 1.0));
   for (int dy = -g.h; dy <= g.h; ++dy)
     for (int dx = -g.h; dx <= g.h; ++dx) {
-      const double d2 = (dx * dx + dy * dy) * g.pitch * g.pitch;
-      double v;
-      if (g.psf_kind == 0) v = std::exp(-d2 / (2.0 * sig * sig));
-      else v = std::pow(1.0 + d2 / (alpha * alpha), -g.beta);
+      if (!in_window(g, dx, dy)) continue;
+      const double v = psf_value(g, dx, dy);
       w[(dy + g.h) * n + (dx + g.h)] = v;
       tot += v;
     }
@@ -331,13 +365,42 @@ std::vector<double> psf_weights(const Galaxy& g) {
 template <class T>
 void fine_field(const Galaxy& g, const Model<T>& m, const RadialRule& q, std::vector<T>& f) {
   const int W = g.W(), H = g.H();
+  const bool flux = (g.psf_mode & kPsfFlux) != 0;
   f.assign((size_t)4 * W * H, T(0.0));
 #pragma omp parallel for schedule(static)
   for (int qy = 0; qy < H; ++qy)
     for (int qx = 0; qx < W; ++qx) {
       T o[4];
-      eval_point(m, g.xq(qx), g.yq(qy), g.kpa, q, o);
+      eval_point(m, g.xq(qx), g.yq(qy), g.kpa, q, o, flux);
       for (int c = 0; c < 4; ++c) f[((size_t)c * H + qy) * W + qx] = o[c];
+    }
+}
+
+// App. A's centre sampling (kPsfCentre): each spaxel's value is the PSF-weighted mean
+// (Eq. 21) of the fine points around its centre, fine coordinate (h + i os + (os-1)/2,
+// h + j os + (os-1)/2): the points inside the window, and always the one to four points
+// nearest the centre (|dx|, |dy| <= 1/2), which alone are used without a PSF (equal
+// weights).
+template <class T>
+void convolve_centre(const Galaxy& g, const std::vector<T>& f, std::vector<T>& maps) {
+  const int W = g.W(), H = g.H();
+  maps.assign((size_t)4 * g.nx * g.ny, T(0.0));
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < g.ny; ++j)
+    for (int i = 0; i < g.nx; ++i) {
+      const double cx = g.h + i * g.os + 0.5 * (g.os - 1), cy = g.h + j * g.os + 0.5 * (g.os - 1);
+      T acc[4] = {T(0.0), T(0.0), T(0.0), T(0.0)};
+      double tot = 0.0;
+      for (int qy = 0; qy < H; ++qy)
+        for (int qx = 0; qx < W; ++qx) {
+          const double dx = qx - cx, dy = qy - cy;
+          const bool nearest = std::fabs(dx) <= 0.5 && std::fabs(dy) <= 0.5;
+          if (!nearest && !(g.fwhm > 0.0 && in_window(g, dx, dy))) continue;
+          const double w = g.fwhm > 0.0 ? psf_value(g, dx, dy) : 1.0;
+          tot += w;
+          for (int c = 0; c < 4; ++c) acc[c] += w * f[((size_t)c * H + qy) * W + qx];
+        }
+      for (int c = 0; c < 4; ++c) maps[((size_t)c * g.ny + j) * g.nx + i] = acc[c] / tot;
     }
 }
 
@@ -345,6 +408,10 @@ void fine_field(const Galaxy& g, const Model<T>& m, const RadialRule& q, std::ve
 // PSF-weighted mean of the field around each sub-point (Eq. 21).  maps[c][j][i].
 template <class T>
 void convolve_bin(const Galaxy& g, const std::vector<double>& wts, const std::vector<T>& f, std::vector<T>& maps) {
+  if (g.psf_mode & kPsfCentre) {
+    convolve_centre(g, f, maps);
+    return;
+  }
   const int W = g.W(), H = g.H(), n = 2 * g.h + 1;
   maps.assign((size_t)4 * g.nx * g.ny, T(0.0));
 #pragma omp parallel for schedule(static)
@@ -367,10 +434,19 @@ void convolve_bin(const Galaxy& g, const std::vector<double>& wts, const std::ve
 }
 
 // Observable maps compared with the data: B, v_los + v_sys, sigma_los, M/L = 1 / <L/M>.
+// Flux-weighted moments: v = C1 / C0, sigma^2 = C2 / C0 - v^2, M/L = C3 / C0.
 template <class T>
 void observables(const Galaxy& g, const Model<T>& m, std::vector<T>& maps) {
   const size_t n = (size_t)g.nx * g.ny;
   for (size_t s = 0; s < n; ++s) {
+    if (g.psf_mode & kPsfFlux) {
+      const T B = maps[s], v = maps[n + s] / B;
+      const T s2 = maps[2 * n + s] / B - v * v;
+      maps[n + s] = v + m.vsys;
+      maps[2 * n + s] = sqrt(s2);
+      maps[3 * n + s] = maps[3 * n + s] / B;
+      continue;
+    }
     maps[n + s] = maps[n + s] + m.vsys;
     maps[3 * n + s] = 1.0 / maps[3 * n + s];
   }
@@ -419,6 +495,7 @@ typedef struct {
   const double* data;      // [4][ny][nx]: B, v, sigma, M/L
   const double* err;       // [4][ny][nx]: delta > 0
   const uint8_t* mask;     // [4][ny][nx] or NULL
+  int psf_mode;            // bits: 1 circular window, 2 centre sampling, 4 flux-weighted
 } bang_oracle_galaxy;
 
 typedef struct { int n_discs; int n_quad; int halo_kind; } bang_oracle_opts;
@@ -429,6 +506,8 @@ static Galaxy make_galaxy(const bang_oracle_galaxy* d) {
   g.dpix = d->spaxel_arcsec; g.kpa = d->kpc_per_arcsec; g.pitch = d->spaxel_arcsec / d->oversample;
   g.psf_kind = d->psf_kind; g.fwhm = d->psf_fwhm_arcsec; g.beta = d->moffat_beta;
   g.h = d->psf_fwhm_arcsec > 0.0 ? psf_halfwidth(d->psf_fwhm_arcsec, g.pitch) : 0;
+  g.psf_mode = d->psf_mode;
+  g.rho = d->psf_fwhm_arcsec > 0.0 ? 3.0 * d->psf_fwhm_arcsec / (2.0 * std::sqrt(2.0 * std::log(2.0))) / g.pitch : 0.0;
   g.data = d->data; g.err = d->err; g.mask = d->mask;
   return g;
 }
