@@ -76,13 +76,25 @@ typedef struct {
   const uint8_t *mask;      /* host, [4][ny][nx], nonzero = used; NULL = all used */
 } bang_galaxy_desc;
 
+/* bits of bang_model_opts.psf_mode (no counterpart names in the paper) */
+#define BANG_PSF_CIRCLE 1
+#define BANG_PSF_CENTRE 2
+#define BANG_PSF_FLUX 4
+
 typedef struct {
   int n_discs;     /* 1 or 2 */
   int bulge_kind;  /* 0: Dehnen gamma family (the only kind) */
   int halo_kind;   /* 0: NFW (M200, c); 1: Hernquist (M_h, R_h), the paper's halo (Sec. 2.2):
                       v^2 = G M_h r / (r + R_h)^2, Eq. 2 with the halo's mass and radius */
   int n_quad;      /* radial quadrature nodes: 64 or 128 */
-  int psf_mode;    /* 0: convolve B, v, sigma and <L/M> each on its own (Sec. 3.1) */
+  int psf_mode;    /* 0 (default): square window |dx|, |dy| <= 3 sigma, each spaxel the mean over its
+                      os x os fine points of the PSF-weighted average around each, and B, v,
+                      sigma and <L/M> convolved each on its own (Sec. 3.1).  Or any sum of:
+                      BANG_PSF_CIRCLE - the window is the circle of radius 3 sigma (Eq. 21);
+                      BANG_PSF_CENTRE - each spaxel is the PSF-weighted average of the fine
+                        points around its centre (App. A), without the os x os mean;
+                      BANG_PSF_FLUX - B, B v, B (sigma^2 + v^2) and the surface mass are
+                        convolved; v = C1/C0, sigma^2 = C2/C0 - v^2, M/L = C3/C0 per spaxel. */
   int bulge_table; /* 0: the radial quadrature at every fine point (default).  N in [256, 4096]:
                       per parameter vector, the same n_quad-node quadrature at N radii spaced
                       uniformly in log R between the 1e-6 kpc floor and the farthest fine point,

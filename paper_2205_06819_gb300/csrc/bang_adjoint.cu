@@ -210,10 +210,18 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float f3 = B * 1e6f * iS;
 
   // ---- reverse
-  const float gB = a.x - a.y * f1 * iB - 0.5f * a.z * f2 * iB + a.w * f3 * iB;
-  const float gBv = a.y * iB;
-  const float gBs2 = f2 > 0.f ? __fdividef(0.5f * a.z, f2 * B) : 0.f;
-  const float gStot = -a.w * f3 * iS;
+  float gB, gBv, gBs2, gStot;
+  if (m.flux) {   // point values (B, Bv, Bs2 + Bv^2 / B, 1e-6 Stot)
+    gB = a.x - a.z * f1 * f1;
+    gBv = fmaf(2.0f * a.z, f1, a.y);
+    gBs2 = a.z;
+    gStot = 1e-6f * a.w;
+  } else {        // point values (B, Bv / B, sqrt(Bs2 / B), 1e6 B / Stot)
+    gB = a.x - a.y * f1 * iB - 0.5f * a.z * f2 * iB + a.w * f3 * iB;
+    gBv = a.y * iB;
+    gBs2 = f2 > 0.f ? __fdividef(0.5f * a.z, f2 * B) : 0.f;
+    gStot = -a.w * f3 * iS;
+  }
   const float gSb = fmaf(gB, m.Lb, gStot);
   const float gQb = gBs2 * m.Lb;
   acc[A_LB] += fmaf(gB, bd.Sb, gBs2 * bd.Qb);
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ModelConst mc;
   __shared__ GalDev gs;
-  __shared__ double red[kAdjThreads / 32][NACC + 1];
+  __shared__ double red[kAdjThreads / 32][NACC];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int next_item;
@@ -376,10 +384,6 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
     float acc[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) acc[k] = 0.f;
-    double vsys_part = 0.0;
-    if (w.j0 == 0) {   // the first band of a row also adds d logL / d v_sys = sum_s lambda_v
-      for (int s = tid; s < n; s += kAdjThreads) vsys_part += (double)__ldg(seed + n + s);
-    }
     const float pk = gs.pitch_kpa;
     for (int y0 = w.j0; y0 < w.j1; y0 += a.G) {
       const int G = min(a.G, w.j1 - y0);
@@ -458,15 +462,11 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
       const double v = warp_sum((double)acc[k]);
       if (lane == 0) red[warp][k] = v;
     }
-    {
-      const double v = warp_sum(vsys_part);
-      if (lane == 0) red[warp][NACC] = v;
-    }
     __syncthreads();
-    if (tid <= NACC) {   // one thread per accumulator: sum over warps, add to the row's slot
+    if (tid < NACC) {   // one thread per accumulator: sum over warps, add to the row's slot
       double sum = 0.0;
       for (int q = 0; q < kAdjThreads / 32; ++q) sum += red[q][tid];
-      if (sum != 0.0) atomicAdd(a.grad_acc + (size_t)w.b * kGradAccStride + (tid < NACC ? tid : 24), sum);
+      if (sum != 0.0) atomicAdd(a.grad_acc + (size_t)w.b * kGradAccStride + tid, sum);
     }
     BANG_NEXT_ITEM(it);
   }
@@ -492,7 +492,7 @@ __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, 
   if (ok) {
     const double* s = acc + (size_t)b * kGradAccStride;
     constants_to_theta(th, T, nd, halo_kind, s, g);
-    g[14] = s[24];
+    g[14] = s[kVsysSlot];
   }
   for (int p = 0; p < P; ++p) grad[(size_t)b * P + p] = (float)g[p];
 }

@@ -115,56 +115,93 @@ int psf_halfwidth(double fwhm, double pitch) {
   return (int)std::floor(3.0 * sig / pitch);
 }
 
-// Combined PSF (x) box-filter taps.  Spaxel column i averages fine columns h + i*os + m,
-// m in [0, os); each of those is the PSF-weighted mean over offsets d in [-h, h].  Their
-// composition weights padded fine column i*os + c, c in [0, os + 2h), by
-//   T[c] = (1/os) sum_{m} g(c - m - h),  g normalised to unit sum.
-// Gaussian: separable, one axis (the two-axis normalisation is the square of the one-axis
-// sum).  Moffat: the two-dimensional table W2[cy][cx].
-std::vector<float> make_taps(int kind, double fwhm, double beta, int os, int h, double pitch) {
-  const int L = os + 2 * h, n = 2 * h + 1;
-  if (kind == 0) {
-    std::vector<double> g(n, 1.0);
-    if (h > 0) {
-      const double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
-      double tot = 0.0;
-      for (int d = -h; d <= h; ++d) tot += (g[d + h] = std::exp(-(d * pitch) * (d * pitch) / (2.0 * sig * sig)));
-      for (double& v : g) v /= tot;
-    }
-    std::vector<float> T(L);
-    for (int c = 0; c < L; ++c) {
-      double s = 0.0;
-      for (int m = 0; m < os; ++m) {
-        const int d = c - m - h;
-        if (d >= -h && d <= h) s += g[d + h];
-      }
-      T[c] = (float)(s / os);
-    }
-    return T;
-  }
-  std::vector<double> M((size_t)n * n, 1.0);
-  if (h > 0) {
-    const double alpha = fwhm / (2.0 * std::sqrt(std::pow(2.0, 1.0 / beta) - 1.0));
+// PSF taps, in fine pixels of pitch p.  The PSF g (Eq. 21's Gaussian, or Moffat) is cut
+// to its window: the square |dx|, |dy| <= rho, rho = 3 sigma / p, or with the circular mode
+// (psf_mode bit 1) the circle of radius rho that Eq. 21 names.
+//  * Binning (default): spaxel column i averages fine columns h + i*os + m, m in [0, os);
+//    each of those is the PSF-weighted mean over integer offsets in the window.  Their
+//    composition weights padded fine column i*os + c, c in [0, os + 2h), by
+//      T[c] = (1/os) sum_m g(c - m - h)    (g normalised to unit sum over the window).
+//  * Centre sampling (psf_mode bit 2, App. A): spaxel (i, j) is the PSF-weighted mean of
+//    the fine points around its centre, at offset c - h - (os-1)/2 from padded column
+//    i*os + c: the points in the window, and always the one or two per axis nearest the
+//    centre (|offset| <= 1/2), which alone are used (equal weights) without a PSF.
+// Separable ([L], the two-axis weight is T[cy] T[cx]) for a Gaussian with the square
+// window; otherwise the two-dimensional table W2[cy][cx] ([L][L]).
+std::vector<float> make_taps(int kind, double fwhm, double beta, int os, int h, double pitch, int mode) {
+  const int L = os + 2 * h;
+  const bool circle = (mode & BANG_PSF_CIRCLE) != 0, centre = (mode & BANG_PSF_CENTRE) != 0;
+  const bool two_d = kind == 1 || circle;
+  const bool psf = fwhm > 0.0;
+  const double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+  const double rho = psf ? 3.0 * sig / pitch : 0.0;
+  const double alpha = kind == 1 ? fwhm / (2.0 * std::sqrt(std::pow(2.0, 1.0 / beta) - 1.0)) : 1.0;
+  auto value = [&](double dx, double dy) {
+    const double d2 = (dx * dx + dy * dy) * pitch * pitch;
+    return kind == 0 ? std::exp(-d2 / (2.0 * sig * sig)) : std::pow(1.0 + d2 / (alpha * alpha), -beta);
+  };
+  auto inside = [&](double dx, double dy) {
+    return circle ? dx * dx + dy * dy <= rho * rho : std::fabs(dx) <= rho && std::fabs(dy) <= rho;
+  };
+  const double c0 = h + 0.5 * (os - 1);   // centre of spaxel 0 in padded fine columns
+  if (!two_d) {
+    std::vector<double> t(L, 0.0);
     double tot = 0.0;
-    for (int dy = -h; dy <= h; ++dy)
-      for (int dx = -h; dx <= h; ++dx) {
-        const double r2 = (double)(dx * dx + dy * dy) * pitch * pitch;
-        tot += (M[(size_t)(dy + h) * n + (dx + h)] = std::pow(1.0 + r2 / (alpha * alpha), -beta));
+    if (centre) {
+      for (int c = 0; c < L; ++c) {
+        const double d = c - c0;
+        if (std::fabs(d) <= 0.5 || (psf && std::fabs(d) <= rho)) tot += (t[c] = psf ? value(d, 0.0) : 1.0);
       }
-    for (double& v : M) v /= tot;
-  }
-  std::vector<float> W2((size_t)L * L);
-  for (int cy = 0; cy < L; ++cy)
-    for (int cx = 0; cx < L; ++cx) {
-      double s = 0.0;
-      for (int mn = 0; mn < os; ++mn)
-        for (int mm = 0; mm < os; ++mm) {
-          const int dx = cx - mm - h, dy = cy - mn - h;
-          if (dx >= -h && dx <= h && dy >= -h && dy <= h) s += M[(size_t)(dy + h) * n + (dx + h)];
+      for (double& v : t) v /= tot;
+    } else {
+      std::vector<double> g(2 * h + 1, 1.0);
+      if (h > 0) {
+        for (int d = -h; d <= h; ++d) tot += (g[d + h] = value(d, 0.0));
+        for (double& v : g) v /= tot;
+      }
+      for (int c = 0; c < L; ++c) {
+        for (int m = 0; m < os; ++m) {
+          const int d = c - m - h;
+          if (d >= -h && d <= h) t[c] += g[d + h];
         }
-      W2[(size_t)cy * L + cx] = (float)(s / ((double)os * os));
+        t[c] /= os;
+      }
     }
-  return W2;
+    return std::vector<float>(t.begin(), t.end());
+  }
+  std::vector<double> W2((size_t)L * L, 0.0);
+  double tot = 0.0;
+  if (centre) {
+    for (int cy = 0; cy < L; ++cy)
+      for (int cx = 0; cx < L; ++cx) {
+        const double dx = cx - c0, dy = cy - c0;
+        const bool nearest = std::fabs(dx) <= 0.5 && std::fabs(dy) <= 0.5;
+        if (nearest || (psf && inside(dx, dy))) tot += (W2[(size_t)cy * L + cx] = psf ? value(dx, dy) : 1.0);
+      }
+    for (double& v : W2) v /= tot;
+  } else {
+    const int n = 2 * h + 1;
+    std::vector<double> M((size_t)n * n, 0.0);
+    if (h == 0) {
+      M[0] = 1.0;
+    } else {
+      for (int dy = -h; dy <= h; ++dy)
+        for (int dx = -h; dx <= h; ++dx)
+          if (inside(dx, dy)) tot += (M[(size_t)(dy + h) * n + (dx + h)] = value(dx, dy));
+      for (double& v : M) v /= tot;
+    }
+    for (int cy = 0; cy < L; ++cy)
+      for (int cx = 0; cx < L; ++cx) {
+        double acc = 0.0;
+        for (int mn = 0; mn < os; ++mn)
+          for (int mm = 0; mm < os; ++mm) {
+            const int dy = cy - mn - h, dx = cx - mm - h;
+            if (dy >= -h && dy <= h && dx >= -h && dx <= h) acc += M[(size_t)(dy + h) * n + (dx + h)];
+          }
+        W2[(size_t)cy * L + cx] = acc / ((double)os * os);
+      }
+  }
+  return std::vector<float>(W2.begin(), W2.end());
 }
 
 // Device memory the library allocates while serving calls (plans, staging, scratch), with
@@ -494,7 +531,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
 int psf2d_of(const bang_model* m, const Plan* p) { return m->gals[p->row_g[0]].psf_kind; }
 
 cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode, double* logL, float* out,
-                            cudaStream_t st) {
+                            cudaStream_t st, double* grad_acc = nullptr) {
   bang::FwdArgs a{};
   a.theta = theta;
   a.P = m->P;
@@ -506,6 +543,7 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.partial = p->d_partial.as<double>();
   a.maps = mode == bang::kModeMaps ? out : nullptr;
   a.seed = mode == bang::kModeSeed ? out : nullptr;
+  a.grad_acc = mode == bang::kModeSeed ? grad_acc : nullptr;
   a.out_off = p->d_out_off.as<int64_t>();
   a.queue = p->d_queue.as<int>();
   a.consts = p->d_consts.as<bang::ModelConst>();
@@ -533,7 +571,7 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
                          float* grad, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->B * bang::kGradAccStride, st);
   if (e != cudaSuccess) return e;
-  e = enqueue_forward(m, p, theta, bang::kModeSeed, logL, seed, st);
+  e = enqueue_forward(m, p, theta, bang::kModeSeed, logL, seed, st, grad_acc);
   if (e != cudaSuccess) return e;
   bang::AdjArgs a{};
   a.theta = theta;
@@ -606,7 +644,9 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
   if (opts->bulge_kind != 0) return fail(BANG_E_UNSUPPORTED, "bulge_kind %d not available", opts->bulge_kind);
   if (opts->halo_kind != 0 && opts->halo_kind != 1)
     return fail(BANG_E_UNSUPPORTED, "halo_kind %d not available (0 NFW, 1 Hernquist)", opts->halo_kind);
-  if (opts->psf_mode != 0) return fail(BANG_E_UNSUPPORTED, "psf_mode %d not available", opts->psf_mode);
+  if (opts->psf_mode < 0 || opts->psf_mode > (BANG_PSF_CIRCLE | BANG_PSF_CENTRE | BANG_PSF_FLUX))
+    return fail(BANG_E_INVALID_ARG, "psf_mode %d: a sum of BANG_PSF_CIRCLE, BANG_PSF_CENTRE, BANG_PSF_FLUX",
+                opts->psf_mode);
   if (opts->bulge_table != 0 && (opts->bulge_table < 256 || opts->bulge_table > 4096))
     return fail(BANG_E_INVALID_ARG, "bulge_table must be 0 or in [256, 4096]");
   for (int g = 0; g < n_gal; ++g) {
@@ -642,7 +682,8 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
     G.L = G.os + 2 * G.h;
     G.W = G.os * G.nx + 2 * G.h;
     G.H = G.os * G.ny + 2 * G.h;
-    G.psf_kind = d.psf_kind;
+    G.psf_kind = (d.psf_kind == 1 || (opts->psf_mode & BANG_PSF_CIRCLE)) ? 1 : 0;   // two-dimensional taps
+    G.flux = (opts->psf_mode & BANG_PSF_FLUX) ? 1 : 0;
     G.pitch_kpa = (float)(pitch * d.kpc_per_arcsec);
     // sky x of padded fine column q: s ((q - h + 1/2) / os - nx / 2)
     G.xoff_kpa = d.spaxel_arcsec * ((0.5 - G.h) / d.oversample - 0.5 * d.nx) * d.kpc_per_arcsec;
@@ -665,7 +706,8 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
     bang_status st;
     if ((st = upload(m.get(), data, &G.data)) != BANG_OK) return st;
     if ((st = upload(m.get(), iv, &G.iv)) != BANG_OK) return st;
-    const std::vector<float> taps = make_taps(d.psf_kind, d.psf_fwhm_arcsec, d.moffat_beta, G.os, G.h, pitch);
+    const std::vector<float> taps =
+        make_taps(d.psf_kind, d.psf_fwhm_arcsec, d.moffat_beta, G.os, G.h, pitch, opts->psf_mode);
     if ((st = upload(m.get(), taps, &G.taps)) != BANG_OK) return st;
     m->gals.push_back(G);
     m->desc.push_back(d);

@@ -38,11 +38,12 @@ struct GalDev {
   int nx, ny, os, h;
   int L;                 // os + 2h: taps of the combined PSF (x) box filter per axis
   int W, H;              // padded fine grid: os*nx + 2h by os*ny + 2h
-  int psf_kind;          // 0 separable Gaussian, 1 two-dimensional (Moffat)
+  int psf_kind;          // taps: 0 separable (Gaussian, square window), 1 two-dimensional
+  int flux;              // 1: flux-weighted moments are convolved (psf_mode bit 4)
   float pitch_kpa;       // fine pitch in kpc
   double xoff_kpa;       // x (kpc) of padded fine column 0 is xoff_kpa + 0 * pitch_kpa
   double yoff_kpa;
-  const float* taps;     // [L] (Gaussian) or [L][L] (Moffat)
+  const float* taps;     // [L] (separable) or [L][L]
   const float* data;     // [4][ny][nx]
   const float* iv;       // [4][ny][nx]: mask / delta^2
   double norm_const;     // sum over used spaxels of ln(sqrt(2 pi) delta)
@@ -68,6 +69,7 @@ struct ModelConst {
   // discs
   float inv_Rd[2], half_inv_Rd[2], vd_c[2], Sd_c[2], Ld[2], ks[2], omk[2];
   float vsys;
+  int flux;                // the galaxy's flux-weighted PSF mode (GalDev::flux)
   int valid;
 };
 
@@ -202,6 +204,7 @@ __device__ inline void decode_finish(const float* __restrict__ th, const double*
     m.omk[j] = (float)((1.0 - k * k) / 3.0);
   }
   m.vsys = th[14];
+  m.flux = g.flux;
 }
 
 // theta -> per-model constants by one thread; 0 for a row outside the domain.
@@ -433,7 +436,10 @@ __device__ __forceinline__ void fill_node_weights(const ModelConst& m, float2* n
   }
 }
 
-// The four observables at one padded fine grid point: (B, v_los, sigma_los, <L/M>).
+// The four observables at one padded fine grid point: (B, v_los, sigma_los, <L/M>); in the
+// flux-weighted PSF mode the quantities that are convolved instead: (B, B v_los,
+// B (sigma_los^2 + v_los^2), 1e-6 Sigma_tot), so that after the PSF v = C1 / C0,
+// sigma^2 = C2 / C0 - v^2 and M/L = C3 / C0.
 template <int NQ, int ND>
 __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float Y, const float* tab = nullptr,
                                              int T = 0, const float2* nodew = nullptr) {
@@ -484,6 +490,7 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
     Stot += Sd[j];
   }
   const float iB = rcp_approx(B);
+  if (m.flux) return make_float4(B, Bv, fmaf(Bv * iB, Bv, Bs2), 1e-6f * Stot);
   return make_float4(B, Bv * iB, sqrt_approx(Bs2 * iB), __fdividef(B * 1e6f, Stot));
 }
 

@@ -50,25 +50,53 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Residual terms of spaxel (i, j) of galaxy g from the filtered value F = (B, v, sigma, <L/M>).
-// Writes the model maps / adjoint seeds when requested.  Returns chi^2 of the four maps.
+// Residual terms of spaxel (i, j) of galaxy g from the filtered value F = (B, v, sigma, <L/M>)
+// (flux-weighted mode: the filtered moments).  Writes the model maps / adjoint seeds when
+// requested and d logL / d v_lam in lam_v.  Returns chi^2 of the four maps.
 template <int MODE>
 __device__ __forceinline__ float finish_spaxel(const GalDev& g, const ModelConst& m, float4 F, int i, int j,
-                                               float* __restrict__ out) {
+                                               float* __restrict__ out, float& lam_v) {
   const int n = g.nx * g.ny;
   const int s = j * g.nx + i;
-  const float model[4] = {F.x, F.y + m.vsys, F.z, 1.0f / F.w};
-  float chi = 0.f;
+  float model[4];
+  float v = 0.f, sig = 0.f, iC0 = 0.f;
+  if (g.flux) {   // flux-weighted moments: v = C1/C0, sigma^2 = C2/C0 - v^2, M/L = C3/C0
+    iC0 = 1.0f / F.x;
+    v = F.y * iC0;
+    sig = sqrtf(fmaxf(fmaf(F.z, iC0, -v * v), 0.f));
+    model[0] = F.x;
+    model[1] = v + m.vsys;
+    model[2] = sig;
+    model[3] = F.w * iC0;
+  } else {        // each quantity convolved on its own; M/L = 1 / F_l
+    model[0] = F.x;
+    model[1] = F.y + m.vsys;
+    model[2] = F.z;
+    model[3] = 1.0f / F.w;
+  }
+  float chi = 0.f, lam[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const float iv = __ldg(g.iv + c * n + s);
     const float r = model[c] - __ldg(g.data + c * n + s);
     chi = fmaf(r * iv, r, chi);
+    lam[c] = -r * iv;   // d logL / d model_c
     if (MODE == kModeMaps) out[c * n + s] = model[c];
-    if (MODE == kModeSeed) {
-      // d logL / dF for each filtered channel; M/L = 1 / F_l
-      const float lam = -r * iv;
-      out[c * n + s] = c == 3 ? -lam * model[3] * model[3] : lam;
+  }
+  lam_v = lam[1];       // the model velocity map is v + v_sys: d logL / d v_sys sums these
+  if (MODE == kModeSeed) {   // d logL / dF_c for each filtered channel
+    if (g.flux) {
+      // dv = (dC1 - v dC0) / C0; dsigma = (dC2 - 2 v dC1 + (2 v^2 - C2/C0) dC0) / (2 sigma C0);
+      // dML = (dC3 - ML dC0) / C0
+      const float hs = sig > 0.f ? 0.5f * lam[2] / sig : 0.f;
+      out[s] = lam[0] + iC0 * (-v * lam[1] + hs * (2.0f * v * v - F.z * iC0) - model[3] * lam[3]);
+      out[n + s] = iC0 * (lam[1] - 2.0f * v * hs);
+      out[2 * n + s] = iC0 * hs;
+      out[3 * n + s] = iC0 * lam[3];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[c * n + s] = lam[c];
+      out[3 * n + s] = -lam[3] * model[3] * model[3];
     }
   }
   return chi;
@@ -137,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     if (!tab) fill_node_weights<NQ>(mc, nodew, tid, kThreads);
     __syncthreads();
 
-    double chi_thread = 0.0;
+    double chi_thread = 0.0, vsys_thread = 0.0;
     const int y_begin = w.j0 * os;
     const int y_end = (w.j1 - 1) * os + L;                   // exclusive
     const int nchunks = (y_end - y_begin + a.G - 1) / a.G;
@@ -202,7 +230,9 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
               const int j = yl / os;
               if (j >= w.j0 && j < w.j1) {
                 float4& A = acc[(j % NA) * nx + i];
-                chi_thread += (double)finish_spaxel<MODE>(gs, mc, A, i, j, out);
+                float lam_v;
+                chi_thread += (double)finish_spaxel<MODE>(gs, mc, A, i, j, out, lam_v);
+                if (MODE == kModeSeed) vsys_thread += (double)lam_v;
                 A = make_float4(0.f, 0.f, 0.f, 0.f);
               }
             }
@@ -232,7 +262,9 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
             }
           }
           if (j * os + L - 1 <= ylast) {
-            chi_thread += (double)finish_spaxel<MODE>(gs, mc, A, i, j, out);
+            float lam_v;
+            chi_thread += (double)finish_spaxel<MODE>(gs, mc, A, i, j, out, lam_v);
+            if (MODE == kModeSeed) vsys_thread += (double)lam_v;
             A = make_float4(0.f, 0.f, 0.f, 0.f);
           }
           acc[(j % NA) * nx + i] = A;
@@ -252,11 +284,21 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       for (int k = 0; k < kThreads / 32; ++k) s += red[k];
       a.partial[item_id] = s;
     }
+    if (MODE == kModeSeed) {   // the item's share of d logL / d v_sys, added to the row's slot
+      __syncthreads();         // red is reused
+      const double u = warp_sum(vsys_thread);
+      if ((tid & 31) == 0) red[tid >> 5] = u;
+      __syncthreads();
+      if (tid == 0) {
+        double s = 0.0;
+        for (int k = 0; k < kThreads / 32; ++k) s += red[k];
+        atomicAdd(a.grad_acc + (size_t)w.b * kGradAccStride + kVsysSlot, s);
+      }
+    }
     BANG_NEXT_ITEM(it);
   }
 }
 
-// One thread per row: theta -> per-model constants (float64 decode), against the row's galaxy.
 // One warp per row: lane i < kDecodeTerms evaluates decode term i (the float64
 // transcendentals are independent), lane 0 gathers them and finishes the row, so a row
 // costs the latency of one transcendental instead of thirteen in a chain.

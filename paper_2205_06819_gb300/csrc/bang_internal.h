@@ -16,6 +16,7 @@ struct ModelConst;
 // Gradient accumulator row: adjoints of the per-model constants (slots 0..23, the second
 // disc's unused for one-disc models) and d logL / d v_sys (slot 24).
 constexpr int kGradAccStride = 25;
+constexpr int kVsysSlot = 24;   // grad_acc slot of d logL / d v_sys (filled by the forward seed pass)
 
 enum { kModeLogL = 0, kModeMaps = 1, kModeSeed = 2 };
 
@@ -34,6 +35,7 @@ struct FwdArgs {
   double* partial;          // [n_items] chi^2 of each item (NaN for an out-of-domain row)
   float* maps;              // kModeMaps: model maps, row b at out_off[b]
   float* seed;              // kModeSeed: d logL / dF per spaxel, row b at out_off[b]
+  double* grad_acc;         // kModeSeed: [B][kGradAccStride]; slot kVsysSlot gets d logL / d v_sys
   const int64_t* out_off;   // [B] float offsets of each row's [4][ny][nx] block
   const float* tables;      // radial tables, row b at b * table_stride (NULL: quadrature per point)
   int table_T;              // radii per table

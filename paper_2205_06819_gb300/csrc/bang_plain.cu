@@ -111,6 +111,12 @@ __global__ void plain_combine(const GalDev* __restrict__ gal, const ModelConst* 
   }
   const float iB = 1.0f / B;
   b.f[p] = B;
+  if (m.flux) {   // flux-weighted PSF mode: B v, B (sigma^2 + v^2), 1e-6 Sigma_tot
+    b.f[N + p] = Bv;
+    b.f[2 * N + p] = fmaf(Bv * iB, Bv, Bs2);
+    b.f[3 * N + p] = 1e-6f * Stot;
+    return;
+  }
   b.f[N + p] = Bv * iB;
   b.f[2 * N + p] = sqrtf(Bs2 * iB);
   b.f[3 * N + p] = B * 1e6f / Stot;
@@ -151,7 +157,13 @@ __global__ void plain_chi2(const GalDev* __restrict__ gal, const ModelConst* __r
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
   if (s < n && mcp->valid) {
-    const float model[4] = {b.F[s], b.F[n + s] + mcp->vsys, b.F[2 * n + s], 1.0f / b.F[3 * n + s]};
+    float model[4] = {b.F[s], b.F[n + s] + mcp->vsys, b.F[2 * n + s], 1.0f / b.F[3 * n + s]};
+    if (mcp->flux) {   // v = C1/C0, sigma^2 = C2/C0 - v^2, M/L = C3/C0
+      const float iC0 = 1.0f / b.F[s], v = b.F[n + s] * iC0;
+      model[1] = v + mcp->vsys;
+      model[2] = sqrtf(fmaxf(b.F[2 * n + s] * iC0 - v * v, 0.f));
+      model[3] = b.F[3 * n + s] * iC0;
+    }
     float c2 = 0.f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {

@@ -8,8 +8,9 @@ from paper_2205_06819_gb300 import synth
 
 class Dataset:
     def __init__(self, spec: synth.GalaxySpec, theta_true, n_discs=1, n_quad=64, seed=1, noise=True, mask=None,
-                 halo_kind=0):
+                 halo_kind=0, psf_mode=0):
         self.spec, self.n_discs, self.n_quad, self.halo_kind = spec, n_discs, n_quad, halo_kind
+        self.psf_mode = psf_mode
         self.theta_true = np.asarray(theta_true, dtype=np.float64)
         g0 = self.oracle_galaxy(None, None, None)
         true = oracle.maps(g0, self.theta_true, n_discs=n_discs, n_quad=n_quad, halo_kind=halo_kind)
@@ -21,7 +22,7 @@ class Dataset:
         s = self.spec
         return oracle.Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec,
                              spaxel_arcsec=s.spaxel_arcsec, psf_kind=s.psf_kind, moffat_beta=s.moffat_beta,
-                             data=data, err=err, mask=mask)
+                             data=data, err=err, mask=mask, psf_mode=self.psf_mode)
 
     def model_galaxy(self):
         from paper_2205_06819_gb300.model import Galaxy
