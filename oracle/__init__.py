@@ -47,7 +47,8 @@ class _Galaxy(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("n_discs", ctypes.c_int), ("n_quad", ctypes.c_int), ("halo_kind", ctypes.c_int)]
+    _fields_ = [("n_discs", ctypes.c_int), ("n_quad", ctypes.c_int), ("halo_kind", ctypes.c_int),
+                ("bulge_kind", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -67,6 +68,7 @@ def _load():
                 "bang_oracle_psf_weights": (ctypes.c_int, [G, _D]),
                 "bang_oracle_gauss_legendre": (None, [ctypes.c_int, _D, _D]),
                 "bang_oracle_bulge_projected": (None, [ctypes.c_double] * 4 + [ctypes.c_int, _D, _D]),
+                "bang_oracle_bulge_model": (None, [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int, _D, _D]),
                 "bang_oracle_bulge_vc2": (ctypes.c_double, [ctypes.c_double] * 4),
                 "bang_oracle_dehnen_rho": (ctypes.c_double, [ctypes.c_double] * 4),
                 "bang_oracle_dehnen_mass": (ctypes.c_double, [ctypes.c_double] * 4),
@@ -124,8 +126,8 @@ class Galaxy:
         return (self.os * self.ny + 2 * self.h, self.os * self.nx + 2 * self.h)
 
 
-def _opts(n_discs, n_quad, halo_kind=0):
-    return _Opts(int(n_discs), int(n_quad), int(halo_kind))
+def _opts(n_discs, n_quad, halo_kind=0, bulge_kind=0):
+    return _Opts(int(n_discs), int(n_quad), int(halo_kind), int(bulge_kind))
 
 
 def nparams(n_discs: int) -> int:
@@ -153,6 +155,15 @@ def bulge_projected(R, a, gamma, M, n_quad=64):
     s = ctypes.c_double(); s2 = ctypes.c_double()
     _load().bang_oracle_bulge_projected(float(R), float(a), float(gamma), float(M), int(n_quad),
                                         ctypes.byref(s), ctypes.byref(s2))
+    return s.value, s2.value
+
+
+def bulge_model(R, a, gamma, M, n_quad=64, bulge_kind=0):
+    """(Sigma, sigma^2) as the model uses them: the radial rule, or for bulge_kind 1
+    (Hernquist) / 2 (Jaffe) the paper's closed forms below R / a = 1e-3."""
+    s, s2 = ctypes.c_double(), ctypes.c_double()
+    _load().bang_oracle_bulge_model(float(R), float(a), float(gamma), float(M), int(n_quad), int(bulge_kind),
+                                    ctypes.byref(s), ctypes.byref(s2))
     return s.value, s2.value
 
 
@@ -196,13 +207,13 @@ def rho_crit() -> float:
     return _load().bang_oracle_rho_crit()
 
 
-def points(theta, xs, ys, kpc_per_arcsec, n_discs=1, n_quad=64, halo_kind=0):
+def points(theta, xs, ys, kpc_per_arcsec, n_discs=1, n_quad=64, halo_kind=0, bulge_kind=0):
     """Unconvolved observables [4, n] (B, v_los, sigma_los, <L/M>) at sky points (arcsec)."""
     th = np.ascontiguousarray(theta, dtype=np.float64)
     xs = np.ascontiguousarray(xs, dtype=np.float64).ravel()
     ys = np.ascontiguousarray(ys, dtype=np.float64).ravel()
     out = np.zeros((4, xs.size))
-    o = _opts(n_discs, n_quad, halo_kind)
+    o = _opts(n_discs, n_quad, halo_kind, bulge_kind)
     rc = _load().bang_oracle_points(ctypes.byref(o), _dptr(th), _dptr(xs), _dptr(ys), xs.size,
                                     float(kpc_per_arcsec), _dptr(out))
     if rc:
@@ -210,11 +221,11 @@ def points(theta, xs, ys, kpc_per_arcsec, n_discs=1, n_quad=64, halo_kind=0):
     return out
 
 
-def fine_field(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0):
+def fine_field(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0, bulge_kind=0):
     th = np.ascontiguousarray(theta, dtype=np.float64)
     H, W = gal.padded_shape
     out = np.zeros((4, H, W))
-    o = _opts(n_discs, n_quad, halo_kind)
+    o = _opts(n_discs, n_quad, halo_kind, bulge_kind)
     rc = _load().bang_oracle_fine_field(ctypes.byref(gal._c), ctypes.byref(o), _dptr(th), _dptr(out), nthreads)
     if rc:
         raise ValueError("theta outside the parameter domain")
@@ -230,11 +241,11 @@ def convolve_bin(gal: Galaxy, field, nthreads=0):
     return out
 
 
-def maps(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0):
+def maps(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0, bulge_kind=0):
     """Model maps [4, ny, nx]: B, v_los + v_sys, sigma_los, M/L."""
     th = np.ascontiguousarray(theta, dtype=np.float64)
     out = np.zeros((4, gal.ny, gal.nx))
-    o = _opts(n_discs, n_quad, halo_kind)
+    o = _opts(n_discs, n_quad, halo_kind, bulge_kind)
     rc = _load().bang_oracle_maps(ctypes.byref(gal._c), ctypes.byref(o), _dptr(th), _dptr(out), nthreads)
     if rc:
         raise ValueError("theta outside the parameter domain")
@@ -245,7 +256,7 @@ def norm_const(gal: Galaxy) -> float:
     return _load().bang_oracle_norm_const(ctypes.byref(gal._c))
 
 
-def loglike(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0):
+def loglike(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0, bulge_kind=0):
     """(logL[B], chi2[B]) for theta[B, P]."""
     th = np.ascontiguousarray(np.atleast_2d(theta), dtype=np.float64)
     B = th.shape[0]
@@ -253,13 +264,13 @@ def loglike(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0):
     if gal.data is None or gal.err is None:
         raise ValueError("galaxy has no data")
     logL = np.zeros(B); chi2 = np.zeros(B)
-    o = _opts(n_discs, n_quad, halo_kind)
+    o = _opts(n_discs, n_quad, halo_kind, bulge_kind)
     _load().bang_oracle_loglike(ctypes.byref(gal._c), ctypes.byref(o), _dptr(th), B, _dptr(logL), _dptr(chi2),
                                 nthreads)
     return logL, chi2
 
 
-def loglike_grad(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0):
+def loglike_grad(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind=0, bulge_kind=0):
     """(logL[B], grad[B, P]) with grad = d logL / d theta (forward-mode duals)."""
     th = np.ascontiguousarray(np.atleast_2d(theta), dtype=np.float64)
     B, P = th.shape
@@ -267,7 +278,7 @@ def loglike_grad(gal: Galaxy, theta, n_discs=1, n_quad=64, nthreads=0, halo_kind
     if gal.data is None or gal.err is None:
         raise ValueError("galaxy has no data")
     logL = np.zeros(B); grad = np.zeros((B, P))
-    o = _opts(n_discs, n_quad, halo_kind)
+    o = _opts(n_discs, n_quad, halo_kind, bulge_kind)
     _load().bang_oracle_loglike_grad(ctypes.byref(gal._c), ctypes.byref(o), _dptr(th), B, _dptr(logL),
                                      _dptr(grad), nthreads)
     return logL, grad

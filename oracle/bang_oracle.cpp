@@ -181,6 +181,40 @@ void bulge_projected(const T& R, const T& a, const T& g, const T& M, const Radia
   *sigma2 = 2.0 * kG * p / *Sigma;
 }
 
+// The closed forms of the paper for the projected density and dispersion of the Hernquist
+// bulge (Eqs. 4-6, X(s) of Eq. 5 for s = R / a < 1) and of the Jaffe bulge (Eqs. B4-B5), for
+// the closed-form bulge option at s < 1e-3.  There the fixed radial rule, which reaches only
+// r = R cosh 16 ~ 4.4e6 R, no longer covers a Hernquist bulge, while the closed forms have no
+// cancellation (they do near s = 1 and, for the dispersion, at large s, where the rule is
+// used instead).
+template <class T>
+void bulge_closed_small(const T& R, const T& a, int kind, const T& M, T* Sigma, T* sigma2) {
+  const T s = R / a;
+  const T q = 1.0 - s * s;
+  const T X = log((1.0 + sqrt(q)) / s) / sqrt(q);
+  if (kind == 1) {
+    *Sigma = M / (2.0 * kPi * a * a * q * q) * ((2.0 + s * s) * X - 3.0);
+    const T brace = (-3.0 * s * s * X * (8.0 * pow(s, 6.0) - 28.0 * pow(s, 4.0) + 35.0 * s * s - 20.0)
+                     - 24.0 * pow(s, 6.0) + 68.0 * pow(s, 4.0) - 65.0 * s * s + 6.0) / (2.0 * q * q * q)
+                    - 6.0 * kPi * s;
+    *sigma2 = kG * M * M / (12.0 * kPi * a * a * a * *Sigma) * brace;
+    return;
+  }
+  *Sigma = M / (a * a) * (1.0 / (4.0 * s) + (1.0 - (2.0 - s * s) * X) / (2.0 * kPi * q));
+  const T br = kPi / (2.0 * s) + 11.0 - 6.5 * kPi * s - 12.0 * s * s + 6.0 * kPi * s * s * s
+               - X * (6.0 - 19.0 * s * s + 12.0 * pow(s, 4.0));
+  *sigma2 = kG * M * M / (4.0 * kPi * a * a * a * *Sigma) / q * br;
+}
+
+// The bulge's projected density and dispersion as the model uses them: the radial rule,
+// or for the closed-form bulges (kind 1, 2) their closed forms below s = 1e-3.
+template <class T>
+void bulge_model(const T& R, const T& a, const T& g, const T& M, int kind, const RadialRule& q, T* Sigma,
+                 T* sigma2) {
+  if (kind != 0 && val(R / a) < 1e-3) bulge_closed_small(R, a, kind, M, Sigma, sigma2);
+  else bulge_projected(R, a, g, M, q, Sigma, sigma2);
+}
+
 // Circular velocity squared of the bulge at 3-D radius r: G M(<r) / r (Eq. 2 at gamma = 1).
 template <class T> T bulge_vc2(const T& r, const T& a, const T& g, const T& M) {
   return kG * dehnen_mass(r, a, g, M) / r;
@@ -220,16 +254,22 @@ template <class T> struct Model {
   T a, g, Mb, MLb;
   T Md[2], Rd[2], k[2], MLd[2];
   int halo;             // 0: NFW (M200, c); 1: Hernquist (M_h, R_h), the paper's halo
+  int bulge_kind;       // 0: Dehnen gamma; 1: Hernquist, 2: Jaffe (closed forms at small R/a)
   T M200, c, vsys;      // for the Hernquist halo M200 holds M_h and c holds R_h
 };
 
-template <class T> Model<T> decode(const T* th, int nd, int halo) {
+// bulge_kind 1 (Hernquist, Eqs. 1-6) and 2 (Jaffe, Eqs. B1-B5) fix gamma at 1 and 2: the
+// theta slot of gamma is then not used (zero gradient) and the bulge is the same radial
+// quadrature at that gamma (the closed forms equal it, see the bulge pins).
+template <class T> Model<T> decode(const T* th, int nd, int halo, int bulge_kind = 0) {
   Model<T> m;
   m.nd = nd;
   m.x0 = th[0]; m.y0 = th[1];
   m.cpa = cos(th[2]); m.spa = sin(th[2]);
   m.ci = cos(th[3]); m.si = sin(th[3]);
-  m.Mb = pow(10.0, th[4]); m.a = pow(10.0, th[5]); m.g = th[6];
+  m.Mb = pow(10.0, th[4]); m.a = pow(10.0, th[5]);
+  m.g = bulge_kind == 0 ? th[6] : T((double)bulge_kind);
+  m.bulge_kind = bulge_kind;
   m.Md[0] = pow(10.0, th[7]); m.Rd[0] = pow(10.0, th[8]); m.k[0] = th[9];
   m.MLb = th[10]; m.MLd[0] = th[11];
   m.halo = halo;
@@ -239,10 +279,10 @@ template <class T> Model<T> decode(const T* th, int nd, int halo) {
   return m;
 }
 
-bool in_domain(const double* th, int np, int halo) {
+bool in_domain(const double* th, int np, int halo, int bulge_kind = 0) {
   for (int i = 0; i < np; ++i) if (!std::isfinite(th[i])) return false;
   if (!(th[3] >= 0.0 && th[3] < 0.5 * kPi)) return false;   // inclination
-  if (!(th[6] >= 0.0 && th[6] < 3.0)) return false;         // Dehnen inner slope
+  if (bulge_kind == 0 && !(th[6] >= 0.0 && th[6] < 3.0)) return false;   // Dehnen inner slope
   if (!(std::fabs(th[9]) <= 1.0)) return false;             // Satoh k
   if (!(th[10] > 0.0 && th[11] > 0.0)) return false;        // M/L
   if (halo == 0 && !(th[13] > 0.0)) return false;           // NFW concentration
@@ -270,7 +310,7 @@ void eval_point(const Model<T>& m, double xs, double ys, double kpa, const Radia
   const T cphi = xr / r;                                    // azimuth from the major axis
 
   T Sb, s2b;
-  bulge_projected(R, m.a, m.g, m.Mb, q, &Sb, &s2b);
+  bulge_model(R, m.a, m.g, m.Mb, m.bulge_kind, q, &Sb, &s2b);
 
   // Eq. 10: every component's circular velocity adds in quadrature
   T vint2 = bulge_vc2(r, m.a, m.g, m.Mb) + halo_vc2(r, m.M200, m.c, m.halo);
@@ -498,7 +538,7 @@ typedef struct {
   int psf_mode;            // bits: 1 circular window, 2 centre sampling, 4 flux-weighted
 } bang_oracle_galaxy;
 
-typedef struct { int n_discs; int n_quad; int halo_kind; } bang_oracle_opts;
+typedef struct { int n_discs; int n_quad; int halo_kind; int bulge_kind; } bang_oracle_opts;
 
 static Galaxy make_galaxy(const bang_oracle_galaxy* d) {
   Galaxy g;
@@ -545,6 +585,11 @@ void bang_oracle_bulge_projected(double R, double a, double gamma, double M, int
   const RadialRule q(nq);
   bulge_projected(R, a, gamma, M, q, Sigma, sigma2);
 }
+void bang_oracle_bulge_model(double R, double a, double gamma, double M, int nq, int bulge_kind, double* Sigma,
+                             double* sigma2) {
+  const RadialRule q(nq);
+  bulge_model(R, a, bulge_kind == 0 ? gamma : (double)bulge_kind, M, bulge_kind, q, Sigma, sigma2);
+}
 double bang_oracle_bulge_vc2(double r, double a, double gamma, double M) { return bulge_vc2(r, a, gamma, M); }
 double bang_oracle_dehnen_rho(double r, double a, double gamma, double M) { return dehnen_rho(r, a, gamma, M); }
 double bang_oracle_dehnen_mass(double r, double a, double gamma, double M) { return dehnen_mass(r, a, gamma, M); }
@@ -560,9 +605,9 @@ double bang_oracle_rho_crit(void) { return kRhoCrit; }
 int bang_oracle_points(const bang_oracle_opts* o, const double* theta, const double* xs, const double* ys, int n,
                        double kpa, double* out) {
   const int np = bang_oracle_nparams(o->n_discs);
-  if (!in_domain(theta, np, o->halo_kind)) return 1;
+  if (!in_domain(theta, np, o->halo_kind, o->bulge_kind)) return 1;
   const RadialRule q(o->n_quad);
-  const Model<double> m = decode(theta, o->n_discs, o->halo_kind);
+  const Model<double> m = decode(theta, o->n_discs, o->halo_kind, o->bulge_kind);
   for (int p = 0; p < n; ++p) {
     double v[4];
     eval_point(m, xs[p], ys[p], kpa, q, v);
@@ -577,10 +622,10 @@ int bang_oracle_fine_field(const bang_oracle_galaxy* d, const bang_oracle_opts* 
   set_threads(nthreads);
   const Galaxy g = make_galaxy(d);
   const int np = bang_oracle_nparams(o->n_discs);
-  if (!in_domain(theta, np, o->halo_kind)) return 1;
+  if (!in_domain(theta, np, o->halo_kind, o->bulge_kind)) return 1;
   const RadialRule q(o->n_quad);
   std::vector<double> f;
-  fine_field(g, decode(theta, o->n_discs, o->halo_kind), q, f);
+  fine_field(g, decode(theta, o->n_discs, o->halo_kind, o->bulge_kind), q, f);
   std::memcpy(field, f.data(), f.size() * sizeof(double));
   return 0;
 }
@@ -601,10 +646,10 @@ int bang_oracle_maps(const bang_oracle_galaxy* d, const bang_oracle_opts* o, con
   set_threads(nthreads);
   const Galaxy g = make_galaxy(d);
   const int np = bang_oracle_nparams(o->n_discs);
-  if (!in_domain(theta, np, o->halo_kind)) return 1;
+  if (!in_domain(theta, np, o->halo_kind, o->bulge_kind)) return 1;
   const RadialRule q(o->n_quad);
   std::vector<double> out;
-  model_maps(g, decode(theta, o->n_discs, o->halo_kind), q, out);
+  model_maps(g, decode(theta, o->n_discs, o->halo_kind, o->bulge_kind), q, out);
   std::memcpy(maps, out.data(), out.size() * sizeof(double));
   return 0;
 }
@@ -622,13 +667,13 @@ int bang_oracle_loglike(const bang_oracle_galaxy* d, const bang_oracle_opts* o, 
   const double cst = norm_const(g);
   for (int b = 0; b < B; ++b) {
     const double* th = theta + (size_t)b * np;
-    if (!in_domain(th, np, o->halo_kind)) {
+    if (!in_domain(th, np, o->halo_kind, o->bulge_kind)) {
       logL[b] = -INFINITY;
       if (chi2) chi2[b] = INFINITY;
       continue;
     }
     std::vector<double> maps;
-    model_maps(g, decode(th, o->n_discs, o->halo_kind), q, maps);
+    model_maps(g, decode(th, o->n_discs, o->halo_kind, o->bulge_kind), q, maps);
     const double c2 = chi2_of(g, maps);
     logL[b] = -0.5 * c2 - cst;
     if (chi2) chi2[b] = c2;
@@ -647,7 +692,7 @@ int bang_oracle_loglike_grad(const bang_oracle_galaxy* d, const bang_oracle_opts
   const double cst = norm_const(g);
   for (int b = 0; b < B; ++b) {
     const double* th = theta + (size_t)b * np;
-    if (!in_domain(th, np, o->halo_kind)) {
+    if (!in_domain(th, np, o->halo_kind, o->bulge_kind)) {
       logL[b] = -INFINITY;
       for (int p = 0; p < np; ++p) grad[(size_t)b * np + p] = 0.0;
       continue;
@@ -655,7 +700,7 @@ int bang_oracle_loglike_grad(const bang_oracle_galaxy* d, const bang_oracle_opts
     Dual td[PMAX];
     for (int p = 0; p < np; ++p) { td[p] = Dual(th[p]); td[p].d[p] = 1.0; }
     std::vector<Dual> maps;
-    model_maps(g, decode(td, o->n_discs, o->halo_kind), q, maps);
+    model_maps(g, decode(td, o->n_discs, o->halo_kind, o->bulge_kind), q, maps);
     const Dual c2 = chi2_of(g, maps);
     logL[b] = -0.5 * c2.v - cst;
     for (int p = 0; p < np; ++p) grad[(size_t)b * np + p] = -0.5 * c2.d[p];

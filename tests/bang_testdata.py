@@ -8,12 +8,13 @@ from paper_2205_06819_gb300 import synth
 
 class Dataset:
     def __init__(self, spec: synth.GalaxySpec, theta_true, n_discs=1, n_quad=64, seed=1, noise=True, mask=None,
-                 halo_kind=0, psf_mode=0):
+                 halo_kind=0, psf_mode=0, bulge_kind=0):
         self.spec, self.n_discs, self.n_quad, self.halo_kind = spec, n_discs, n_quad, halo_kind
-        self.psf_mode = psf_mode
+        self.psf_mode, self.bulge_kind = psf_mode, bulge_kind
         self.theta_true = np.asarray(theta_true, dtype=np.float64)
         g0 = self.oracle_galaxy(None, None, None)
-        true = oracle.maps(g0, self.theta_true, n_discs=n_discs, n_quad=n_quad, halo_kind=halo_kind)
+        true = oracle.maps(g0, self.theta_true, n_discs=n_discs, n_quad=n_quad, halo_kind=halo_kind,
+                           bulge_kind=bulge_kind)
         self.data, self.err, m = synth.noisy_data(true, seed=seed, noise=noise)
         self.mask = m if mask is None else np.asarray(mask, dtype=np.uint8)
         self.og = self.oracle_galaxy(self.data.astype(np.float64), self.err.astype(np.float64), self.mask)
@@ -33,11 +34,12 @@ class Dataset:
     def oracle_loglike(self, theta32, nthreads=0):
         th = np.asarray(theta32, dtype=np.float32).astype(np.float64)
         return oracle.loglike(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad, nthreads=nthreads,
-                              halo_kind=self.halo_kind)
+                              halo_kind=self.halo_kind, bulge_kind=self.bulge_kind)
 
     def oracle_maps(self, theta32):
         th = np.asarray(theta32, dtype=np.float32).astype(np.float64)
-        return oracle.maps(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad, halo_kind=self.halo_kind)
+        return oracle.maps(self.og, th, n_discs=self.n_discs, n_quad=self.n_quad, halo_kind=self.halo_kind,
+                           bulge_kind=self.bulge_kind)
 
 
 def theta_batch(n_discs, theta_true, B, seed, gamma_fixed=None, halo_kind=0):
