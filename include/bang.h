@@ -83,7 +83,11 @@ typedef struct {
 
 typedef struct {
   int n_discs;     /* 1 or 2 */
-  int bulge_kind;  /* 0: Dehnen gamma family (the only kind) */
+  int bulge_kind;  /* 0: Dehnen gamma family, projected by the radial quadrature (default).
+                      1: Hernquist (gamma = 1, Eqs. 1-6), 2: Jaffe (gamma = 2, Eqs. B1-B5): the
+                      projected density and dispersion from float32 fits of the closed forms'
+                      universal profiles (about 2e-7 relative); the gamma slot of theta is then
+                      not used and its gradient is 0.  Not with bulge_table. */
   int halo_kind;   /* 0: NFW (M200, c); 1: Hernquist (M_h, R_h), the paper's halo (Sec. 2.2):
                       v^2 = G M_h r / (r + R_h)^2, Eq. 2 with the halo's mass and radius */
   int n_quad;      /* radial quadrature nodes: 64 or 128 */

@@ -157,6 +157,22 @@ __device__ __forceinline__ BulgeDer bulge_table_vjp(const ModelConst& m, const f
   return o;
 }
 
+// The same derivatives for the closed-form bulges: Sigma = M a^-2 F_S(R/a) and
+// Q = G M^2 a^-3 F_Q(R/a) with the fitted slopes s = d ln F / d ln(R/a); gamma is fixed.
+__device__ __forceinline__ BulgeDer bulge_closed_vjp(const ModelConst& m, float R) {
+  BulgeDer o;
+  float sS, sQ;
+  bulge_closed(m, R, o.Sb, o.Qb, &sS, &sQ);
+  const float iR = rcp_approx(R);
+  o.dSb_dR = o.Sb * sS * iR;
+  o.dQb_dR = o.Qb * sQ * iR;
+  o.dSb_da = -o.Sb * (2.0f + sS) * m.inv_a;
+  o.dQb_da = -o.Qb * (3.0f + sQ) * m.inv_a;
+  o.dSb_dg = 0.f;
+  o.dQb_dg = 0.f;
+  return o;
+}
+
 // Vector-Jacobian product of one fine point: adds sum_c a_c d f_c / d(constants) to acc.
 template <int NQ, int ND>
 __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y, float4 a, float* acc,
@@ -173,7 +189,8 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float inv_r = rcp_approx(r);
   const float cphi = xr * inv_r;
 
-  const BulgeDer bd = tab ? bulge_table_vjp(m, tab, T, R) : bulge_projected_vjp<NQ>(m, R, nodew);
+  const BulgeDer bd = tab ? bulge_table_vjp(m, tab, T, R)
+                           : (m.bulge_fit ? bulge_closed_vjp(m, R) : bulge_projected_vjp<NQ>(m, R, nodew));
 
   const float xa = r * m.inv_a;
   const float ub = xa * rcp_approx(xa + 1.0f);
@@ -300,7 +317,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
 // d logL / d theta from the reduced constant adjoints and the row's decode terms T
 // (float64, one thread).
 __device__ void constants_to_theta(const float* __restrict__ th, const double* T, int nd, int halo_kind,
-                                   const double* s, double* g) {
+                                   int bulge_kind, const double* s, double* g) {
   const double ln10 = 2.302585092994045684;
   const double ci = T[0], si = T[1];
   const double a = T[5];
@@ -310,7 +327,7 @@ __device__ void constants_to_theta(const float* __restrict__ th, const double* T
   double gi = s[A_INVCI] * si / (ci * ci);
   g[4] = ln10 * s[A_MB];
   g[5] = ln10 * a * s[A_A];
-  g[6] = s[A_G];
+  g[6] = bulge_kind == 0 ? s[A_G] : 0.0;   // a fixed gamma has no slot to differentiate
   g[10] = -s[A_LB] * (1e-6 / th[10]) / th[10];
   if (halo_kind == 0) {   // NFW: vh_c = G M200 / m(c), 1/rs = c / r200(M200)
     const double M200 = T[6], c = th[13], r200 = T[7], mc = T[8];
@@ -378,7 +395,7 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
       const int nt = kTabHdr + 8 * a.table_T;
       for (int t = tid; t < nt; t += kAdjThreads) tab[t] = __ldg(src + t);
     } else {
-      fill_node_weights<NQ>(mc, nodew, tid, kAdjThreads);
+      if (!mc.bulge_fit) fill_node_weights<NQ>(mc, nodew, tid, kAdjThreads);
     }
 
     float acc[NACC];
@@ -475,13 +492,13 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
 // One warp per row: the reduced constant adjoints -> d logL / d theta (float64), or zero
 // for a row outside the parameter domain.  As in decode_kernel, lane i < kDecodeTerms
 // evaluates decode term i and lane 0 does the rest.
-__global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind,
+__global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind, int bulge_kind,
                                 const double* __restrict__ acc, int B, double l10k, float* __restrict__ grad) {
   const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (b >= B) return;   // whole warps
   const float* th = theta + (size_t)b * P;
-  const bool ok = theta_in_domain(th, nd, halo_kind);
+  const bool ok = theta_in_domain(th, nd, halo_kind, bulge_kind);
   const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
   double T[kDecodeTerms];
 #pragma unroll
@@ -491,7 +508,7 @@ __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, 
   for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
   if (ok) {
     const double* s = acc + (size_t)b * kGradAccStride;
-    constants_to_theta(th, T, nd, halo_kind, s, g);
+    constants_to_theta(th, T, nd, halo_kind, bulge_kind, s, g);
     g[14] = s[kVsysSlot];
   }
   for (int p = 0; p < P; ++p) grad[(size_t)b * P + p] = (float)g[p];
@@ -605,13 +622,12 @@ cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const in
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, const double* acc, int B,
-                            float* grad, cudaStream_t st) {
+cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind, const double* acc,
+                            int B, float* grad, cudaStream_t st) {
   constexpr int kRowsPerBlock = 4;   // 4 warps, one row each
   const double l10k = std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit));
-  grad_out_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(theta, P, n_discs,
-                                                                                          halo_kind, acc, B, l10k,
-                                                                                          grad);
+  grad_out_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(
+      theta, P, n_discs, halo_kind, bulge_kind, acc, B, l10k, grad);
   return cudaGetLastError();
 }
 

@@ -595,7 +595,8 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   if (e != cudaSuccess) return e;
   e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
   if (e != cudaSuccess) return e;
-  return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, grad_acc, p->B, grad, st);
+  return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, m->opts.bulge_kind, grad_acc, p->B,
+                               grad, st);
 }
 
 }  // namespace
@@ -641,7 +642,10 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
   *out = nullptr;
   if (opts->n_discs != 1 && opts->n_discs != 2) return fail(BANG_E_INVALID_ARG, "n_discs must be 1 or 2");
   if (opts->n_quad != 64 && opts->n_quad != 128) return fail(BANG_E_INVALID_ARG, "n_quad must be 64 or 128");
-  if (opts->bulge_kind != 0) return fail(BANG_E_UNSUPPORTED, "bulge_kind %d not available", opts->bulge_kind);
+  if (opts->bulge_kind < 0 || opts->bulge_kind > 2)
+    return fail(BANG_E_UNSUPPORTED, "bulge_kind %d not available (0 Dehnen, 1 Hernquist, 2 Jaffe)", opts->bulge_kind);
+  if (opts->bulge_kind != 0 && opts->bulge_table != 0)
+    return fail(BANG_E_UNSUPPORTED, "the radial-table option applies to the Dehnen bulge (bulge_kind 0) only");
   if (opts->halo_kind != 0 && opts->halo_kind != 1)
     return fail(BANG_E_UNSUPPORTED, "halo_kind %d not available (0 NFW, 1 Hernquist)", opts->halo_kind);
   if (opts->psf_mode < 0 || opts->psf_mode > (BANG_PSF_CIRCLE | BANG_PSF_CENTRE | BANG_PSF_FLUX))
@@ -684,6 +688,7 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
     G.H = G.os * G.ny + 2 * G.h;
     G.psf_kind = (d.psf_kind == 1 || (opts->psf_mode & BANG_PSF_CIRCLE)) ? 1 : 0;   // two-dimensional taps
     G.flux = (opts->psf_mode & BANG_PSF_FLUX) ? 1 : 0;
+    G.bulge_kind = opts->bulge_kind;
     G.pitch_kpa = (float)(pitch * d.kpc_per_arcsec);
     // sky x of padded fine column q: s ((q - h + 1/2) / os - nx / 2)
     G.xoff_kpa = d.spaxel_arcsec * ((0.5 - G.h) / d.oversample - 0.5 * d.nx) * d.kpc_per_arcsec;

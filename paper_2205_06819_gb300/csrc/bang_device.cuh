@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "bulge_fit.h"
 #include "disc_fit.h"
 
 namespace bang {
@@ -40,6 +41,7 @@ struct GalDev {
   int W, H;              // padded fine grid: os*nx + 2h by os*ny + 2h
   int psf_kind;          // taps: 0 separable (Gaussian, square window), 1 two-dimensional
   int flux;              // 1: flux-weighted moments are convolved (psf_mode bit 4)
+  int bulge_kind;        // 0 Dehnen gamma (radial rule); 1 Hernquist, 2 Jaffe (closed-form fits)
   float pitch_kpa;       // fine pitch in kpc
   double xoff_kpa;       // x (kpc) of padded fine column 0 is xoff_kpa + 0 * pitch_kpa
   double yoff_kpa;
@@ -70,6 +72,7 @@ struct ModelConst {
   float inv_Rd[2], half_inv_Rd[2], vd_c[2], Sd_c[2], Ld[2], ks[2], omk[2];
   float vsys;
   int flux;                // the galaxy's flux-weighted PSF mode (GalDev::flux)
+  int bulge_fit;           // GalDev::bulge_kind: 0 radial rule, 1 / 2 closed-form fits
   int valid;
 };
 
@@ -102,13 +105,14 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // the parameter domain (non-finite, i not in [0, pi/2), gamma not in [0, 3), |k| > 1,
 // M/L <= 0, and for the NFW halo c <= 0).  halo_kind 0: NFW (slot 13 = c); 1: Hernquist
 // (slot 13 = log10 R_h, the paper's halo).
-__device__ inline bool theta_in_domain(const float* __restrict__ th, int nd, int halo_kind) {
+// bulge_kind 1 and 2 fix gamma at 1 and 2: the gamma slot is then not used.
+__device__ inline bool theta_in_domain(const float* __restrict__ th, int nd, int halo_kind, int bulge_kind) {
   const int np = nd == 2 ? 19 : 15;
   for (int i = 0; i < np; ++i)
     if (!isfinite((double)th[i])) return false;
   const double inc = th[3], gam = th[6];
   if (!(inc >= 0.0 && inc < 0.5 * kPi)) return false;
-  if (!(gam >= 0.0 && gam < 3.0)) return false;
+  if (bulge_kind == 0 && !(gam >= 0.0 && gam < 3.0)) return false;
   if (!(fabs((double)th[9]) <= 1.0)) return false;
   if (!(th[10] > 0.f && th[11] > 0.f)) return false;
   if (halo_kind == 0 && !(th[13] > 0.f)) return false;
@@ -165,7 +169,7 @@ __device__ inline void decode_finish(const float* __restrict__ th, const double*
   m.inv_ci = (float)(1.0 / ci);
   m.si = (float)si;
   // bulge
-  const double Mb = T[4], a = T[5], gam = th[6];
+  const double Mb = T[4], a = T[5], gam = g.bulge_kind == 0 ? (double)th[6] : (double)g.bulge_kind;
   m.inv_a = (float)(1.0 / a);
   m.ngam = (float)(-gam);
   m.g4 = (float)(gam - 4.0);
@@ -174,6 +178,11 @@ __device__ inline void decode_finish(const float* __restrict__ th, const double*
   m.cS = (float)((3.0 - gam) * Mb / (2.0 * kPi * a * a));
   m.cQ = (float)(kG * (3.0 - gam) * Mb * Mb / (2.0 * kPi * a * a * a));
   m.vb_c = (float)(kG * Mb / a);
+  m.bulge_fit = g.bulge_kind;
+  if (g.bulge_kind != 0) {   // closed-form fits: Sigma = (M / a^2) F_S, Sigma sigma^2 = (G M^2 / a^3) F_Q
+    m.cS = (float)(Mb / (a * a));
+    m.cQ = (float)(kG * Mb * Mb / (a * a * a));
+  }
   m.Lb = (float)(1e-6 / (double)th[10]);
   // halo
   m.hern = halo_kind;
@@ -210,7 +219,7 @@ __device__ inline void decode_finish(const float* __restrict__ th, const double*
 // theta -> per-model constants by one thread; 0 for a row outside the domain.
 __device__ inline int decode_model(const float* __restrict__ th, int nd, int halo_kind, const GalDev& g,
                                    ModelConst& m) {
-  if (!theta_in_domain(th, nd, halo_kind)) return 0;
+  if (!theta_in_domain(th, nd, halo_kind, g.bulge_kind)) return 0;
   double T[kDecodeTerms];
   const double l10k = decode_l10k();
   for (int i = 0; i < kDecodeTerms; ++i) T[i] = decode_term(i, th, nd, halo_kind, l10k);
@@ -341,6 +350,37 @@ __device__ __forceinline__ void bulge_projected(const ModelConst& m, float R, fl
   SigS2 = m.cQ * pQ * Q;
 }
 
+// Projected density and Sigma sigma^2 of the closed-form bulges (bulge_kind 1 Hernquist,
+// 2 Jaffe; Eqs. 4-6, B4-B5) from the fits of bulge_fit.h: Sigma = (M / a^2) F_S(s),
+// Sigma sigma^2 = (G M^2 / a^3) F_Q(s), s = R / a, log2 F = E_k + p_k(u) on unit pieces of
+// t = log2 s.  With sS, sQ also the slopes d ln F / d ln s (the adjoint's).
+__device__ __forceinline__ void bulge_closed(const ModelConst& m, float R, float& Sigma, float& SigS2,
+                                             float* sS = nullptr, float* sQ = nullptr) {
+  const int kind = m.bulge_fit - 1;
+  const float t = lg2_approx(R * m.inv_a) - (float)BANG_BULGE_FIT_T0;
+  int k = (int)floorf(t);
+  k = k < 0 ? 0 : (k > BANG_BULGE_FIT_N - 1 ? BANG_BULGE_FIT_N - 1 : k);   // the edge pieces extrapolate
+  const float u = t - (float)k;
+  const float* cS = kBulgeFitC[kind][0][k];
+  const float* cQ = kBulgeFitC[kind][1][k];
+  float pS = cS[BANG_BULGE_FIT_DEG], pQ = cQ[BANG_BULGE_FIT_DEG], dS = 0.f, dQ = 0.f;
+#pragma unroll
+  for (int i = BANG_BULGE_FIT_DEG - 1; i >= 0; --i) {
+    if (sS) {
+      dS = fmaf(dS, u, pS);
+      dQ = fmaf(dQ, u, pQ);
+    }
+    pS = fmaf(pS, u, cS[i]);
+    pQ = fmaf(pQ, u, cQ[i]);
+  }
+  Sigma = m.cS * kBulgeFitScale[kind][0][k] * ex2_approx(pS);
+  SigS2 = m.cQ * kBulgeFitScale[kind][1][k] * ex2_approx(pQ);
+  if (sS) {
+    *sS = dS;
+    *sQ = dQ;
+  }
+}
+
 // ---------------------------------------------------------------- radial table (option)
 // Per parameter vector, the projected density Sigma and Q = Sigma sigma^2 of the bulge are
 // computed by the same radial quadrature at T radii uniformly spaced in t = log2(R / a),
@@ -459,6 +499,8 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
     const TabPos tp = table_pos(tab, T, R * m.inv_a);
     Sb = table_value(tab, T, TAB_VS, tp);
     SbS2 = table_value(tab, T, TAB_VQ, tp);
+  } else if (m.bulge_fit) {
+    bulge_closed(m, R, Sb, SbS2);
   } else if (nodew) {
     bulge_projected_w<NQ>(m, nodew, R, Sb, SbS2);
   } else {

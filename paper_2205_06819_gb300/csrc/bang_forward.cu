@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       for (int t = tid; t < nt; t += kThreads) tab[t] = __ldg(src + t);
     }
     if (tid < 2) chunk_ctr[tid] = 0;
-    if (!tab) fill_node_weights<NQ>(mc, nodew, tid, kThreads);
+    if (!tab && !mc.bulge_fit) fill_node_weights<NQ>(mc, nodew, tid, kThreads);
     __syncthreads();
 
     double chi_thread = 0.0, vsys_thread = 0.0;
@@ -309,7 +309,8 @@ __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, in
   const int lane = threadIdx.x & 31;
   if (b >= B) return;   // whole warps: b is uniform across the warp
   const float* th = theta + (size_t)b * P;
-  const bool ok = theta_in_domain(th, nd, halo_kind);
+  const GalDev& gal = gals[row_g[b]];
+  const bool ok = theta_in_domain(th, nd, halo_kind, gal.bulge_kind);
   const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
   double T[kDecodeTerms];
 #pragma unroll
@@ -318,7 +319,7 @@ __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, in
   ModelConst m;
   m.valid = 0;
   if (ok) {
-    decode_finish(th, T, nd, halo_kind, gals[row_g[b]], m);
+    decode_finish(th, T, nd, halo_kind, gal, m);
     m.valid = 1;
   }
   out[b] = m;

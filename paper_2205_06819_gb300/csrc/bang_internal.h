@@ -91,8 +91,8 @@ cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const in
 const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d);
 cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
                            cudaStream_t st);
-cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, const double* acc, int B,
-                            float* grad, cudaStream_t st);
+cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind, const double* acc,
+                            int B, float* grad, cudaStream_t st);
 size_t model_const_bytes();
 cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
                           int B, ModelConst* out, cudaStream_t st);

@@ -56,7 +56,8 @@ __global__ void plain_bulge(const GalDev* __restrict__ gal, const ModelConst* __
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= gal->W * gal->H || !mcp->valid) return;
   float S, Q;
-  bulge_projected<NQ>(*mcp, b.R[p], S, Q);
+  if (mcp->bulge_fit) bulge_closed(*mcp, b.R[p], S, Q);
+  else bulge_projected<NQ>(*mcp, b.R[p], S, Q);
   b.Sb[p] = S;
   b.Qb[p] = Q;
 }

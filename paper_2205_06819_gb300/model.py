@@ -52,12 +52,12 @@ class Model:
     """A likelihood model over one or more galaxies (bang_model_create)."""
 
     def __init__(self, galaxies, n_discs: int = 1, n_quad: int = 64, device: int = 0, bulge_table: int = 0,
-                 halo_kind: int = 0, psf_mode: int = 0):
+                 halo_kind: int = 0, psf_mode: int = 0, bulge_kind: int = 0):
         if isinstance(galaxies, Galaxy):
             galaxies = [galaxies]
         self.galaxies = list(galaxies)
         self.n_discs, self.n_quad, self.device, self.bulge_table = n_discs, n_quad, device, bulge_table
-        self.halo_kind, self.psf_mode = halo_kind, psf_mode
+        self.halo_kind, self.psf_mode, self.bulge_kind = halo_kind, psf_mode, bulge_kind
         L = _lib.lib()
         keep = []
         descs = (_lib.GalaxyDesc * len(self.galaxies))()
@@ -71,7 +71,7 @@ class Model:
             d.psf_kind, d.psf_fwhm_arcsec, d.moffat_beta = g.psf_kind, g.psf_fwhm_arcsec, g.moffat_beta
             d.data, d.err = data.ctypes.data, err.ctypes.data
             d.mask = None if mask is None else mask.ctypes.data
-        opts = _lib.ModelOpts(n_discs, 0, halo_kind, n_quad, psf_mode, bulge_table)
+        opts = _lib.ModelOpts(n_discs, bulge_kind, halo_kind, n_quad, psf_mode, bulge_table)
         h = ctypes.c_void_p()
         _lib.check(L.bang_model_create(descs, len(self.galaxies), ctypes.byref(opts), device, ctypes.byref(h)))
         self._h = h
