@@ -44,7 +44,7 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 128.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "f3c01e63c21af6cf", "bytes_per_launch": 562688}
+NCU_TRAFFIC = {"stamp": "921c8b69b1d5a1f7", "bytes_per_launch": 462080}
 
 
 def kernel_stamp() -> str:
@@ -72,6 +72,10 @@ def parse():
                     help="time logL + gradient (bang_loglike_grad_batch) instead of logL")
     ap.add_argument("--bulge-table", type=int, default=0,
                     help="radial-table option with T radii (0: per-point quadrature, the method as defined)")
+    ap.add_argument("--bulge-kind", type=int, default=0,
+                    help="1 Hernquist / 2 Jaffe closed-form bulge instead of the Dehnen quadrature")
+    ap.add_argument("--psf-mode", type=int, default=0,
+                    help="PSF mode bits: 1 circular window, 2 centre sampling, 4 flux-weighted moments")
     return ap.parse_args()
 
 
@@ -171,7 +175,7 @@ def sfu_peak_ops_per_s(n_quad: int, mhz: float, sms: int) -> float:
 
 
 # ----------------------------------------------------------------------------- data
-def make_model(wl: synth.Workload, rank: int, torch, bulge_table: int = 0):
+def make_model(wl: synth.Workload, rank: int, torch, bulge_table: int = 0, bulge_kind: int = 0, psf_mode: int = 0):
     """Seeded synthetic galaxies: noise-free maps from the library at each galaxy's
     theta_true plus noise; the batch is rows_per_galaxy rows per galaxy."""
     from paper_2205_06819_gb300.model import Galaxy, Model
@@ -181,7 +185,7 @@ def make_model(wl: synth.Workload, rank: int, torch, bulge_table: int = 0):
     probes = [Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec,
                      np.ones((4, s.ny, s.nx), np.float32), np.ones((4, s.ny, s.nx), np.float32),
                      psf_kind=s.psf_kind, moffat_beta=s.moffat_beta) for s in wl.galaxies]
-    probe = Model(probes, n_discs=wl.n_discs, n_quad=wl.n_quad)
+    probe = Model(probes, n_discs=wl.n_discs, n_quad=wl.n_quad, bulge_kind=bulge_kind, psf_mode=psf_mode)
     gi = np.arange(len(wl.galaxies), dtype=np.int32)
     true = probe.maps(torch.from_numpy(np.stack(tts).astype(np.float32)).cuda(), gi if len(gi) > 1 else None)
     probe.close()
@@ -190,7 +194,8 @@ def make_model(wl: synth.Workload, rank: int, torch, bulge_table: int = 0):
         data, err, mask = synth.noisy_data(true[g].cpu().numpy().astype(np.float64), seed=synth.dataset_seed(wid, g))
         gals.append(Galaxy(s.nx, s.ny, s.oversample, s.psf_fwhm_arcsec, s.kpc_per_arcsec, data, err, mask,
                            psf_kind=s.psf_kind, moffat_beta=s.moffat_beta))
-    model = Model(gals, n_discs=wl.n_discs, n_quad=wl.n_quad, bulge_table=bulge_table)
+    model = Model(gals, n_discs=wl.n_discs, n_quad=wl.n_quad, bulge_table=bulge_table, bulge_kind=bulge_kind,
+                  psf_mode=psf_mode)
     seed = rank_batch_seed(wid, rank)
     theta = np.concatenate([synth.draw_theta_batch(box, tts[g], wl.rows_per_galaxy, seed + 7 * g)
                             for g in range(len(gals))]).astype(np.float32)
@@ -378,7 +383,8 @@ def run_ours(args):
     from paper_2205_06819_gb300 import build as bmod
     bmod.build()
     wl = synth.workload(args.workload)
-    model, gals, theta_np, gal_idx = make_model(wl, rank, torch, bulge_table=args.bulge_table)
+    model, gals, theta_np, gal_idx = make_model(wl, rank, torch, bulge_table=args.bulge_table,
+                                                bulge_kind=args.bulge_kind, psf_mode=args.psf_mode)
     gal = gals[0]
     B_full = theta_np.shape[0]
     if args.rows:
@@ -395,7 +401,7 @@ def run_ours(args):
             return model.loglike(th, gal_idx, out=out)
     # kernels per step: decode, forward, finalize (+ the table kernel; + adjoint and gradient map)
     launches_per_step = 3 + (1 if args.bulge_table else 0) + (2 if args.grad else 0)
-    headline = not (args.rows or args.grad or args.bulge_table)
+    headline = not (args.rows or args.grad or args.bulge_table or args.bulge_kind or args.psf_mode)
     theta = torch.from_numpy(theta_np).cuda()
     logL = torch.empty(B, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -469,7 +475,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{wl.name}: {wl.description}", "rows": B, "rows_of_workload": B_full,
                    "path": ("logL + gradient" if args.grad else "logL")
-                   + (f", radial table T={args.bulge_table}" if args.bulge_table else ""),
+                   + (f", radial table T={args.bulge_table}" if args.bulge_table else "")
+                   + (f", closed-form bulge kind {args.bulge_kind}" if args.bulge_kind else "")
+                   + (f", psf_mode {args.psf_mode}" if args.psf_mode else ""),
                    "padded_fine_points_per_row": points_per_eval(wl.galaxies[0]) if len(wl.galaxies) == 1 else
                    "per galaxy", "n_quad": wl.n_quad, "galaxies": len(wl.galaxies),
                    "l2": "flushed between steps (256 MiB write outside the timed events)"},
@@ -485,8 +493,9 @@ def run_ours(args):
         "wall_s_timed": wall,
     }
     if not headline:
-        line["note"] = "profiling case (--rows / --grad / --bulge-table), not the headline configuration"
-        if args.grad or args.bulge_table:
+        line["note"] = ("profiling or variant case (--rows / --grad / --bulge-table / --bulge-kind / --psf-mode), "
+                        "not the headline configuration")
+        if args.grad or args.bulge_table or args.bulge_kind or args.psf_mode:
             line["roofline"] = None        # the SFU count above is the forward per-point quadrature's
     if ws == 1 and headline and not args.no_extras and len(wl.galaxies) == 1:
         line["plain_gpu"] = time_plain(model, theta, logL, B)
