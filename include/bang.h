@@ -164,6 +164,21 @@ int64_t bang_model_maps_size(const bang_model *m, const int32_t *gal_idx, int B)
 bang_status bang_loglike_plain(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
                                double *logL, void *stream);
 
+/* One galaxy observed on several spaxel grids (the paper's tool takes maps with different
+   numbers of pixels, Sec. 3.2): galaxies grids[0 .. n_grids) of the model are grids of the
+   same galaxy (sky coordinates centred on the same point), each usually masked to the maps
+   it holds (e.g. B on a fine photometric grid, v and sigma on a coarse kinematic one).
+   Every parameter vector is evaluated against each of them:
+     logL[b] = sum_k logL(theta_b, grids[k]),   grad[b] = sum_k d logL(theta_b, grids[k]) / d theta.
+   theta [B][P] f32, logL [B] f64 and grad [B][P] f32 (NULL: no gradient) are host or device
+   pointers; grids is a host array of n_grids galaxy indices (repeats allowed).  The B x
+   n_grids rows run as one batch of bang_loglike_batch / bang_loglike_grad_batch; the sums
+   are formed by a kernel.  Returns BANG_E_INVALID_ARG for null pointers, B < 1, n_grids < 1
+   or an index out of range; scratch of about B x n_grids x (4 P + 8) bytes is kept by the
+   model between calls. */
+bang_status bang_loglike_grids(bang_model *m, const float *theta, int B, const int32_t *grids, int n_grids,
+                               double *logL, float *grad, void *stream);
+
 /* No-allocation variant of bang_loglike_batch.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory while they run.
  *

@@ -54,6 +54,7 @@ _SIGNATURES = {
     "bang_model_maps": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "bang_model_maps_size": (ctypes.c_int64, [_VP, _VP, ctypes.c_int]),
     "bang_loglike_plain": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    "bang_loglike_grids": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP]),
     "bang_loglike_batch_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "bang_model_tune": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "bang_last_error": (ctypes.c_char_p, []),

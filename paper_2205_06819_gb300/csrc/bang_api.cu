@@ -309,6 +309,8 @@ struct bang_model {
   std::vector<std::unique_ptr<DevBuf>> owned;
   DevBuf d_gals;
   DevBuf stage_theta, stage_out, stage_out2, scratch_seed, scratch_grad, scratch_plain;
+  DevBuf grids_in, grids_theta, grids_out;   // bang_loglike_grids: staged theta, expanded rows, sums
+  std::mutex grids_mu;
   std::list<std::unique_ptr<Plan>> plans;   // most recently used first
   struct Tuning {
     int G = 4;       // fine rows per block step of the forward kernel
@@ -882,6 +884,51 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   if (!g_dev) BANG_CUDA(cudaMemcpyAsync(grad, d_grad, th_bytes, cudaMemcpyDeviceToHost, st));
   if (!th_dev || !l_dev || !g_dev) BANG_CUDA(cudaStreamSynchronize(st));
+  return BANG_OK;
+}
+
+bang_status bang_loglike_grids(bang_model* m, const float* theta, int B, const int32_t* grids, int n_grids,
+                               double* logL, float* grad, void* stream) {
+  g_last_error.clear();
+  if (!m) return fail(BANG_E_INVALID_ARG, "null model");
+  if (!theta || !logL || !grids || B < 1 || n_grids < 1)
+    return fail(BANG_E_INVALID_ARG, "theta, logL or grids is null, or B < 1, or n_grids < 1");
+  for (int k = 0; k < n_grids; ++k)
+    if (grids[k] < 0 || grids[k] >= (int)m->gals.size())
+      return fail(BANG_E_INVALID_ARG, "grids[%d] = %d out of range", k, grids[k]);
+  if ((int64_t)B * n_grids > (int64_t)1 << 30) return fail(BANG_E_INVALID_ARG, "B x n_grids too large");
+  std::lock_guard<std::mutex> lock(m->grids_mu);
+  BANG_CUDA(cudaSetDevice(m->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int P = m->P, BX = B * n_grids;
+  const size_t th_bytes = sizeof(float) * (size_t)B * P, thx_bytes = sizeof(float) * (size_t)BX * P;
+  const float* d_theta = theta;
+  if (!is_device_pointer(theta)) {
+    BANG_CUDA(m->grids_in.reserve(th_bytes));
+    BANG_CUDA(cudaMemcpyAsync(m->grids_in.p, theta, th_bytes, cudaMemcpyHostToDevice, st));
+    d_theta = m->grids_in.as<float>();
+  }
+  // expanded rows, their logL and gradients, and the sums (when the caller's buffers are on the host)
+  const size_t lx = sizeof(double) * (size_t)BX, gx = grad ? thx_bytes : 0;
+  const size_t sl = sizeof(double) * (size_t)B, sg = grad ? th_bytes : 0;
+  BANG_CUDA(m->grids_theta.reserve(thx_bytes));
+  BANG_CUDA(m->grids_out.reserve(lx + gx + sl + sg + 64));
+  double* logL_x = m->grids_out.as<double>();
+  float* grad_x = grad ? reinterpret_cast<float*>(m->grids_out.as<char>() + lx) : nullptr;
+  const bool l_dev = is_device_pointer(logL), g_dev = !grad || is_device_pointer(grad);
+  double* d_logL = l_dev ? logL : reinterpret_cast<double*>(m->grids_out.as<char>() + lx + gx);
+  float* d_grad = !grad ? nullptr : (g_dev ? grad : reinterpret_cast<float*>(m->grids_out.as<char>() + lx + gx + sl));
+  BANG_CUDA(bang::launch_expand_rows(d_theta, P, B, n_grids, m->grids_theta.as<float>(), st));
+  std::vector<int32_t> gal_x((size_t)BX);
+  for (int b = 0; b < B; ++b)
+    for (int k = 0; k < n_grids; ++k) gal_x[(size_t)b * n_grids + k] = grids[k];
+  bang_status s = grad ? bang_loglike_grad_batch(m, m->grids_theta.as<float>(), gal_x.data(), BX, logL_x, grad_x, stream)
+                       : bang_loglike_batch(m, m->grids_theta.as<float>(), gal_x.data(), BX, logL_x, stream);
+  if (s != BANG_OK) return s;
+  BANG_CUDA(bang::launch_sum_rows(logL_x, grad_x, P, B, n_grids, d_logL, d_grad, st));
+  if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sl, cudaMemcpyDeviceToHost, st));
+  if (!g_dev) BANG_CUDA(cudaMemcpyAsync(grad, d_grad, sg, cudaMemcpyDeviceToHost, st));
+  BANG_CUDA(cudaStreamSynchronize(st));   // the staged and expanded buffers are reused by the next call
   return BANG_OK;
 }
 

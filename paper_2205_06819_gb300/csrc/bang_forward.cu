@@ -406,6 +406,43 @@ cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind,
   return cudaGetLastError();
 }
 
+// Rows of several grids of one galaxy: theta_x[b n + k] = theta[b] (expand), and
+// logL[b] = sum_k logL_x[b n + k], grad[b] = sum_k grad_x[b n + k] (sum).
+__global__ void expand_rows_kernel(const float* __restrict__ theta, int P, int B, int n, float* __restrict__ theta_x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)B * n * P;
+  if (t >= total) return;
+  const int64_t row = t / P, p = t - row * P;
+  theta_x[t] = theta[(row / n) * P + p];
+}
+
+__global__ void sum_rows_kernel(const double* __restrict__ logL_x, const float* __restrict__ grad_x, int P, int B, int n,
+                                double* __restrict__ logL, float* __restrict__ grad) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) s += logL_x[(size_t)b * n + k];
+  logL[b] = s;
+  if (!grad) return;
+  for (int p = 0; p < P; ++p) {
+    double g = 0.0;
+    for (int k = 0; k < n; ++k) g += (double)grad_x[((size_t)b * n + k) * P + p];
+    grad[(size_t)b * P + p] = (float)g;
+  }
+}
+
+cudaError_t launch_expand_rows(const float* theta, int P, int B, int n, float* theta_x, cudaStream_t st) {
+  const int64_t total = (int64_t)B * n * P;
+  expand_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(theta, P, B, n, theta_x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_rows(const double* logL_x, const float* grad_x, int P, int B, int n, double* logL, float* grad,
+                            cudaStream_t st) {
+  sum_rows_kernel<<<(B + 127) / 128, 128, 0, st>>>(logL_x, grad_x, P, B, n, logL, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
                             double* logL, cudaStream_t st) {
   finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(partial, row_first, row_g, gals, B, logL);

@@ -77,6 +77,9 @@ size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d, int ta
 const void* forward_kernel_ptr(int n_quad, int n_discs, int psf2d, int mode);
 cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d, int mode, int grid, size_t smem,
                            cudaStream_t st);
+cudaError_t launch_expand_rows(const float* theta, int P, int B, int n, float* theta_x, cudaStream_t st);
+cudaError_t launch_sum_rows(const double* logL_x, const float* grad_x, int P, int B, int n, double* logL, float* grad,
+                            cudaStream_t st);
 cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
                             double* logL, cudaStream_t st);
 cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float* ws, const float* wq);

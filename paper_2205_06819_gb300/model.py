@@ -128,6 +128,20 @@ class Model:
                                                       _stream_handle(theta.device) if theta.is_cuda else None))
         return logL, grad
 
+    def loglike_grids(self, theta: torch.Tensor, grids, grad: bool = False):
+        """logL [B] (and d logL / d theta [B, P] with grad=True) of one galaxy observed on the
+        model's galaxies ``grids`` (its maps on several spaxel grids): the sum over the grids
+        (bang_loglike_grids)."""
+        theta = self._check_theta(theta)
+        B = theta.shape[0]
+        g = np.ascontiguousarray(np.asarray(grids, dtype=np.int32).reshape(-1))
+        logL = torch.empty(B, dtype=torch.float64, device=theta.device)
+        gr = torch.empty_like(theta) if grad else None
+        _lib.check(_lib.lib().bang_loglike_grids(self._h, _ptr(theta), B, ctypes.c_void_p(g.ctypes.data), len(g),
+                                                 _ptr(logL), _ptr(gr),
+                                                 _stream_handle(theta.device) if theta.is_cuda else None))
+        return (logL, gr) if grad else logL
+
     def loglike_plain(self, theta: torch.Tensor, gal_idx=None) -> torch.Tensor:
         """logL through the one-kernel-per-task chain (the paper's Alg. 2 form)."""
         theta = self._check_theta(theta)
