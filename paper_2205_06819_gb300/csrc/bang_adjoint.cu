@@ -366,12 +366,12 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int next_item;
-  __shared__ int pt_ctr;
   __shared__ float2 nodew[NQ];
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
   for (int it = blockIdx.x; it < a.n_items;) {
-    const WorkItem w = a.items[a.order ? a.order[it] : it];
+    const int item_id = a.order ? a.order[it] : it;
+    const WorkItem w = a.items[item_id];
     if (tid == 0) {
       gs = a.gals[w.g];
       mc = a.consts[w.b];
@@ -408,7 +408,6 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
       const int jhi = min(ny - 1, (y0 + G - 1) / os);
       const int nj = jhi - jlo + 1;
       __syncthreads();   // taps loaded / previous chunk's lam and V no longer read
-      if (tid == 0) pt_ctr = 0;
       for (int t = tid; t < nj * nx; t += kAdjThreads) {
         const int s = (jlo + t / nx) * nx + (t % nx);
         lam[t] = make_float4(__ldg(seed + s), __ldg(seed + n + s), __ldg(seed + 2 * n + s), __ldg(seed + 3 * n + s));
@@ -435,11 +434,9 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
       // point VJPs, 32 points per grab from the shared counter (balances the warps)
       const int npts = G * W;
       const float inv_W = 1.0f / (float)W;
-      for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&pt_ctr, 32);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= npts) break;
+      // 32-point batches in a fixed order (warp w takes batches w, w + 8, ...): every
+      // accumulation order is fixed, so the gradient is the same bits on every call
+      for (int base = warp * 32; base < npts; base += kAdjThreads) {
         const int p = base + lane;
         if (p >= npts) continue;
         const int gr = __float2int_rz(((float)p + 0.5f) * inv_W);   // p + 1/2 is never a multiple of W
@@ -480,20 +477,24 @@ __global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
       if (lane == 0) red[warp][k] = v;
     }
     __syncthreads();
-    if (tid < NACC) {   // one thread per accumulator: sum over warps, add to the row's slot
+    if (tid < NACC) {   // one thread per accumulator: sum over warps into the item's slots
       double sum = 0.0;
       for (int q = 0; q < kAdjThreads / 32; ++q) sum += red[q][tid];
-      if (sum != 0.0) atomicAdd(a.grad_acc + (size_t)w.b * kGradAccStride + tid, sum);
+      a.acc_partial[(size_t)item_id * kAdjSlots + tid] = sum;
     }
     BANG_NEXT_ITEM(it);
   }
 }
 
-// One warp per row: the reduced constant adjoints -> d logL / d theta (float64), or zero
-// for a row outside the parameter domain.  As in decode_kernel, lane i < kDecodeTerms
-// evaluates decode term i and lane 0 does the rest.
+// One warp per row: the constant adjoints of the row's work items, summed in item order
+// (lane k < kAdjSlots sums slot k, lane kVsysSlot the forward items' d logL / d v_sys),
+// then mapped to d logL / d theta (float64), or zero for a row outside the parameter
+// domain.  As in decode_kernel, lane i < kDecodeTerms also evaluates decode term i and
+// lane 0 does the rest.  No atomics: the gradient is the same bits on every call.
 __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind, int bulge_kind,
-                                const double* __restrict__ acc, int B, double l10k, float* __restrict__ grad) {
+                                const double* __restrict__ acc_partial, const int* __restrict__ adj_row_first,
+                                const double* __restrict__ vsys_partial, const int* __restrict__ row_first, int B,
+                                double l10k, float* __restrict__ grad) {
   const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (b >= B) return;   // whole warps
@@ -503,11 +504,19 @@ __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, 
   double T[kDecodeTerms];
 #pragma unroll
   for (int i = 0; i < kDecodeTerms; ++i) T[i] = __shfl_sync(0xffffffffu, v, i);
+  double sum = 0.0;
+  if (ok && lane < kAdjSlots) {
+    for (int i = adj_row_first[b]; i < adj_row_first[b + 1]; ++i) sum += acc_partial[(size_t)i * kAdjSlots + lane];
+  } else if (ok && lane == kVsysSlot) {
+    for (int i = row_first[b]; i < row_first[b + 1]; ++i) sum += vsys_partial[i];
+  }
+  double s[kVsysSlot + 1];
+#pragma unroll
+  for (int k = 0; k <= kVsysSlot; ++k) s[k] = __shfl_sync(0xffffffffu, sum, k);
   if (lane != 0) return;
   double g[kMaxParams];
   for (int p = 0; p < kMaxParams; ++p) g[p] = 0.0;
   if (ok) {
-    const double* s = acc + (size_t)b * kGradAccStride;
     constants_to_theta(th, T, nd, halo_kind, bulge_kind, s, g);
     g[14] = s[kVsysSlot];
   }
@@ -622,12 +631,13 @@ cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const in
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind, const double* acc,
-                            int B, float* grad, cudaStream_t st) {
+cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind,
+                            const double* acc_partial, const int* adj_row_first, const double* vsys_partial,
+                            const int* row_first, int B, float* grad, cudaStream_t st) {
   constexpr int kRowsPerBlock = 4;   // 4 warps, one row each
   const double l10k = std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit));
   grad_out_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(
-      theta, P, n_discs, halo_kind, bulge_kind, acc, B, l10k, grad);
+      theta, P, n_discs, halo_kind, bulge_kind, acc_partial, adj_row_first, vsys_partial, row_first, B, l10k, grad);
   return cudaGetLastError();
 }
 

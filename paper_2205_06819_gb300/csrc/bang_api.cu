@@ -266,7 +266,7 @@ struct Plan {
   // adjoint sweep (kModeSeed plans only): bands of fine rows
   int adj_items = 0, adj_G = 4, adj_grid = 0;
   size_t adj_smem = 0;
-  DevBuf d_adj_items, d_adj_order;
+  DevBuf d_adj_items, d_adj_order, d_adj_row_first;
   // graph replay
   cudaGraphExec_t graph = nullptr;
   const void* g_theta = nullptr;
@@ -320,6 +320,7 @@ struct bang_model {
   std::mutex mu;
   ScratchBudget budget;
   cudaStream_t capture_stream = nullptr;
+  cudaEvent_t last_work = nullptr;   // recorded after each call's device work (see CallOrder)
   bool use_graphs = true;
 };
 
@@ -481,13 +482,16 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     p->adj_G = rows;
     std::vector<bang::WorkItem> ai;
     std::vector<double> acost;
+    std::vector<int> arow_first(B + 1, 0);
     for (int b = 0; b < B; ++b) {
       const bang::GalDev& G = m->gals[p->row_g[b]];
+      arow_first[b] = (int)ai.size();
       for (int y = 0; y < G.H; y += rows) {
         ai.push_back(bang::WorkItem{b, p->row_g[b], y, std::min(G.H, y + rows)});
         acost.push_back((double)(std::min(G.H, y + rows) - y) * G.W);
       }
     }
+    arow_first[B] = (int)ai.size();
     std::vector<int> aorder(ai.size());
     for (size_t i = 0; i < ai.size(); ++i) aorder[i] = (int)i;
     std::stable_sort(aorder.begin(), aorder.end(), [&](int x, int y) { return acost[x] > acost[y]; });
@@ -511,6 +515,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     p->adj_grid = std::min(p->adj_items, aper * m->num_sms);
     BANG_CUDA(copy_vec(p->d_adj_items, ai));
     BANG_CUDA(copy_vec(p->d_adj_order, aorder));
+    BANG_CUDA(copy_vec(p->d_adj_row_first, arow_first));
   }
   BANG_CUDA(copy_vec(p->d_items, p->items));
   BANG_CUDA(copy_vec(p->d_order, p->order));
@@ -533,7 +538,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
 int psf2d_of(const bang_model* m, const Plan* p) { return m->gals[p->row_g[0]].psf_kind; }
 
 cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode, double* logL, float* out,
-                            cudaStream_t st, double* grad_acc = nullptr) {
+                            cudaStream_t st, double* vsys_partial = nullptr) {
   bang::FwdArgs a{};
   a.theta = theta;
   a.P = m->P;
@@ -545,7 +550,7 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.partial = p->d_partial.as<double>();
   a.maps = mode == bang::kModeMaps ? out : nullptr;
   a.seed = mode == bang::kModeSeed ? out : nullptr;
-  a.grad_acc = mode == bang::kModeSeed ? grad_acc : nullptr;
+  a.vsys_partial = mode == bang::kModeSeed ? vsys_partial : nullptr;
   a.out_off = p->d_out_off.as<int64_t>();
   a.queue = p->d_queue.as<int>();
   a.consts = p->d_consts.as<bang::ModelConst>();
@@ -569,11 +574,17 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   return bang::launch_finalize(a.partial, p->d_row_first.as<int>(), p->d_row_g.as<int>(), a.gals, p->B, logL, st);
 }
 
-cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* logL, float* seed, double* grad_acc,
+// Scratch of a gradient call: the forward items' d logL / d v_sys, then the adjoint items'
+// constant adjoints (every slot is written before it is read: no zeroing).
+size_t grad_scratch_bytes(const Plan* p) {
+  return sizeof(double) * ((size_t)std::max(1, p->n_items) + (size_t)std::max(1, p->adj_items) * bang::kAdjSlots);
+}
+
+cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* logL, float* seed, double* scratch,
                          float* grad, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->B * bang::kGradAccStride, st);
-  if (e != cudaSuccess) return e;
-  e = enqueue_forward(m, p, theta, bang::kModeSeed, logL, seed, st, grad_acc);
+  double* vsys_partial = scratch;
+  double* acc_partial = scratch + std::max(1, p->n_items);
+  cudaError_t e = enqueue_forward(m, p, theta, bang::kModeSeed, logL, seed, st, vsys_partial);
   if (e != cudaSuccess) return e;
   bang::AdjArgs a{};
   a.theta = theta;
@@ -586,7 +597,7 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   a.G = p->adj_G;
   a.seed = seed;
   a.out_off = p->d_out_off.as<int64_t>();
-  a.grad_acc = grad_acc;
+  a.acc_partial = acc_partial;
   if (m->opts.bulge_table > 0) {
     a.tables = p->d_tables.as<float>();
     a.table_T = m->opts.bulge_table;
@@ -597,8 +608,8 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   if (e != cudaSuccess) return e;
   e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
   if (e != cudaSuccess) return e;
-  return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, m->opts.bulge_kind, grad_acc, p->B,
-                               grad, st);
+  return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, m->opts.bulge_kind, acc_partial,
+                               p->d_adj_row_first.as<int>(), vsys_partial, p->d_row_first.as<int>(), p->B, grad, st);
 }
 
 }  // namespace
@@ -722,6 +733,7 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
   }
   BANG_CUDA(copy_vec(m->d_gals, m->gals));
   BANG_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+  BANG_CUDA(cudaEventCreateWithFlags(&m->last_work, cudaEventDisableTiming));
   *out = m.release();
   return BANG_OK;
 }
@@ -731,6 +743,7 @@ bang_status bang_model_destroy(bang_model* m) {
   cudaSetDevice(m->device);
   cudaDeviceSynchronize();
   if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+  if (m->last_work) cudaEventDestroy(m->last_work);
   delete m;
   return BANG_OK;
 }
@@ -770,6 +783,16 @@ namespace {
 
 // Common driver of the forward-type entry points: stages host buffers, runs (or replays)
 // the persistent launch and the finalisation, copies results back for host buffers.
+// Orders a call's device work after the previous call's on the same model, whatever streams
+// the callers use: the model's staging buffers, scratch and plans are shared by its calls
+// (the host side is already serialised by the model's mutex).
+struct CallOrder {
+  bang_model* m;
+  cudaStream_t st;
+  CallOrder(bang_model* m_, cudaStream_t s) : m(m_), st(s) { cudaStreamWaitEvent(st, m->last_work, 0); }
+  ~CallOrder() { cudaEventRecord(m->last_work, st); }
+};
+
 bang_status run_forward(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL, float* maps,
                         int mode, void* stream) {
   g_last_error.clear();
@@ -781,6 +804,7 @@ bang_status run_forward(bang_model* m, const float* theta, const int32_t* gal_id
   ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CallOrder order(m, st);
   Plan* p = nullptr;
   bang_status s = get_plan(m, gal_idx, B, mode, &p);
   if (s != BANG_OK) return s;
@@ -860,6 +884,7 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
   ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CallOrder order(m, st);
   Plan* p = nullptr;
   bang_status s = get_plan(m, gal_idx, B, bang::kModeSeed, &p);
   if (s != BANG_OK) return s;
@@ -879,7 +904,7 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
     if (!g_dev) d_grad = reinterpret_cast<float*>(m->stage_out.as<char>() + sizeof(double) * B);
   }
   BANG_CUDA(m->scratch_seed.reserve(sizeof(float) * (size_t)std::max<int64_t>(p->out_total, 4)));
-  BANG_CUDA(m->scratch_grad.reserve(sizeof(double) * (size_t)B * bang::kGradAccStride));
+  BANG_CUDA(m->scratch_grad.reserve(grad_scratch_bytes(p)));
   BANG_CUDA(enqueue_grad(m, p, d_theta, d_logL, m->scratch_seed.as<float>(), m->scratch_grad.as<double>(), d_grad, st));
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   if (!g_dev) BANG_CUDA(cudaMemcpyAsync(grad, d_grad, th_bytes, cudaMemcpyDeviceToHost, st));
@@ -942,6 +967,7 @@ bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t*
   ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CallOrder order(m, st);
   size_t need = 0;
   for (int b = 0; b < B; ++b) {
     const int g = gal_idx ? gal_idx[b] : 0;
@@ -994,6 +1020,7 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   std::vector<float> th((size_t)B * m->P);
   for (int b = 0; b < B; ++b)
     for (int k = 0; k < m->P; ++k) th[(size_t)b * m->P + k] = kTypical[k] + (k == 2 ? 0.001f * (b % 97) : 0.f);
+  BANG_CUDA(cudaEventSynchronize(m->last_work));   // earlier calls may still read the staging buffers
   BANG_CUDA(m->stage_theta.reserve(th.size() * sizeof(float)));
   BANG_CUDA(cudaMemcpy(m->stage_theta.p, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice));
   BANG_CUDA(m->stage_out.reserve(sizeof(double) * B));
@@ -1003,6 +1030,7 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
     for (int nb : {1, 2, 4, 8, 16})
       if (nb <= ny_max) bands.push_back(nb);
   cudaStream_t st = m->capture_stream;
+  CallOrder order(m, st);
   cudaEvent_t e0, e1;
   BANG_CUDA(cudaEventCreate(&e0));
   BANG_CUDA(cudaEventCreate(&e1));

@@ -149,7 +149,10 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           out[c * nx * gs.ny + w.j0 * nx + rem] = 0.f;
         }
       }
-      if (tid == 0) a.partial[item_id] = __longlong_as_double(0x7ff8000000000000ll);
+      if (tid == 0) {
+        a.partial[item_id] = __longlong_as_double(0x7ff8000000000000ll);
+        if (MODE == kModeSeed) a.vsys_partial[item_id] = 0.0;
+      }
       BANG_NEXT_ITEM(it);
       continue;
     }
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       for (int k = 0; k < kThreads / 32; ++k) s += red[k];
       a.partial[item_id] = s;
     }
-    if (MODE == kModeSeed) {   // the item's share of d logL / d v_sys, added to the row's slot
+    if (MODE == kModeSeed) {   // the item's share of d logL / d v_sys (summed per row in fixed order later)
       __syncthreads();         // red is reused
       const double u = warp_sum(vsys_thread);
       if ((tid & 31) == 0) red[tid >> 5] = u;
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       if (tid == 0) {
         double s = 0.0;
         for (int k = 0; k < kThreads / 32; ++k) s += red[k];
-        atomicAdd(a.grad_acc + (size_t)w.b * kGradAccStride + kVsysSlot, s);
+        a.vsys_partial[item_id] = s;
       }
     }
     BANG_NEXT_ITEM(it);

@@ -15,8 +15,8 @@ struct ModelConst;
 
 // Gradient accumulator row: adjoints of the per-model constants (slots 0..23, the second
 // disc's unused for one-disc models) and d logL / d v_sys (slot 24).
-constexpr int kGradAccStride = 25;
-constexpr int kVsysSlot = 24;   // grad_acc slot of d logL / d v_sys (filled by the forward seed pass)
+constexpr int kAdjSlots = 24;   // constant adjoints per adjoint work item (the adjoint kernel's accumulators)
+constexpr int kVsysSlot = 24;   // index of d logL / d v_sys among a row's summed adjoints (from the forward seed pass)
 
 enum { kModeLogL = 0, kModeMaps = 1, kModeSeed = 2 };
 
@@ -35,7 +35,7 @@ struct FwdArgs {
   double* partial;          // [n_items] chi^2 of each item (NaN for an out-of-domain row)
   float* maps;              // kModeMaps: model maps, row b at out_off[b]
   float* seed;              // kModeSeed: d logL / dF per spaxel, row b at out_off[b]
-  double* grad_acc;         // kModeSeed: [B][kGradAccStride]; slot kVsysSlot gets d logL / d v_sys
+  double* vsys_partial;     // kModeSeed: [n_items] d logL / d v_sys of each work item
   const int64_t* out_off;   // [B] float offsets of each row's [4][ny][nx] block
   const float* tables;      // radial tables, row b at b * table_stride (NULL: quadrature per point)
   int table_T;              // radii per table
@@ -55,7 +55,7 @@ struct AdjArgs {
   int G;                    // fine rows per block step
   const float* seed;        // d logL / dF at the spaxels, row b at out_off[b]
   const int64_t* out_off;
-  double* grad_acc;         // [B][kGradAccStride] float64 constant adjoints (zeroed before the launch)
+  double* acc_partial;      // [n_items][kAdjSlots] float64 constant adjoints of each work item
   const float* tables;      // radial tables with slopes, row b at b * table_stride (NULL: quadrature)
   int table_T;
   int64_t table_stride;
@@ -94,8 +94,9 @@ cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const in
 const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d);
 cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
                            cudaStream_t st);
-cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind, const double* acc,
-                            int B, float* grad, cudaStream_t st);
+cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind,
+                            const double* acc_partial, const int* adj_row_first, const double* vsys_partial,
+                            const int* row_first, int B, float* grad, cudaStream_t st);
 size_t model_const_bytes();
 cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
                           int B, ModelConst* out, cudaStream_t st);
