@@ -41,10 +41,15 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # chains of each PTX instruction (ex2.approx issues at twice the rate of lg2.approx).
 MUFU_EX2_PER_CLK_SM = 32.0
 MUFU_LG2_PER_CLK_SM = 16.0
-FP32_PER_CLK_SM = 128.0
+FP32_PER_CLK_SM = 122.0          # measured FFMA issue (128 nominal)
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "921c8b69b1d5a1f7", "bytes_per_launch": 462080}
+NCU_TRAFFIC = {"stamp": "cde751242eed844b", "bytes_per_launch": 462080}
+# Pipe activity of the forward kernel from the same kind of capture (ncu --set full on 456
+# rows of the benchmark batch): SFU (xu) and FMA pipes, issue active, thread instructions
+# per fine point; stamp-checked like the traffic.
+NCU_PIPES = {"stamp": "cde751242eed844b", "pipe_xu_pct": 46.7, "pipe_fma_pct": 40.9, "issue_active_pct": 70.4,
+             "thread_instr_per_point": 944}
 
 
 def kernel_stamp() -> str:
@@ -150,6 +155,27 @@ def algorithmic_sfu_ops(wl: synth.Workload, gal_idx=None, rows: int | None = Non
         per = [points_per_eval(g) for g in wl.galaxies]
         pts = sum(per[0 if gal_idx is None else int(gal_idx[b])] for b in range(rows))
     return float(pts) * (2 * wl.n_quad + 16)
+
+
+def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = None) -> float:
+    """FP32 instructions of one batch: per padded fine point 6 per radial node (the argument
+    of the logarithm, the exponent, and the two weighted sums with the (q^(g-4))^2 q
+    product) plus ~200 for geometry, velocities, discs and light weighting; per galaxy the
+    PSF stencil (separable: 4 channels x (fine rows x nx + nx x ny) x (os + 2h); two-
+    dimensional: 4 x nx x ny x (os + 2h)^2) and ~40 per spaxel for the chi-square."""
+    def per_row(spec):
+        sig = spec.psf_fwhm_arcsec / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+        h = int(math.floor(3.0 * sig / (spec.spaxel_arcsec / spec.oversample))) if spec.psf_fwhm_arcsec > 0 else 0
+        L = spec.oversample + 2 * h
+        if spec.psf_kind == 1:
+            psf = 4.0 * spec.nx * spec.ny * L * L
+        else:
+            psf = 4.0 * ((spec.oversample * spec.ny + 2 * h) * spec.nx + spec.nx * spec.ny) * L
+        return points_per_eval(spec) * (6.0 * wl.n_quad + 200.0) + psf + 40.0 * spec.nx * spec.ny
+    per = [per_row(g) for g in wl.galaxies]
+    if rows is None:
+        return float(sum(per) * wl.rows_per_galaxy)
+    return float(sum(per[0 if gal_idx is None else int(gal_idx[b])] for b in range(rows)))
 
 
 def combine_max(local: float, dist, device) -> float:
@@ -466,6 +492,12 @@ def run_ours(args):
     ops = algorithmic_sfu_ops(wl, gal_idx, B)
     achieved = ops / step_s / 1e9
     peak = sfu_peak_ops_per_s(wl.n_quad, mhz, sms) / 1e9
+    fp32_ops = algorithmic_fp32_ops(wl, gal_idx, B)
+    fp32_peak = sms * mhz * 1e6 * FP32_PER_CLK_SM / 1e9
+    fp32_achieved = fp32_ops / step_s / 1e9
+    # t_roof = max over the two pipes of algorithmic work / peak, against the measured time
+    t_roof = max(ops / (peak * 1e9), fp32_ops / (fp32_peak * 1e9))
+    pipes = NCU_PIPES if NCU_PIPES["stamp"] == kernel_stamp() else None
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["stamp"] == kernel_stamp() else None
 
     metric = "logL+gradient evals/s" if args.grad else "logL evals/s"
@@ -486,6 +518,10 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SFU op/s", "frac": achieved / peak,
                      "traffic": traffic,
+                     "fp32": {"achieved": fp32_achieved, "peak": fp32_peak, "unit": "G FP32 instr/s",
+                              "frac": fp32_achieved / fp32_peak},
+                     "t_roof_over_t_meas": t_roof / step_s,
+                     "ncu_pipes": pipes,
                      "peak_basis": f"{sms} SMs x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz) x measured per-SM rates "
                                    f"lg2 {MUFU_LG2_PER_CLK_SM:.0f}/clk, ex2 {MUFU_EX2_PER_CLK_SM:.0f}/clk for the "
                                    "radial-rule mix (1 lg2 : 1 ex2)"},
