@@ -75,3 +75,25 @@ def test_noalloc_refuses_batches_beyond_its_scratch(setup):
     assert st == 1                                          # BANG_E_INVALID_ARG
     assert b"32768" in _lib.lib().bang_last_error()
     assert torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("opts", [{"psf_mode": 7}, {"bulge_kind": 1}, {"halo_kind": 1, "psf_mode": 4}])
+def test_noalloc_under_model_options(setup, opts):
+    """The no-allocation launch decodes each row itself; under the PSF modes, the closed-form
+    bulge and the Hernquist halo it must still equal the allocating entry point."""
+    _lib, m0, box, synth = setup
+    from paper_2205_06819_gb300.model import Model
+    m = Model(m0.galaxies, **opts)
+    th = TH1.copy()
+    if opts.get("halo_kind") == 1:
+        th[13] = math.log10(30.0)
+    b = synth.prior_box(1, halo_kind=opts.get("halo_kind", 0))
+    theta = torch.from_numpy(synth.draw_theta_batch(b, th, 64, 95).astype(np.float32)).cuda()
+    out = torch.zeros(64, dtype=torch.float64, device="cuda")
+    _lib.check(noalloc(_lib, m, theta, out))
+    ref = m.loglike(theta).cpu().numpy()
+    got = out.cpu().numpy()
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(got)) and fin.any()
+    assert (np.abs(got[fin] - ref[fin]) / np.abs(ref[fin])).max() < CHI2_RTOL
+    m.close()
