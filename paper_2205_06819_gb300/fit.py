@@ -117,6 +117,7 @@ def run_model(model_name: str, spec, data, err, truth, n_live: int, batch: int, 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--nx", type=int, default=30)
+    ap.add_argument("--ny", type=int, default=0, help="spaxel rows (default: nx)")
     ap.add_argument("--oversample", type=int, default=3)
     ap.add_argument("--psf-fwhm", type=float, default=2.5)
     ap.add_argument("--n-live", type=int, default=300)
@@ -126,7 +127,7 @@ def main(argv=None):
     ap.add_argument("--free-geometry", action="store_true")
     ap.add_argument("--models", default="BD1D2,BD,BD_rot")
     a = ap.parse_args(argv)
-    spec = synth.GalaxySpec(a.nx, a.nx, a.oversample, a.psf_fwhm)
+    spec = synth.GalaxySpec(a.nx, a.ny or a.nx, a.oversample, a.psf_fwhm)
     truth = truth_two_discs()
     data, err, _ = synthetic_data(spec, truth, seed=a.seed)
     out = {}
