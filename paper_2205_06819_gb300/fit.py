@@ -114,6 +114,39 @@ def run_model(model_name: str, spec, data, err, truth, n_live: int, batch: int, 
                  "posterior_median_plus_minus": post}
 
 
+def max_likelihood(model, theta0: np.ndarray, free, lo, hi, iters: int = 60):
+    """Maximum-likelihood fit of the slots ``free`` of theta by L-BFGS on the GPU, the
+    gradient coming from the adjoint through the LogLike autograd function (the likelihood
+    shared with a gradient-based method).  The free slots move in the unit box
+    (theta = lo + (hi - lo) sigmoid(z)); the others stay at theta0.  Returns (theta, logL)."""
+    import torch
+    from .model import LogLike
+    free = np.asarray(free)
+    base = torch.from_numpy(theta0.astype(np.float32)).cuda()
+    lo_t = torch.from_numpy(np.asarray(lo, np.float32)).cuda()
+    span = torch.from_numpy((np.asarray(hi) - np.asarray(lo)).astype(np.float32)).cuda()
+    u0 = np.clip((theta0[free] - lo) / (hi - lo), 1e-4, 1 - 1e-4)
+    z = torch.tensor(np.log(u0 / (1 - u0)), dtype=torch.float32, device="cuda", requires_grad=True)
+    idx = torch.from_numpy(free).cuda()
+    opt = torch.optim.LBFGS([z], lr=1.0, max_iter=iters, line_search_fn="strong_wolfe")
+
+    def theta_of(zv):
+        th = base.clone()
+        th[idx] = lo_t + span * torch.sigmoid(zv)
+        return th[None, :]
+
+    def closure():
+        opt.zero_grad()
+        nll = -LogLike.apply(theta_of(z), model).sum() / 1e4    # scaled for the line search
+        nll.backward()
+        return nll
+
+    opt.step(closure)
+    with torch.no_grad():
+        th = theta_of(z)
+        return th[0].cpu().numpy().astype(np.float64), float(model.loglike(th)[0])
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--nx", type=int, default=30)
