@@ -359,8 +359,10 @@ __device__ __forceinline__ void bulge_closed(const ModelConst& m, float R, float
   const int kind = m.bulge_fit - 1;
   const float t = lg2_approx(R * m.inv_a) - (float)BANG_BULGE_FIT_T0;
   int k = (int)floorf(t);
-  k = k < 0 ? 0 : (k > BANG_BULGE_FIT_N - 1 ? BANG_BULGE_FIT_N - 1 : k);   // the edge pieces extrapolate
-  const float u = t - (float)k;
+  k = k < 0 ? 0 : (k > BANG_BULGE_FIT_N - 1 ? BANG_BULGE_FIT_N - 1 : k);
+  // beyond the fitted range (s outside [2^-48, 2^32)) the edge values hold, with zero slope
+  const bool inside = t >= 0.f && t < (float)BANG_BULGE_FIT_N;
+  const float u = fminf(fmaxf(t - (float)k, 0.f), 1.f);
   const float* cS = kBulgeFitC[kind][0][k];
   const float* cQ = kBulgeFitC[kind][1][k];
   float pS = cS[BANG_BULGE_FIT_DEG], pQ = cQ[BANG_BULGE_FIT_DEG], dS = 0.f, dQ = 0.f;
@@ -376,8 +378,8 @@ __device__ __forceinline__ void bulge_closed(const ModelConst& m, float R, float
   Sigma = m.cS * kBulgeFitScale[kind][0][k] * ex2_approx(pS);
   SigS2 = m.cQ * kBulgeFitScale[kind][1][k] * ex2_approx(pQ);
   if (sS) {
-    *sS = dS;
-    *sQ = dQ;
+    *sS = inside ? dS : 0.f;
+    *sQ = inside ? dQ : 0.f;
   }
 }
 

@@ -16,7 +16,7 @@ done by mpmath quadrature.
 Representation: t = log2 s in [T0, T0 + N) is cut into N unit pieces; on piece k,
   log2 F(t) = E_k + p_k(u),  u = t - (T0 + k) in [0, 1),
 with E_k an integer (so 2^E_k is exact in float32) and p_k a degree-DEG polynomial fitted
-by least squares on Chebyshev points.  Outside [T0, T0 + N) the edge pieces extrapolate.
+by least squares on Chebyshev points.  Outside [T0, T0 + N) the edge values hold (u clamped).
 The slope d log2 F / d t = p_k'(u) (= R dln F / dR) serves the adjoint.  The script emulates
 the float32 evaluation (Horner, one rounding per operation) and prints the worst relative
 errors.  Run:  python gen_bulge_fit.py > bulge_fit.h
@@ -28,7 +28,7 @@ import numpy as np
 
 mpmath.mp.dps = 80
 
-T0, N, DEG = -32, 48, 7
+T0, N, DEG = -48, 80, 7
 NODES = 28
 
 

@@ -83,3 +83,15 @@ def test_closed_form_equals_dehnen_at_fixed_gamma_and_refuses_table(lib):
     assert (np.abs(chi2(ds, a) - chi2(ds, b)) / chi2(ds, a)).max() < CHI2_RTOL
     with pytest.raises(Exception):
         lib(ds.model_galaxy(), n_discs=1, bulge_kind=1, bulge_table=1024)
+
+
+def test_extreme_bulge_scales_stay_finite(lib):
+    """Bulge scales far outside any prior (a = 1e-6 or 1e6 kpc) put s = R/a beyond the fitted
+    range; the edge values hold, so logL and the gradient stay finite."""
+    ds, theta = make(1, 1, synth.GalaxySpec(21, 17, 3, 2.5))
+    m = lib(ds.model_galaxy(), n_discs=1, bulge_kind=1)
+    th = theta[:4].copy()
+    th[:, 5] = [-6.0, -4.0, 5.0, 6.0]
+    t = torch.from_numpy(th).cuda()
+    lg, g = m.loglike_grad(t)
+    assert torch.isfinite(lg).all() and torch.isfinite(g).all()
