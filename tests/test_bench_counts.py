@@ -1,0 +1,46 @@
+"""bench.py's algorithmic operation counts and peaks (the roofline denominators): the
+per-point SFU and FP32 counts of the forward path as documented, the row-subset counts,
+and the peak arithmetic from the measured per-SM rates."""
+import math
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+from paper_2205_06819_gb300 import synth  # noqa: E402
+
+
+def test_padded_points_and_sfu_count_of_the_batched_workload():
+    wl = synth.workload("batched")
+    assert bench.points_per_eval(wl.galaxies[0]) == 430 * 430          # 80 x 5 + 2 x 15
+    per_eval = bench.algorithmic_sfu_ops(wl) / wl.batch
+    assert per_eval == 430 * 430 * (2 * 64 + 16)
+
+
+def test_fp32_count_of_the_batched_and_largest_workloads():
+    wl = synth.workload("batched")
+    L = 5 + 2 * 15
+    psf = 4.0 * ((5 * 80 + 30) * 80 + 80 * 80) * L
+    expect = 430 * 430 * (6 * 64 + 200) + psf + 40 * 6400
+    assert bench.algorithmic_fp32_ops(wl) / wl.batch == pytest.approx(expect, rel=1e-12)
+    big = synth.workload("largest")                                   # Moffat: two-dimensional taps
+    h = int(math.floor(3.0 * 2.5 / 2.35482 / (1.0 / 7)))
+    L = 7 + 2 * h
+    expect = (7 * 128 + 2 * h) ** 2 * (6 * 128 + 200) + 4.0 * 128 * 128 * L * L + 40 * 128 * 128
+    assert bench.algorithmic_fp32_ops(big) / big.batch == pytest.approx(expect, rel=1e-12)
+
+
+def test_row_subsets_of_an_uneven_batch():
+    wl = synth.workload("uneven")
+    gi = [0] * 3 + [5] * 2
+    per = [bench.points_per_eval(g) for g in wl.galaxies]
+    assert bench.algorithmic_sfu_ops(wl, gi, 5) == (3 * per[0] + 2 * per[5]) * (2 * 64 + 16)
+
+
+def test_sfu_peak_from_the_per_sm_rates():
+    # one lg2 (16/clk) and one ex2 (32/clk) per node: 2 ops per 3/32 SM-cycles
+    peak = bench.sfu_peak_ops_per_s(64, 2070.0, 152)
+    assert peak == pytest.approx(152 * 2070e6 * 2 / (1 / 16 + 1 / 32), rel=1e-12)
