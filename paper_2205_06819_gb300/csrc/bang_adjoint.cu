@@ -83,12 +83,15 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
   constexpr int base = NodeBase<NQ>::value;
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
-  const float w = x / xp1;
+  const float ix1 = rcp_approx(xp1);
+  const float w = x * ix1;
   const float lw = lg2_approx(w);
-  const float i2 = rcp_approx(xp1 * xp1);
+  const float i2 = ix1 * ix1;
   const float ip4 = i2 * i2;
   const float pS = ex2_approx(m.ngam * lw) * ip4;
   const float pQ = ex2_approx(m.g3 * lw) * ip4;
+  // u_k = r_k / (r_k + a) = w 2^(lc_k - d_k): the per-point factors w and log2 w are taken
+  // out of the sums, which carry t u / w and t (log2 u - log2 w)
   float S = 0.f, Su = 0.f, Sl = 0.f, Q = 0.f, Qu = 0.f, Ql = 0.f;
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
@@ -110,15 +113,19 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
       t1 = kNodeWs[base + k] * E;
       t2 = (kNodeWq[base + k] * E) * (E * (c * c) * (c * q));
     }
-    const float lu = (lw + lc) - d;                  // log2 u_k, u_k = r_k / (r_k + a)
-    const float u = ex2_approx(lu);
+    const float mk = lc - d;                         // log2(u_k / w)
+    const float uw = ex2_approx(mk);                 // u_k / w
     S += t1;
-    Su = fmaf(t1, u, Su);
-    Sl = fmaf(t1, lu, Sl);
+    Su = fmaf(t1, uw, Su);
+    Sl = fmaf(t1, mk, Sl);
     Q += t2;
-    Qu = fmaf(t2, u, Qu);
-    Ql = fmaf(t2, lu, Ql);
+    Qu = fmaf(t2, uw, Qu);
+    Ql = fmaf(t2, mk, Ql);
   }
+  Su *= w;
+  Qu *= w;
+  Sl = fmaf(lw, S, Sl);
+  Ql = fmaf(lw, Q, Ql);
   const float fS = m.cS * x * pS, fQ = m.cQ * pQ;
   const float g = -m.ngam;
   const float inv3g = rcp_approx(m.three_mg);
