@@ -154,7 +154,7 @@ __device__ __forceinline__ BulgeDer bulge_table_vjp(const ModelConst& m, const f
   o.Qb = table_value(tab, T, TAB_VQ, p);
   const float sS = table_plain(tab, T, TAB_SS, p), sQ = table_plain(tab, T, TAB_SQ, p);
   const float gS = table_plain(tab, T, TAB_GS, p), gQ = table_plain(tab, T, TAB_GQ, p);
-  const float iR = __frcp_rn(R);
+  const float iR = rcp_approx(R);
   o.dSb_dR = o.Sb * sS * iR;
   o.dQb_dR = o.Qb * sQ * iR;
   o.dSb_da = -o.Sb * (2.0f + sS) * m.inv_a;
