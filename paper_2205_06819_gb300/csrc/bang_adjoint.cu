@@ -364,7 +364,7 @@ __device__ void constants_to_theta(const float* __restrict__ th, const double* T
 }
 
 template <int NQ, int ND, int PSF>
-__global__ void __launch_bounds__(kAdjThreads, 2) adjoint_kernel(AdjArgs a) {
+__global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
   constexpr int NACC = A_D0 + kPerDisc * ND;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ModelConst mc;
