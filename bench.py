@@ -229,8 +229,10 @@ def make_model(wl: synth.Workload, rank: int, torch, bulge_table: int = 0, bulge
     return model, gals, theta, gal_idx
 
 
-def cpu_oracle_sample(wl, gal, theta, seconds: float):
-    """The FP64 oracle, as it stands, on consecutive rows until the time budget is spent."""
+def cpu_oracle_sample(wl, gal, theta, seconds: float, gpu_logL=None):
+    """The FP64 oracle, as it stands, on consecutive rows until the time budget is spent.
+    With ``gpu_logL`` (the timed batch's logL from the CUDA path) the oracle's chi^2 of the
+    rows it evaluated is also compared with the GPU's, as a parity sample of the bench run."""
     import oracle
     oracle.build()
     og = oracle.Galaxy(gal.nx, gal.ny, gal.oversample, gal.psf_fwhm_arcsec, gal.kpc_per_arcsec,
@@ -240,8 +242,11 @@ def cpu_oracle_sample(wl, gal, theta, seconds: float):
     t0 = time.perf_counter()
     n = 0
     B = theta.shape[0]
+    ref_chi2 = []
     while n < max(B, 1 << 30):
-        oracle.loglike(og, theta[n % B:n % B + 1].astype(np.float64), n_discs=wl.n_discs, n_quad=wl.n_quad)
+        _, c2 = oracle.loglike(og, theta[n % B:n % B + 1].astype(np.float64), n_discs=wl.n_discs, n_quad=wl.n_quad)
+        if n < B:
+            ref_chi2.append(float(c2[0]))
         n += 1
         if time.perf_counter() - t0 > seconds:
             break
@@ -258,10 +263,18 @@ def cpu_oracle_sample(wl, gal, theta, seconds: float):
     dt1 = time.perf_counter() - t1
     oracle.loglike(og, theta[:1].astype(np.float64), n_discs=wl.n_discs, n_quad=wl.n_quad,
                    nthreads=cores)   # restore the thread count
-    return {"value": n / dt, "unit": "logL evals/s", "cores": cores, "kind": "oracle",
-            "single_thread_value": n1 / dt1, "single_thread_sample": f"{n1} rows, {dt1:.1f} s",
-            "sample": f"{n} oracle calls on consecutive rows of the {B}-row batch (OpenMP over fine-grid rows), "
-                      f"{dt:.1f} s"}
+    out = {"value": n / dt, "unit": "logL evals/s", "cores": cores, "kind": "oracle",
+           "single_thread_value": n1 / dt1, "single_thread_sample": f"{n1} rows, {dt1:.1f} s",
+           "sample": f"{n} oracle calls on consecutive rows of the {B}-row batch (OpenMP over fine-grid rows), "
+                     f"{dt:.1f} s"}
+    if gpu_logL is not None and ref_chi2:
+        k = len(ref_chi2)
+        ref = np.asarray(ref_chi2)
+        gpu_chi2 = -2.0 * (np.asarray(gpu_logL[:k], np.float64) + oracle.norm_const(og))
+        rel = np.abs(gpu_chi2 - ref) / ref
+        out["parity"] = {"rows": k, "max_rel_chi2_err": float(rel.max()), "median_rel_chi2_err": float(np.median(rel)),
+                         "tolerance": 1e-5, "pass": bool(rel.max() < 1e-5)}
+    return out
 
 
 def time_plain(model, theta, logL, B):
@@ -486,7 +499,8 @@ def run_ours(args):
         return 0
 
     peaks = measured_peaks()
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
     mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL))
     step_s = dev_s / args.steps
     ops = algorithmic_sfu_ops(wl, gal_idx, B)
@@ -527,6 +541,8 @@ def run_ours(args):
                                    "radial-rule mix (1 lg2 : 1 ex2)"},
         "clocks": clk,
         "wall_s_timed": wall,
+        "device": {"name": props.name, "sms": sms, "host_cores": os.cpu_count(), "torch": torch.__version__,
+                   "cuda": torch.version.cuda},
     }
     if not headline:
         line["note"] = ("profiling or variant case (--rows / --grad / --bulge-table / --bulge-kind / --psf-mode), "
@@ -537,7 +553,7 @@ def run_ours(args):
         line["plain_gpu"] = time_plain(model, theta, logL, B)
         line["fwd_adjoint"] = time_adjoint(torch)
         line["radial_table"] = time_table(wl, torch)
-        line["cpu_baseline"] = cpu_oracle_sample(wl, gal, theta_np, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_oracle_sample(wl, gal, theta_np, args.cpu_seconds, logL.cpu().numpy())
     elif ws == 1:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)

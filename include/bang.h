@@ -57,7 +57,10 @@ typedef enum {
   BANG_E_CUDA = 2,        /* a CUDA runtime call failed; see bang_last_error() */
   BANG_E_OOM = 3,         /* device or host allocation failed */
   BANG_E_UNSUPPORTED = 4, /* option not implemented (e.g. Hernquist halo kind) */
-  BANG_E_TIMEOUT = 5      /* a bounded device-side wait gave up */
+  BANG_E_TIMEOUT = 5,     /* a bounded device-side wait gave up (reserved: no kernel of this
+                             library waits on another block, so none is returned) */
+  BANG_E_BOUNDS = 6       /* checked build only: a kernel's index check failed (see
+                             bang_checked_build); bang_last_error() names the check site */
 } bang_status;
 
 /* One observed galaxy (Sec. 3.1).  The arrays are read during bang_model_create only and
@@ -216,6 +219,23 @@ bang_status bang_model_tune(bang_model *m, const int32_t *gal_idx, int B);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *bang_last_error(void);
+
+/* 1 when this library is the checked build, else 0.  In the checked build every kernel
+ * checks the indexes it computes (work items, rows, galaxies, shared-memory layout, stencil
+ * and tap indexes, spaxels, output blocks, radial tables) against the sizes of their
+ * buffers; an index out of range is not used, and the first such index of a call is
+ * recorded on the device (site, index, bound) instead of trapping.  Each compute entry
+ * point then synchronises its stream after its launches, reads and clears the records, and
+ * returns BANG_E_BOUNDS with the site in bang_last_error().  The records are per library,
+ * not per model: run checked calls one at a time.  The normal build compiles the checks
+ * out and never returns BANG_E_BOUNDS. */
+int bang_checked_build(void);
+
+/* Checked build: one device-side index check of `index` against [0, bound) on `device`,
+ * reported like a kernel's (BANG_E_BOUNDS when out of range; nothing is read or written at
+ * the index), so that the recording and reporting path can be tested without an
+ * out-of-range access.  Synchronous.  The normal build returns BANG_E_UNSUPPORTED. */
+bang_status bang_check_selftest(int device, long long index, long long bound);
 
 #ifdef __cplusplus
 }

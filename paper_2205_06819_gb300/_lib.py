@@ -1,7 +1,9 @@
 """ctypes binding of libbang.so (include/bang.h).  Argument marshalling only.
 
 Importing this module does not load the library; ``lib()`` does, and raises if the CUDA
-extension is missing or does not export the full ABI.  There is no fallback path.
+extension is missing or does not export the full ABI.  There is no fallback path.  With
+BANG_CHECKED=1 in the environment it loads the checked build (libbang_checked.so, see
+build.py) instead.
 """
 from __future__ import annotations
 
@@ -12,11 +14,12 @@ import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbang.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "libbang_checked.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "bang.h")
 
 BANG_OK = 0
 STATUS_NAMES = {0: "BANG_OK", 1: "BANG_E_INVALID_ARG", 2: "BANG_E_CUDA", 3: "BANG_E_OOM",
-                4: "BANG_E_UNSUPPORTED", 5: "BANG_E_TIMEOUT"}
+                4: "BANG_E_UNSUPPORTED", 5: "BANG_E_TIMEOUT", 6: "BANG_E_BOUNDS"}
 
 
 class BangError(RuntimeError):
@@ -58,6 +61,8 @@ _SIGNATURES = {
     "bang_loglike_batch_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "bang_model_tune": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "bang_last_error": (ctypes.c_char_p, []),
+    "bang_checked_build": (ctypes.c_int, []),
+    "bang_check_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong]),
 }
 
 _lock = threading.Lock()
@@ -71,14 +76,20 @@ def header_functions() -> list[str]:
     return sorted(set(re.findall(r"\b(bang_[a-z0-9_]+)\s*\(", text)))
 
 
+def library_path() -> str:
+    """The library lib() loads: the checked build when BANG_CHECKED=1, else libbang.so."""
+    return LIB_CHECKED_PATH if os.environ.get("BANG_CHECKED", "0") == "1" else LIB_PATH
+
+
 def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2205_06819_gb300.build.build() "
-                                   "(there is no CPU fallback)")
-            L = ctypes.CDLL(LIB_PATH)
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with paper_2205_06819_gb300.build.build("
+                                   f"checked={path == LIB_CHECKED_PATH}) (there is no CPU fallback)")
+            L = ctypes.CDLL(path)
             for name, (res, args) in _SIGNATURES.items():
                 fn = getattr(L, name)
                 fn.restype = res

@@ -3,6 +3,12 @@
 Each .cu translation unit is compiled by nvcc in parallel, then linked into
 ``paper_2205_06819_gb300/libbang.so`` against the shared CUDA runtime.  A stamp of the
 sources and flags skips the build when nothing changed.
+
+``build(checked=True)`` (or ``python -m paper_2205_06819_gb300.build --checked``) builds
+the checked library ``libbang_checked.so`` with -DBANG_CHECKED: every kernel checks the
+indexes it computes and the entry points return BANG_E_BOUNDS instead of touching memory
+out of range.  The binding loads it instead of libbang.so when BANG_CHECKED=1 is set in
+the environment.
 """
 from __future__ import annotations
 
@@ -17,7 +23,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbang.so")
+LIB_CHECKED = os.path.join(HERE, "libbang_checked.so")
 BUILD_DIR = os.path.join(HERE, "_build")
+BUILD_DIR_CHECKED = os.path.join(HERE, "_build_checked")
+CHECKED_FLAGS = ["-DBANG_CHECKED"]
 
 SOURCES = ["bang_api.cu", "bang_forward.cu", "bang_adjoint.cu", "bang_plain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,7 +44,7 @@ def _present_sources():
     return [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
 
 
-def _stamp() -> str:
+def _stamp(flags) -> str:
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
         if name.endswith((".cu", ".cuh", ".h")):
@@ -43,24 +52,27 @@ def _stamp() -> str:
                 h.update(name.encode() + f.read())
     with open(os.path.join(ROOT, "include", "bang.h"), "rb") as f:
         h.update(f.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + flags).encode())
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    stamp_path = LIB + ".stamp"
-    stamp = _stamp()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_path):
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib_path = LIB_CHECKED if checked else LIB
+    build_dir = BUILD_DIR_CHECKED if checked else BUILD_DIR
+    flags = FLAGS + (CHECKED_FLAGS if checked else [])
+    stamp_path = lib_path + ".stamp"
+    stamp = _stamp(flags)
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp_path):
         with open(stamp_path) as f:
             if f.read() == stamp:
-                return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+                return lib_path
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [cc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
+        cmd = [cc] + ARCH + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -71,16 +83,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     srcs = _present_sources()
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp_path, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

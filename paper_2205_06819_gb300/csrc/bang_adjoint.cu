@@ -21,8 +21,9 @@
 // with Su, Qu the u-weighted and Sl, Ql the (ln u)-weighted sums.  Nothing is stored
 // between the forward and the backward evaluation: the quadrature is recomputed.
 // Work items are bands of fine rows (no halo is needed: the seeds live in global memory).
-// Per-thread float32 partials are reduced per block in float64 and added atomically to
-// float64 accumulators; the per-model constants are mapped to theta in float64.
+// Per-thread float32 partials are reduced per block in float64 into the work item's own
+// slots; grad_out_kernel sums a row's items in item order (no atomics) and maps the
+// per-model constants to theta in float64.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -378,7 +379,15 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
   // scheduling, longest items first) or a fixed stride
   for (int it = blockIdx.x; it < a.n_items;) {
     const int item_id = a.order ? a.order[it] : it;
+    if (!BANG_IN(item_id, a.n_items, kSiteAdjItem)) {
+      BANG_NEXT_ITEM(it);
+      continue;
+    }
     const WorkItem w = a.items[item_id];
+    if (!BANG_IN(w.b, a.B, kSiteAdjRow) || !BANG_IN(w.g, a.n_gal, kSiteAdjGal)) {
+      BANG_NEXT_ITEM(it);
+      continue;
+    }
     if (tid == 0) {
       gs = a.gals[w.g];
       mc = a.consts[w.b];
@@ -396,6 +405,18 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
     const int nj_max = (a.G + L - 1) / os + 2;
     float4* V = lam + (size_t)nj_max * nx;
     float* tab = a.tables ? reinterpret_cast<float*>(V + (PSF == 0 ? (size_t)a.G * nx : 0)) : nullptr;
+    // checked build: the layout fits the launch's shared memory; the item's fine rows, the
+    // row's seed block and radial table are in range
+    if (!BANG_IN((tab ? reinterpret_cast<const unsigned char*>(tab + kTabHdr + 8 * a.table_T)
+                      : reinterpret_cast<const unsigned char*>(V + (PSF == 0 ? (size_t)a.G * nx : 0))) - smem_raw - 1,
+                 dynamic_smem_bytes(), kSiteAdjSmem) ||
+        !BANG_IN(w.j0, w.j1, kSiteAdjItem) || !BANG_IN(w.j1 - 1, gs.H, kSiteAdjItem) ||
+        !BANG_IN(a.out_off[w.b] + 4ll * n - 1, a.seed_total, kSiteAdjSeed) ||
+        (tab && !BANG_IN((long long)w.b * a.table_stride + kTabHdr + 8 * a.table_T - 1,
+                         (long long)a.B * a.table_stride, kSiteAdjTable))) {
+      BANG_NEXT_ITEM(it);
+      continue;
+    }
     for (int t = tid; t < ntaps; t += kAdjThreads) taps[t] = __ldg(gs.taps + t);
     if (tab) {
       const float* src = a.tables + (size_t)w.b * a.table_stride;
@@ -415,6 +436,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
       const int jhi = min(ny - 1, (y0 + G - 1) / os);
       const int nj = jhi - jlo + 1;
       __syncthreads();   // taps loaded / previous chunk's lam and V no longer read
+      if (!BANG_IN(nj, nj_max + 1, kSiteAdjLam)) break;   // uniform: every thread leaves the item's loop
       for (int t = tid; t < nj * nx; t += kAdjThreads) {
         const int s = (jlo + t / nx) * nx + (t % nx);
         lam[t] = make_float4(__ldg(seed + s), __ldg(seed + n + s), __ldg(seed + 2 * n + s), __ldg(seed + 3 * n + s));
@@ -429,6 +451,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
           const int j1 = min(ny - 1, y / os);
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
           for (int j = j0; j <= j1; ++j) {
+            if (!BANG_IN(y - j * os, L, kSiteAdjTap) || !BANG_IN(j - jlo, nj, kSiteAdjLam)) continue;
             const float tv = taps[y - j * os];
             const float4 l = lam[(j - jlo) * nx + i];
             v.x = fmaf(tv, l.x, v.x); v.y = fmaf(tv, l.y, v.y);
@@ -454,6 +477,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
         float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (PSF == 0) {
           for (int i = i0; i <= i1; ++i) {
+            if (!BANG_IN(qx - i * os, L, kSiteAdjTap) || !BANG_IN(gr * nx + i, G * nx, kSiteAdjV)) continue;
             const float th_ = taps[qx - i * os];
             const float4 v = V[gr * nx + i];
             s4.x = fmaf(th_, v.x, s4.x); s4.y = fmaf(th_, v.y, s4.y);
@@ -463,8 +487,10 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
           int j0 = y - L + 1 <= 0 ? 0 : (y - L + os) / os;
           const int j1 = min(ny - 1, y / os);
           for (int j = j0; j <= j1; ++j) {
+            if (!BANG_IN(y - j * os, L, kSiteAdjTap) || !BANG_IN(j - jlo, nj, kSiteAdjLam)) continue;
             const float* wrow = taps + (y - j * os) * L;
             for (int i = i0; i <= i1; ++i) {
+              if (!BANG_IN(qx - i * os, L, kSiteAdjTap)) continue;
               const float tw = wrow[qx - i * os];
               const float4 l = lam[(j - jlo) * nx + i];
               s4.x = fmaf(tw, l.x, s4.x); s4.y = fmaf(tw, l.y, s4.y);
@@ -501,7 +527,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
 __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind, int bulge_kind,
                                 const double* __restrict__ acc_partial, const int* __restrict__ adj_row_first,
                                 const double* __restrict__ vsys_partial, const int* __restrict__ row_first, int B,
-                                double l10k, float* __restrict__ grad) {
+                                int n_items, int adj_items, double l10k, float* __restrict__ grad) {
   const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (b >= B) return;   // whole warps
@@ -513,9 +539,11 @@ __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, 
   for (int i = 0; i < kDecodeTerms; ++i) T[i] = __shfl_sync(0xffffffffu, v, i);
   double sum = 0.0;
   if (ok && lane < kAdjSlots) {
-    for (int i = adj_row_first[b]; i < adj_row_first[b + 1]; ++i) sum += acc_partial[(size_t)i * kAdjSlots + lane];
+    for (int i = adj_row_first[b]; i < adj_row_first[b + 1]; ++i)
+      if (BANG_IN(i, adj_items, kSiteFinalizeItem)) sum += acc_partial[(size_t)i * kAdjSlots + lane];
   } else if (ok && lane == kVsysSlot) {
-    for (int i = row_first[b]; i < row_first[b + 1]; ++i) sum += vsys_partial[i];
+    for (int i = row_first[b]; i < row_first[b + 1]; ++i)
+      if (BANG_IN(i, n_items, kSiteFinalizeItem)) sum += vsys_partial[i];
   }
   double s[kVsysSlot + 1];
 #pragma unroll
@@ -537,14 +565,16 @@ __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, 
 // lookup's t0 + k h holds to float32 rounding.
 template <int NQ>
 __global__ void table_kernel(const ModelConst* __restrict__ consts, const GalDev* __restrict__ gals,
-                             const int* __restrict__ row_g, int T, int derivs, float* __restrict__ tables,
+                             const int* __restrict__ row_g, int n_gal, int T, int derivs, float* __restrict__ tables,
                              int64_t stride) {
   const int b = blockIdx.x;
   __shared__ ModelConst m;
   __shared__ double t0h[2];
   if (threadIdx.x == 0) {
     m = consts[b];
-    const GalDev g = gals[row_g[b]];
+    if (!BANG_IN(row_g[b], n_gal, kSiteDecodeGal) || !BANG_IN(kTabHdr + (derivs ? 8 : 4) * T - 1, stride, kSiteTable))
+      m.valid = 0;
+    const GalDev g = gals[BANG_IN(row_g[b], n_gal, kSiteDecodeGal) ? row_g[b] : 0];
     const double xa = m.X0, xb = m.X0 + (double)(g.W - 1) * g.pitch_kpa;
     const double ya = m.Y0, yb = m.Y0 + (double)(g.H - 1) * g.pitch_kpa;
     const double rmax = sqrt(fmax(xa * xa, xb * xb) + fmax(ya * ya, yb * yb));
@@ -631,20 +661,23 @@ cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d,
   return n_discs == 2 ? launch_nd<128, 2>(a, psf2d, grid, smem, st) : launch_nd<128, 1>(a, psf2d, grid, smem, st);
 }
 
-cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int B, int n_quad, int T,
-                          int derivs, float* tables, int64_t stride, cudaStream_t st) {
-  if (n_quad == 64) table_kernel<64><<<B, 256, 0, st>>>(consts, gals, row_g, T, derivs, tables, stride);
-  else table_kernel<128><<<B, 256, 0, st>>>(consts, gals, row_g, T, derivs, tables, stride);
+cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int n_gal, int B, int n_quad,
+                          int T, int derivs, float* tables, int64_t stride, cudaStream_t st) {
+  if (n_quad == 64) table_kernel<64><<<B, 256, 0, st>>>(consts, gals, row_g, n_gal, T, derivs, tables, stride);
+  else table_kernel<128><<<B, 256, 0, st>>>(consts, gals, row_g, n_gal, T, derivs, tables, stride);
   return cudaGetLastError();
 }
 
+BANG_DEFINE_FAULT_TAKER(take_fault_adjoint)
+
 cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind,
                             const double* acc_partial, const int* adj_row_first, const double* vsys_partial,
-                            const int* row_first, int B, float* grad, cudaStream_t st) {
+                            const int* row_first, int B, int n_items, int adj_items, float* grad, cudaStream_t st) {
   constexpr int kRowsPerBlock = 4;   // 4 warps, one row each
   const double l10k = std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit));
   grad_out_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(
-      theta, P, n_discs, halo_kind, bulge_kind, acc_partial, adj_row_first, vsys_partial, row_first, B, l10k, grad);
+      theta, P, n_discs, halo_kind, bulge_kind, acc_partial, adj_row_first, vsys_partial, row_first, B, n_items,
+      adj_items, l10k, grad);
   return cudaGetLastError();
 }
 

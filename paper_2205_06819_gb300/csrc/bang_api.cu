@@ -555,15 +555,17 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.queue = p->d_queue.as<int>();
   a.consts = p->d_consts.as<bang::ModelConst>();
   a.halo_kind = m->opts.halo_kind;
+  a.B = p->B;
+  a.n_gal = (int)m->gals.size();
+  a.out_total = p->out_total;
   cudaError_t e = bang::launch_decode(theta, m->P, m->opts.n_discs, m->opts.halo_kind, a.gals, p->d_row_g.as<int>(),
-                                      p->B,
-                                      p->d_consts.as<bang::ModelConst>(), st);
+                                      a.n_gal, p->B, p->d_consts.as<bang::ModelConst>(), st);
   if (e != cudaSuccess) return e;
   if (m->opts.bulge_table > 0) {
     a.tables = p->d_tables.as<float>();
     a.table_T = m->opts.bulge_table;
     a.table_stride = p->table_stride;
-    e = bang::launch_tables(a.consts, a.gals, p->d_row_g.as<int>(), p->B, m->opts.n_quad, a.table_T,
+    e = bang::launch_tables(a.consts, a.gals, p->d_row_g.as<int>(), a.n_gal, p->B, m->opts.n_quad, a.table_T,
                             mode == bang::kModeSeed, p->d_tables.as<float>(), p->table_stride, st);
     if (e != cudaSuccess) return e;
   }
@@ -571,7 +573,8 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   if (e != cudaSuccess) return e;
   e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
   if (e != cudaSuccess || !logL) return e;
-  return bang::launch_finalize(a.partial, p->d_row_first.as<int>(), p->d_row_g.as<int>(), a.gals, p->B, logL, st);
+  return bang::launch_finalize(a.partial, p->d_row_first.as<int>(), p->d_row_g.as<int>(), a.gals, p->B, p->n_items,
+                               a.n_gal, logL, st);
 }
 
 // Scratch of a gradient call: the forward items' d logL / d v_sys, then the adjoint items'
@@ -598,6 +601,9 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   a.seed = seed;
   a.out_off = p->d_out_off.as<int64_t>();
   a.acc_partial = acc_partial;
+  a.B = p->B;
+  a.n_gal = (int)m->gals.size();
+  a.seed_total = p->out_total;
   if (m->opts.bulge_table > 0) {
     a.tables = p->d_tables.as<float>();
     a.table_T = m->opts.bulge_table;
@@ -609,7 +615,8 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
   if (e != cudaSuccess) return e;
   return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, m->opts.bulge_kind, acc_partial,
-                               p->d_adj_row_first.as<int>(), vsys_partial, p->d_row_first.as<int>(), p->B, grad, st);
+                               p->d_adj_row_first.as<int>(), vsys_partial, p->d_row_first.as<int>(), p->B,
+                               p->n_items, p->adj_items, grad, st);
 }
 
 }  // namespace
@@ -642,14 +649,42 @@ bang_status set_error(bang_status s, const char* fmt, ...) {
   return s;
 }
 
+bang_status check_faults(cudaStream_t st) {
+  if (!kChecked) return BANG_OK;
+  BANG_CUDA(cudaStreamSynchronize(st));
+  struct {
+    const char* unit;
+    cudaError_t (*take)(Fault*);
+  } units[] = {{"forward", take_fault_forward}, {"adjoint", take_fault_adjoint}, {"plain", take_fault_plain}};
+  for (const auto& u : units) {
+    Fault f;
+    BANG_CUDA(u.take(&f));
+    if (f.site)
+      return fail(BANG_E_BOUNDS, "index check failed in the %s kernels: %s, index %lld outside [0, %lld)", u.unit,
+                  check_site_name((int)f.site - 1), f.index, f.bound);
+  }
+  return BANG_OK;
+}
+
 }  // namespace bang
 
 extern "C" {
 
 const char* bang_last_error(void) { return g_last_error.c_str(); }
 
+int bang_checked_build(void) { return bang::kChecked ? 1 : 0; }
+
+bang_status bang_check_selftest(int device, long long index, long long bound) {
+  g_last_error.clear();
+  if (!bang::kChecked) return fail(BANG_E_UNSUPPORTED, "bang_check_selftest: not the checked build");
+  BANG_CUDA(cudaSetDevice(device));
+  BANG_CUDA(bang::launch_check_selftest(index, bound, nullptr));
+  return bang::check_faults(nullptr);
+}
+
 bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang_model_opts* opts, int device,
                               bang_model** out) {
+  bang::NvtxRange nvtx("bang_model_create");
   g_last_error.clear();
   if (!gal || !opts || !out || n_gal < 1) return fail(BANG_E_INVALID_ARG, "bang_model_create: null argument or n_gal < 1");
   *out = nullptr;
@@ -858,7 +893,7 @@ bang_status run_forward(bang_model* m, const float* theta, const int32_t* gal_id
   } else if (!th_dev) {
     BANG_CUDA(cudaStreamSynchronize(st));   // the staged theta buffer is reused by the next call
   }
-  return BANG_OK;
+  return bang::check_faults(st);
 }
 
 }  // namespace
@@ -867,16 +902,19 @@ extern "C" {
 
 bang_status bang_loglike_batch(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,
                                void* stream) {
+  bang::NvtxRange nvtx("bang_loglike_batch");
   return run_forward(m, theta, gal_idx, B, logL, nullptr, bang::kModeLogL, stream);
 }
 
 bang_status bang_model_maps(bang_model* m, const float* theta, const int32_t* gal_idx, int B, float* maps,
                             void* stream) {
+  bang::NvtxRange nvtx("bang_model_maps");
   return run_forward(m, theta, gal_idx, B, nullptr, maps, bang::kModeMaps, stream);
 }
 
 bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,
                                     float* grad, void* stream) {
+  bang::NvtxRange nvtx("bang_loglike_grad_batch");
   g_last_error.clear();
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
   if (!theta || !logL || !grad || B < 1) return fail(BANG_E_INVALID_ARG, "theta, logL or grad is null, or B < 1");
@@ -909,11 +947,12 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   if (!g_dev) BANG_CUDA(cudaMemcpyAsync(grad, d_grad, th_bytes, cudaMemcpyDeviceToHost, st));
   if (!th_dev || !l_dev || !g_dev) BANG_CUDA(cudaStreamSynchronize(st));
-  return BANG_OK;
+  return bang::check_faults(st);
 }
 
 bang_status bang_loglike_grids(bang_model* m, const float* theta, int B, const int32_t* grids, int n_grids,
                                double* logL, float* grad, void* stream) {
+  bang::NvtxRange nvtx("bang_loglike_grids");
   g_last_error.clear();
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
   if (!theta || !logL || !grids || B < 1 || n_grids < 1)
@@ -954,11 +993,12 @@ bang_status bang_loglike_grids(bang_model* m, const float* theta, int B, const i
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sl, cudaMemcpyDeviceToHost, st));
   if (!g_dev) BANG_CUDA(cudaMemcpyAsync(grad, d_grad, sg, cudaMemcpyDeviceToHost, st));
   BANG_CUDA(cudaStreamSynchronize(st));   // the staged and expanded buffers are reused by the next call
-  return BANG_OK;
+  return bang::check_faults(st);
 }
 
 bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t* gal_idx, int B, double* logL,
                                void* stream) {
+  bang::NvtxRange nvtx("bang_loglike_plain");
   g_last_error.clear();
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
   if (!theta || !logL || B < 1) return fail(BANG_E_INVALID_ARG, "theta or logL is null, or B < 1");
@@ -996,12 +1036,13 @@ bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t*
   }
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   if (!th_dev || !l_dev) BANG_CUDA(cudaStreamSynchronize(st));
-  return BANG_OK;
+  return bang::check_faults(st);
 }
 
 // Autotuner: times the forward launch for every (fine rows per block step G, spaxel-row
 // bands per row) candidate on this batch shape and keeps the fastest for later calls.
 bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
+  bang::NvtxRange nvtx("bang_model_tune");
   g_last_error.clear();
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
   if (B < 1) return fail(BANG_E_INVALID_ARG, "B < 1");
@@ -1070,7 +1111,7 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
     return fail(BANG_E_UNSUPPORTED, "no launch configuration fits this batch");
   }
   m->tuned[skey] = best_t;
-  return BANG_OK;
+  return bang::check_faults(st);
 }
 
 }  // extern "C"

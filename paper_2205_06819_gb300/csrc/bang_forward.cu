@@ -58,6 +58,10 @@ __device__ __forceinline__ float finish_spaxel(const GalDev& g, const ModelConst
                                                float* __restrict__ out, float& lam_v) {
   const int n = g.nx * g.ny;
   const int s = j * g.nx + i;
+  if (!BANG_IN(s, n, kSiteFwdSpaxel)) {
+    lam_v = 0.f;
+    return 0.f;
+  }
   float model[4];
   float v = 0.f, sig = 0.f, iC0 = 0.f;
   if (g.flux) {   // flux-weighted moments: v = C1/C0, sigma^2 = C2/C0 - v^2, M/L = C3/C0
@@ -118,7 +122,15 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
   // scheduling, longest items first) or a fixed stride
   for (int it = blockIdx.x; it < a.n_items;) {
     const int item_id = a.order ? a.order[it] : it;
+    if (!BANG_IN(item_id, a.n_items, kSiteFwdItem)) {
+      BANG_NEXT_ITEM(it);
+      continue;
+    }
     const WorkItem w = a.items[item_id];
+    if (!BANG_IN(w.b, a.B, kSiteFwdRow) || !BANG_IN(w.g, a.n_gal, kSiteFwdGal)) {
+      BANG_NEXT_ITEM(it);
+      continue;
+    }
     if (tid == 0) {
       gs = a.gals[w.g];
       if (a.consts) mc = a.consts[w.b];
@@ -135,6 +147,19 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     float* out = nullptr;
     if (MODE == kModeMaps) out = a.maps + a.out_off[w.b];
     if (MODE == kModeSeed) out = a.seed + a.out_off[w.b];
+    // checked build: the layout fits the launch's shared memory, a fine row holds every
+    // stencil read, the item's spaxel rows, output block and radial table are in range
+    if (!BANG_IN((tab ? reinterpret_cast<const unsigned char*>(tab + kTabHdr + 4 * a.table_T)
+                      : reinterpret_cast<const unsigned char*>(stage + 2 * (size_t)a.G * W)) - smem_raw - 1,
+                 dynamic_smem_bytes(), kSiteFwdSmem) ||
+        !BANG_IN((nx - 1) * os + L - 1, W, kSiteFwdStencil) || !BANG_IN(w.j0, w.j1, kSiteFwdSpaxel) ||
+        !BANG_IN(w.j1 - 1, gs.ny, kSiteFwdSpaxel) ||
+        (MODE != kModeLogL && !BANG_IN(a.out_off[w.b] + 4ll * nx * gs.ny - 1, a.out_total, kSiteFwdOut)) ||
+        (tab && !BANG_IN((long long)w.b * a.table_stride + kTabHdr + 4 * a.table_T - 1,
+                         (long long)a.B * a.table_stride, kSiteFwdTable))) {
+      BANG_NEXT_ITEM(it);
+      continue;
+    }
 
     if (!mc.valid) {
       if (MODE == kModeMaps) {
@@ -182,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       const int y0 = y_begin + c * a.G;
       const int npts = min(a.G, y_end - y0) * W;
       float4* st = stage + (size_t)(c & 1) * a.G * W;
+      if (!BANG_IN(npts, a.G * W + 1, kSiteFwdStage)) return;
       for (;;) {
         int base = 0;
         if (lane == 0) base = atomicAdd(&chunk_ctr[c & 1], 32);
@@ -223,6 +249,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
             jlo = max(jlo, w.j0);
             const int jhi = min(y / os, w.j1 - 1);
             for (int j = jlo; j <= jhi; ++j) {
+              if (!BANG_IN(y - j * os, L, kSiteFwdTap)) continue;
               const float tv = taps[y - j * os];
               float4& A = acc[(j % NA) * nx + i];
               A.x = fmaf(tv, hs.x, A.x); A.y = fmaf(tv, hs.y, A.y);
@@ -255,6 +282,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           const int ga = max(0, j * os - y0);
           const int gb = min(G - 1, j * os + L - 1 - y0);
           for (int gr = ga; gr <= gb; ++gr) {
+            if (!BANG_IN(y0 + gr - j * os, L, kSiteFwdTap)) continue;
             const float* wrow = taps + (y0 + gr - j * os) * L;
             const float4* srow = stage_c + gr * W + i * os;
             for (int k = 0; k < L; ++k) {
@@ -306,14 +334,15 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
 // transcendentals are independent), lane 0 gathers them and finishes the row, so a row
 // costs the latency of one transcendental instead of thirteen in a chain.
 __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind,
-                              const GalDev* __restrict__ gals, const int* __restrict__ row_g, int B,
+                              const GalDev* __restrict__ gals, const int* __restrict__ row_g, int n_gal, int B,
                               double l10k, ModelConst* __restrict__ out) {
   const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (b >= B) return;   // whole warps: b is uniform across the warp
   const float* th = theta + (size_t)b * P;
-  const GalDev& gal = gals[row_g[b]];
-  const bool ok = theta_in_domain(th, nd, halo_kind, gal.bulge_kind);
+  const bool gal_ok = BANG_IN(row_g[b], n_gal, kSiteDecodeGal);
+  const GalDev& gal = gals[gal_ok ? row_g[b] : 0];
+  const bool ok = gal_ok && theta_in_domain(th, nd, halo_kind, gal.bulge_kind);
   const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
   double T[kDecodeTerms];
 #pragma unroll
@@ -330,17 +359,19 @@ __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, in
 
 // logL[b] = -chi^2/2 - const from the per-item partial sums (items of row b are contiguous).
 __global__ void finalize_kernel(const double* __restrict__ partial, const int* __restrict__ row_first,
-                                const int* __restrict__ row_g, const GalDev* __restrict__ gals, int B,
-                                double* __restrict__ logL) {
+                                const int* __restrict__ row_g, const GalDev* __restrict__ gals, int B, int n_items,
+                                int n_gal, double* __restrict__ logL) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   double s = 0.0;
   bool bad = false;
   for (int k = row_first[b]; k < row_first[b + 1]; ++k) {
+    if (!BANG_IN(k, n_items, kSiteFinalizeItem)) continue;
     const double v = partial[k];
     bad |= isnan(v);
     s += v;
   }
+  if (!BANG_IN(row_g[b], n_gal, kSiteDecodeGal)) return;
   logL[b] = bad ? -INFINITY : -0.5 * s - gals[row_g[b]].norm_const;
 }
 
@@ -401,11 +432,11 @@ cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d,
 size_t model_const_bytes() { return sizeof(ModelConst); }
 
 cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
-                          int B, ModelConst* out, cudaStream_t st) {
+                          int n_gal, int B, ModelConst* out, cudaStream_t st) {
   constexpr int kRowsPerBlock = 4;   // 4 warps of 32 lanes, one row each
   const double l10k = std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit));
-  decode_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(theta, P, n_discs, halo_kind,
-                                                                                       gals, row_g, B, l10k, out);
+  decode_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(
+      theta, P, n_discs, halo_kind, gals, row_g, n_gal, B, l10k, out);
   return cudaGetLastError();
 }
 
@@ -447,8 +478,21 @@ cudaError_t launch_sum_rows(const double* logL_x, const float* grad_x, int P, in
 }
 
 cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
-                            double* logL, cudaStream_t st) {
-  finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(partial, row_first, row_g, gals, B, logL);
+                            int n_items, int n_gal, double* logL, cudaStream_t st) {
+  finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(partial, row_first, row_g, gals, B, n_items, n_gal, logL);
+  return cudaGetLastError();
+}
+
+BANG_DEFINE_FAULT_TAKER(take_fault_forward)
+
+namespace {
+__global__ void check_selftest_kernel(long long i, long long n) { (void)BANG_IN(i, n, kSiteSelftest); }
+}  // namespace
+
+// One check of i against n on the device: in the checked build an out-of-range i is
+// recorded as a fault of the selftest site; nothing is read or written at i.
+cudaError_t launch_check_selftest(long long i, long long n, cudaStream_t st) {
+  check_selftest_kernel<<<1, 1, 0, st>>>(i, n);
   return cudaGetLastError();
 }
 
@@ -509,6 +553,7 @@ __global__ void noalloc_items_kernel(const int* __restrict__ gal, const GalDev* 
 extern "C" bang_status bang_loglike_batch_noalloc(bang_model* m, const float* theta, const int32_t* gal_idx, int B,
                                                   double* logL, void* stream) {
   using namespace bang;
+  NvtxRange nvtx("bang_loglike_batch_noalloc");
   ModelView v;
   if (!model_view(m, &v)) return set_error(BANG_E_INVALID_ARG, "null model");
   if (v.bulge_table)
@@ -600,10 +645,12 @@ extern "C" bang_status bang_loglike_batch_noalloc(bang_model* m, const float* th
   a.G = rows_per_step;
   a.partial = partial;
   a.out_off = nullptr;
+  a.B = B;
+  a.n_gal = v.n_gal;
   const int grid = std::min(B, per_sm * v.num_sms);
   if ((e = launch_forward(a, v.n_quad, v.n_discs, psf2d, kModeLogL, grid, smem, st)) != cudaSuccess)
     return set_error(BANG_E_CUDA, "forward kernel: %s", cudaGetErrorString(e));
-  if ((e = launch_finalize(partial, row_first, row_g, v.d_gals, B, logL, st)) != cudaSuccess)
+  if ((e = launch_finalize(partial, row_first, row_g, v.d_gals, B, B, v.n_gal, logL, st)) != cudaSuccess)
     return set_error(BANG_E_CUDA, "finalize kernel: %s", cudaGetErrorString(e));
-  return BANG_OK;
+  return check_faults(st);
 }

@@ -6,12 +6,30 @@
 #include <cuda_runtime.h>
 
 #include "../../include/bang.h"
+#include "bang_check.cuh"
+
+#ifndef BANG_NO_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
 
 namespace bang {
 
 struct GalDev;
 struct WorkItem;
 struct ModelConst;
+
+// NVTX range over one entry point (shown by nsys and usable as an ncu --nvtx filter); a
+// push and a pop through a function pointer that does nothing when no tool is attached.
+struct NvtxRange {
+#ifndef BANG_NO_NVTX
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+#else
+  explicit NvtxRange(const char*) {}
+#endif
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Gradient accumulator row: adjoints of the per-model constants (slots 0..23, the second
 // disc's unused for one-disc models) and d logL / d v_sys (slot 24).
@@ -40,6 +58,9 @@ struct FwdArgs {
   const float* tables;      // radial tables, row b at b * table_stride (NULL: quadrature per point)
   int table_T;              // radii per table
   int64_t table_stride;     // floats per row's table
+  // sizes for the checked build's index checks
+  int B, n_gal;             // rows of the batch, galaxies of the model
+  int64_t out_total;        // floats of maps / seed
 };
 
 // Arguments of the adjoint sweep.
@@ -59,6 +80,9 @@ struct AdjArgs {
   const float* tables;      // radial tables with slopes, row b at b * table_stride (NULL: quadrature)
   int table_T;
   int64_t table_stride;
+  // sizes for the checked build's index checks
+  int B, n_gal;             // rows of the batch, galaxies of the model
+  int64_t seed_total;       // floats of seed
 };
 
 // Read-only view of a model's immutable device state (for entry points defined outside
@@ -81,7 +105,7 @@ cudaError_t launch_expand_rows(const float* theta, int P, int B, int n, float* t
 cudaError_t launch_sum_rows(const double* logL_x, const float* grad_x, int P, int B, int n, double* logL, float* grad,
                             cudaStream_t st);
 cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
-                            double* logL, cudaStream_t st);
+                            int n_items, int n_gal, double* logL, cudaStream_t st);
 cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float* ws, const float* wq);
 
 int adjoint_threads();
@@ -89,18 +113,29 @@ size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d, int table_T =
 // Radial tables of the bulge (see bang_device.cuh): floats per row, and the table kernel
 // (one block per row; slopes only when `derivs`).
 int64_t table_row_floats(int T, int derivs);
-cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int B, int n_quad, int T,
-                          int derivs, float* tables, int64_t stride, cudaStream_t st);
+cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int n_gal, int B, int n_quad,
+                          int T, int derivs, float* tables, int64_t stride, cudaStream_t st);
 const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d);
 cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
                            cudaStream_t st);
 cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind,
                             const double* acc_partial, const int* adj_row_first, const double* vsys_partial,
-                            const int* row_first, int B, float* grad, cudaStream_t st);
+                            const int* row_first, int B, int n_items, int adj_items, float* grad, cudaStream_t st);
 size_t model_const_bytes();
 cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
-                          int B, ModelConst* out, cudaStream_t st);
+                          int n_gal, int B, ModelConst* out, cudaStream_t st);
 cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq);
+
+// Checked build: each kernel translation unit's fault record, read and cleared (synchronous).
+cudaError_t take_fault_forward(Fault* f);
+cudaError_t take_fault_adjoint(Fault* f);
+cudaError_t take_fault_plain(Fault* f);
+// Checked build: synchronises st, reads and clears the fault records of every kernel
+// translation unit, and returns BANG_E_BOUNDS (with the site in the error message) if one
+// was set; BANG_OK otherwise and always in the normal build (which does not synchronise).
+bang_status check_faults(cudaStream_t st);
+// Checked build: one in-range check of i against n run on the device (the selftest site).
+cudaError_t launch_check_selftest(long long i, long long n, cudaStream_t st);
 
 size_t plain_scratch_bytes(int N, int n);
 int plain_launches_per_row();

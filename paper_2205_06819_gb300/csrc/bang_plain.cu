@@ -131,6 +131,10 @@ __global__ void plain_psf(const GalDev* __restrict__ gal, const ModelConst* __re
   if (s >= g.nx * g.ny || !mcp->valid) return;
   const int j = s / g.nx, i = s - j * g.nx;
   const int N = g.W * g.H, L = g.L;
+  // checked build: the spaxel's last window point lies on the padded fine grid
+  if (!BANG_IN((long long)(j * g.os + L - 1) * g.W + i * g.os + L - 1, N, kSitePlain) ||
+      !BANG_IN(i * g.os + L - 1, g.W, kSitePlain))
+    return;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int cy = 0; cy < L; ++cy) {
     const int qy = j * g.os + cy;
@@ -244,6 +248,8 @@ cudaError_t launch_plain_row(const float* theta, int P, int n_quad, int n_discs,
 #undef BANG_CHAIN
   return cudaErrorInvalidValue;
 }
+
+BANG_DEFINE_FAULT_TAKER(take_fault_plain)
 
 cudaError_t upload_nodes_plain(const float* cm1, const float* lc, const float* ws, const float* wq) {
   cudaError_t e = cudaMemcpyToSymbol(kNodeCm1, cm1, 192 * sizeof(float));

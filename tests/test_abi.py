@@ -41,3 +41,23 @@ def test_null_model_queries_do_not_touch_the_gpu(libpath):
     assert L.bang_model_destroy(None) == 0
     assert L.bang_loglike_batch(None, None, None, 1, None, None) == 1   # BANG_E_INVALID_ARG
     assert b"null model" in L.bang_last_error()
+
+
+def test_checked_build_exports_the_same_abi_and_says_so(libpath):
+    """The checked library (kernels check their indexes, BANG_E_BOUNDS) exports every
+    declared function; bang_checked_build tells the two builds apart (a host-only call)."""
+    checked = build_mod.build(checked=True)
+    assert checked != libpath
+    out = subprocess.run(["nm", "-D", "--defined-only", checked], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert not [n for n in _lib.header_functions() if n not in exported]
+    assert ctypes.CDLL(checked).bang_checked_build() == 1
+    assert _lib.lib().bang_checked_build() == 0
+    assert _lib.STATUS_NAMES[6] == "BANG_E_BOUNDS"
+
+
+def test_loader_picks_the_checked_build_from_the_environment(monkeypatch):
+    monkeypatch.setenv("BANG_CHECKED", "1")
+    assert _lib.library_path() == _lib.LIB_CHECKED_PATH
+    monkeypatch.setenv("BANG_CHECKED", "0")
+    assert _lib.library_path() == _lib.LIB_PATH

@@ -44,3 +44,36 @@ def test_sfu_peak_from_the_per_sm_rates():
     # one lg2 (16/clk) and one ex2 (32/clk) per node: 2 ops per 3/32 SM-cycles
     peak = bench.sfu_peak_ops_per_s(64, 2070.0, 152)
     assert peak == pytest.approx(152 * 2070e6 * 2 / (1 / 16 + 1 / 32), rel=1e-12)
+
+
+def test_cpu_baseline_parity_sample():
+    """The cpu_baseline leg compares the oracle's chi^2 of the rows it timed with the logL it
+    is given: the oracle's own logL passes, one perturbed by 1e-4 of chi^2 fails."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    spec = synth.GalaxySpec(12, 10, 2, 2.0)
+    box = synth.prior_box(1)
+    th = synth.draw_theta_true(box, 3)
+    og = oracle.Galaxy(spec.nx, spec.ny, spec.oversample, spec.psf_fwhm_arcsec, spec.kpc_per_arcsec)
+    data, err, mask = synth.noisy_data(oracle.maps(og, th), seed=4)
+    theta = synth.draw_theta_batch(box, th, 3, seed=5).astype(np.float32)
+
+    class Gal:
+        nx, ny, oversample, psf_fwhm_arcsec, kpc_per_arcsec = spec.nx, spec.ny, spec.oversample, 2.0, \
+            spec.kpc_per_arcsec
+        psf_kind, moffat_beta = 0, 3.0
+
+    Gal.data, Gal.err, Gal.mask = data, err, mask
+
+    class WL:
+        n_discs, n_quad = 1, 64
+
+    og2 = oracle.Galaxy(spec.nx, spec.ny, spec.oversample, 2.0, spec.kpc_per_arcsec, data=data.astype(np.float64),
+                        err=err.astype(np.float64), mask=mask)
+    logL, chi2 = oracle.loglike(og2, theta.astype(np.float64))
+    ok = bench.cpu_oracle_sample(WL, Gal, theta, 0.05, logL)
+    assert ok["parity"]["rows"] >= 1 and ok["parity"]["pass"]
+    assert ok["parity"]["max_rel_chi2_err"] < 1e-12
+    bad = bench.cpu_oracle_sample(WL, Gal, theta, 0.05, logL + 0.5e-4 * chi2)
+    assert not bad["parity"]["pass"]
