@@ -44,11 +44,11 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 122.0          # measured FFMA issue (128 nominal)
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "cde751242eed844b", "bytes_per_launch": 462080}
+NCU_TRAFFIC = {"stamp": "3b2a0e9d9660b132", "bytes_per_launch": 668928}
 # Pipe activity of the forward kernel from the same kind of capture (ncu --set full on 456
 # rows of the benchmark batch): SFU (xu) and FMA pipes, issue active, thread instructions
 # per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "cde751242eed844b", "pipe_xu_pct": 46.7, "pipe_fma_pct": 40.9, "issue_active_pct": 70.4,
+NCU_PIPES = {"stamp": "3b2a0e9d9660b132", "pipe_xu_pct": 46.7, "pipe_fma_pct": 40.9, "issue_active_pct": 70.4,
              "thread_instr_per_point": 944}
 
 
