@@ -80,7 +80,7 @@ struct BulgeDer {
 };
 
 template <int NQ>
-__device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, float R, const float2* nw = nullptr) {
+__device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, float R, const float4* nw = nullptr) {
   constexpr int base = NodeBase<NQ>::value;
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
@@ -94,34 +94,59 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
   // u_k = r_k / (r_k + a) = w 2^(lc_k - d_k): the per-point factors w and log2 w are taken
   // out of the sums, which carry t u / w and t (log2 u - log2 w)
   float S = 0.f, Su = 0.f, Sl = 0.f, Q = 0.f, Qu = 0.f, Ql = 0.f;
+  if (nw) {
+    // per-model node factors folded into shared-memory weights, two nodes at a time in
+    // packed two-lane FP32 instructions (see bulge_projected_w); even and odd nodes
+    // accumulate in the two lanes
+    const float2 w2 = make_float2(w, w), g2 = make_float2(m.g4, m.g4), one2 = make_float2(1.0f, 1.0f);
+    const float2 neg2 = make_float2(-1.0f, -1.0f);
+    float2 S2 = make_float2(0.f, 0.f), Su2 = S2, Sl2 = S2, Q2 = S2, Qu2 = S2, Ql2 = S2;
 #pragma unroll
-  for (int k = 0; k < NQ; ++k) {
-    const float lc = kNodeLc[base + k];
-    const float q = fmaf(w, kNodeCm1[base + k], 1.0f);
-    const float d = lg2_approx(q);
-    float t1, t2;
-    if (nw) {   // per-model node factors folded into shared-memory weights (see bulge_projected_w)
-      float2 wk;
-      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
-                   : "=f"(wk.x), "=f"(wk.y)
-                   : "r"((unsigned)__cvta_generic_to_shared(nw + k)));
-      const float e = ex2_approx(m.g4 * d);          // q^(g-4); q^(2g-7) = e^2 q
-      t1 = wk.x * e;
-      t2 = (wk.y * e) * (e * q);
-    } else {
+    for (int k = 0; k < NQ; k += 2) {
+      const float2 q = __ffma2_rn(w2, make_float2(kNodeCm1[base + k], kNodeCm1[base + k + 1]), one2);
+      const float2 d = make_float2(lg2_approx(q.x), lg2_approx(q.y));
+      float4 wk;
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                   : "=f"(wk.x), "=f"(wk.y), "=f"(wk.z), "=f"(wk.w)
+                   : "r"((unsigned)__cvta_generic_to_shared(nw + k / 2)));
+      const float2 t = __fmul2_rn(g2, d);
+      const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));   // q^(g-4); q^(2g-7) = e^2 q
+      const float2 t1 = __fmul2_rn(make_float2(wk.x, wk.y), e);
+      const float2 t2 = __fmul2_rn(__fmul2_rn(make_float2(wk.z, wk.w), e), __fmul2_rn(e, q));
+      const float2 mk = __ffma2_rn(d, neg2, make_float2(kNodeLc[base + k], kNodeLc[base + k + 1]));   // log2(u / w)
+      const float2 uw = make_float2(ex2_approx(mk.x), ex2_approx(mk.y));                             // u / w
+      S2 = __fadd2_rn(S2, t1);
+      Su2 = __ffma2_rn(t1, uw, Su2);
+      Sl2 = __ffma2_rn(t1, mk, Sl2);
+      Q2 = __fadd2_rn(Q2, t2);
+      Qu2 = __ffma2_rn(t2, uw, Qu2);
+      Ql2 = __ffma2_rn(t2, mk, Ql2);
+    }
+    S = S2.x + S2.y;
+    Su = Su2.x + Su2.y;
+    Sl = Sl2.x + Sl2.y;
+    Q = Q2.x + Q2.y;
+    Qu = Qu2.x + Qu2.y;
+    Ql = Ql2.x + Ql2.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const float lc = kNodeLc[base + k];
+      const float q = fmaf(w, kNodeCm1[base + k], 1.0f);
+      const float d = lg2_approx(q);
       const float E = ex2_approx(fmaf(m.g4, d, m.ngam * lc));   // c^-g q^(g-4)
       const float c = kNodeCm1[base + k] + 1.0f;
-      t1 = kNodeWs[base + k] * E;
-      t2 = (kNodeWq[base + k] * E) * (E * (c * c) * (c * q));
+      const float t1 = kNodeWs[base + k] * E;
+      const float t2 = (kNodeWq[base + k] * E) * (E * (c * c) * (c * q));
+      const float mk = lc - d;                         // log2(u_k / w)
+      const float uw = ex2_approx(mk);                 // u_k / w
+      S += t1;
+      Su = fmaf(t1, uw, Su);
+      Sl = fmaf(t1, mk, Sl);
+      Q += t2;
+      Qu = fmaf(t2, uw, Qu);
+      Ql = fmaf(t2, mk, Ql);
     }
-    const float mk = lc - d;                         // log2(u_k / w)
-    const float uw = ex2_approx(mk);                 // u_k / w
-    S += t1;
-    Su = fmaf(t1, uw, Su);
-    Sl = fmaf(t1, mk, Sl);
-    Q += t2;
-    Qu = fmaf(t2, uw, Qu);
-    Ql = fmaf(t2, mk, Ql);
   }
   Su *= w;
   Qu *= w;
@@ -184,7 +209,7 @@ __device__ __forceinline__ BulgeDer bulge_closed_vjp(const ModelConst& m, float 
 // Vector-Jacobian product of one fine point: adds sum_c a_c d f_c / d(constants) to acc.
 template <int NQ, int ND>
 __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y, float4 a, float* acc,
-                                          const float* tab, int T, const float2* nodew) {
+                                          const float* tab, int T, const float4* nodew) {
   // ---- forward (Sec. 2.1-2.4), keeping what the reverse sweep needs
   const float xr = fmaf(X, m.cpa, Y * m.spa);
   const float yr = fmaf(Y, m.cpa, -X * m.spa);
@@ -374,7 +399,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int next_item;
-  __shared__ float2 nodew[NQ];
+  __shared__ float4 nodew[NQ / 2];
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
   for (int it = blockIdx.x; it < a.n_items;) {
@@ -423,7 +448,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
       const int nt = kTabHdr + 8 * a.table_T;
       for (int t = tid; t < nt; t += kAdjThreads) tab[t] = __ldg(src + t);
     } else {
-      if (!mc.bulge_fit) fill_node_weights<NQ>(mc, nodew, tid, kAdjThreads);
+      if (!mc.bulge_fit) fill_node_pairs<NQ>(mc, nodew, tid, kAdjThreads);
     }
 
     float acc[NACC];

@@ -435,11 +435,15 @@ __device__ __forceinline__ float table_plain(const float* __restrict__ tab, int 
 }
 
 // The same sums with the per-model node factors folded into weights staged in shared
-// memory: nw[k] = (w_k cosh t_k c_k^-g, w_k tanh^2 t_k c_k^(3-2g)), so a node needs one
-// 64-bit shared load, one lg2 and one ex2: e = q^(g-4) gives both q^(g-4) and
-// q^(2g-7) = e^2 q.
+// memory, two nodes at a time: nw[k/2] = (ws_k, ws_k+1, wq_k, wq_k+1) with
+// ws_k = w_k cosh t_k c_k^-g and wq_k = w_k tanh^2 t_k c_k^(3-2g).  e = q^(g-4) gives both
+// q^(g-4) and q^(2g-7) = e^2 q, so a node needs one lg2 and one ex2; the FP32 work of a
+// pair of nodes (q, the exponent, the two sums) runs as packed two-lane FMA / MUL
+// instructions (one issue slot for both nodes, each lane rounded like fmaf), and one
+// 128-bit shared load brings the pair's four weights.  Even and odd nodes accumulate in
+// the two lanes, added at the end.
 template <int NQ>
-__device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const float2* __restrict__ nw, float R,
+__device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const float4* __restrict__ nw, float R,
                                                   float& Sigma, float& SigS2) {
   constexpr int base = NodeBase<NQ>::value;
   const float x = R * m.inv_a;
@@ -451,30 +455,34 @@ __device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const flo
   const float ip4 = i2 * i2;
   const float pS = ex2_approx(m.ngam * lw) * ip4;
   const float pQ = ex2_approx(m.g3 * lw) * ip4;
-  float S = 0.f, Q = 0.f;
+  const float2 w2 = make_float2(w, w), g2 = make_float2(m.g4, m.g4), one2 = make_float2(1.0f, 1.0f);
+  float2 S = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int k = 0; k < NQ; ++k) {
-    const float q = fmaf(w, kNodeCm1[base + k], 1.0f);
-    const float d = lg2_approx(q);
-    float2 wk;   // kept in the loop: hoisting 2 NQ invariant weights would exhaust the registers
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
-                 : "=f"(wk.x), "=f"(wk.y)
-                 : "r"((unsigned)__cvta_generic_to_shared(nw + k)));
-    const float e = ex2_approx(m.g4 * d);
-    S = fmaf(wk.x, e, S);
-    Q = fmaf(wk.y * e, e * q, Q);
+  for (int k = 0; k < NQ; k += 2) {
+    const float2 q = __ffma2_rn(w2, make_float2(kNodeCm1[base + k], kNodeCm1[base + k + 1]), one2);
+    const float2 d = make_float2(lg2_approx(q.x), lg2_approx(q.y));
+    float4 wk;   // kept in the loop: hoisting 2 NQ invariant weights would exhaust the registers
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(wk.x), "=f"(wk.y), "=f"(wk.z), "=f"(wk.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(nw + k / 2)));
+    const float2 t = __fmul2_rn(g2, d);
+    const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+    S = __ffma2_rn(make_float2(wk.x, wk.y), e, S);
+    Q = __ffma2_rn(__fmul2_rn(make_float2(wk.z, wk.w), e), __fmul2_rn(e, q), Q);
   }
-  Sigma = m.cS * x * pS * S;
-  SigS2 = m.cQ * pQ * Q;
+  Sigma = m.cS * x * pS * (S.x + S.y);
+  SigS2 = m.cQ * pQ * (Q.x + Q.y);
 }
 
-// Per-model node weights for bulge_projected_w (threads of a block fill them together).
+// Per-model node weights for bulge_projected_w, paired as (ws_k, ws_k+1, wq_k, wq_k+1)
+// (threads of a block fill them together).
 template <int NQ>
-__device__ __forceinline__ void fill_node_weights(const ModelConst& m, float2* nw, int tid, int nthreads) {
+__device__ __forceinline__ void fill_node_pairs(const ModelConst& m, float4* nw, int tid, int nthreads) {
   constexpr int base = NodeBase<NQ>::value;
-  for (int k = tid; k < NQ; k += nthreads) {
-    const float lc = kNodeLc[base + k];
-    nw[k] = make_float2(kNodeWs[base + k] * exp2f(m.ngam * lc), kNodeWq[base + k] * exp2f(m.g3 * lc));
+  for (int j = tid; j < NQ / 2; j += nthreads) {
+    const int k = base + 2 * j;
+    nw[j] = make_float4(kNodeWs[k] * exp2f(m.ngam * kNodeLc[k]), kNodeWs[k + 1] * exp2f(m.ngam * kNodeLc[k + 1]),
+                        kNodeWq[k] * exp2f(m.g3 * kNodeLc[k]), kNodeWq[k + 1] * exp2f(m.g3 * kNodeLc[k + 1]));
   }
 }
 
@@ -484,7 +492,7 @@ __device__ __forceinline__ void fill_node_weights(const ModelConst& m, float2* n
 // sigma^2 = C2 / C0 - v^2 and M/L = C3 / C0.
 template <int NQ, int ND>
 __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float Y, const float* tab = nullptr,
-                                             int T = 0, const float2* nodew = nullptr) {
+                                             int T = 0, const float4* nodew = nullptr) {
   // Sec. 2.1: rotate the major axis onto x; deproject the razor-thin discs by 1 / cos i
   const float xr = fmaf(X, m.cpa, Y * m.spa);
   const float yr = fmaf(Y, m.cpa, -X * m.spa);

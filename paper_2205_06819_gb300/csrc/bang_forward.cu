@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
   const int tid = threadIdx.x;
   __shared__ int next_item;
   __shared__ int chunk_ctr[2];
-  __shared__ float2 nodew[NQ];
+  __shared__ float4 nodew[NQ / 2];
   const int lane = threadIdx.x & 31;
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       for (int t = tid; t < nt; t += kThreads) tab[t] = __ldg(src + t);
     }
     if (tid < 2) chunk_ctr[tid] = 0;
-    if (!tab && !mc.bulge_fit) fill_node_weights<NQ>(mc, nodew, tid, kThreads);
+    if (!tab && !mc.bulge_fit) fill_node_pairs<NQ>(mc, nodew, tid, kThreads);
     __syncthreads();
 
     double chi_thread = 0.0, vsys_thread = 0.0;
