@@ -424,9 +424,10 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
     }
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx, ny = gs.ny, n = nx * ny;
     const float* seed = a.seed + a.out_off[w.b];
-    float* taps = reinterpret_cast<float*>(smem_raw);
+    // taps stored twice, (t, t): a 64-bit load gives the pair the packed two-lane FMAs need
+    float2* taps = reinterpret_cast<float2*>(smem_raw);
     const int ntaps = PSF == 0 ? L : L * L;
-    float4* lam = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 4 + 15) / 16) * 16);
+    float4* lam = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 8 + 15) / 16) * 16);
     const int nj_max = (a.G + L - 1) / os + 2;
     float4* V = lam + (size_t)nj_max * nx;
     float* tab = a.tables ? reinterpret_cast<float*>(V + (PSF == 0 ? (size_t)a.G * nx : 0)) : nullptr;
@@ -442,7 +443,10 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
       BANG_NEXT_ITEM(it);
       continue;
     }
-    for (int t = tid; t < ntaps; t += kAdjThreads) taps[t] = __ldg(gs.taps + t);
+    for (int t = tid; t < ntaps; t += kAdjThreads) {
+      const float tv = __ldg(gs.taps + t);
+      taps[t] = make_float2(tv, tv);
+    }
     if (tab) {
       const float* src = a.tables + (size_t)w.b * a.table_stride;
       const int nt = kTabHdr + 8 * a.table_T;
@@ -474,15 +478,15 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
           const int y = y0 + gr;
           int j0 = y - L + 1 <= 0 ? 0 : (y - L + os) / os;
           const int j1 = min(ny - 1, y / os);
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          float2 vxy = make_float2(0.f, 0.f), vzw = vxy;
           for (int j = j0; j <= j1; ++j) {
             if (!BANG_IN(y - j * os, L, kSiteAdjTap) || !BANG_IN(j - jlo, nj, kSiteAdjLam)) continue;
-            const float tv = taps[y - j * os];
+            const float2 tv = taps[y - j * os];
             const float4 l = lam[(j - jlo) * nx + i];
-            v.x = fmaf(tv, l.x, v.x); v.y = fmaf(tv, l.y, v.y);
-            v.z = fmaf(tv, l.z, v.z); v.w = fmaf(tv, l.w, v.w);
+            vxy = __ffma2_rn(tv, make_float2(l.x, l.y), vxy);
+            vzw = __ffma2_rn(tv, make_float2(l.z, l.w), vzw);
           }
-          V[t] = v;
+          V[t] = make_float4(vxy.x, vxy.y, vzw.x, vzw.y);
         }
         __syncthreads();
       }
@@ -499,33 +503,33 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
         const int y = y0 + gr;
         int i0 = qx - L + 1 <= 0 ? 0 : (qx - L + os) / os;
         const int i1 = min(nx - 1, qx / os);
-        float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 sxy = make_float2(0.f, 0.f), szw = sxy;
         if (PSF == 0) {
           for (int i = i0; i <= i1; ++i) {
             if (!BANG_IN(qx - i * os, L, kSiteAdjTap) || !BANG_IN(gr * nx + i, G * nx, kSiteAdjV)) continue;
-            const float th_ = taps[qx - i * os];
+            const float2 th_ = taps[qx - i * os];
             const float4 v = V[gr * nx + i];
-            s4.x = fmaf(th_, v.x, s4.x); s4.y = fmaf(th_, v.y, s4.y);
-            s4.z = fmaf(th_, v.z, s4.z); s4.w = fmaf(th_, v.w, s4.w);
+            sxy = __ffma2_rn(th_, make_float2(v.x, v.y), sxy);
+            szw = __ffma2_rn(th_, make_float2(v.z, v.w), szw);
           }
         } else {
           int j0 = y - L + 1 <= 0 ? 0 : (y - L + os) / os;
           const int j1 = min(ny - 1, y / os);
           for (int j = j0; j <= j1; ++j) {
             if (!BANG_IN(y - j * os, L, kSiteAdjTap) || !BANG_IN(j - jlo, nj, kSiteAdjLam)) continue;
-            const float* wrow = taps + (y - j * os) * L;
+            const float2* wrow = taps + (y - j * os) * L;
             for (int i = i0; i <= i1; ++i) {
               if (!BANG_IN(qx - i * os, L, kSiteAdjTap)) continue;
-              const float tw = wrow[qx - i * os];
+              const float2 tw = wrow[qx - i * os];
               const float4 l = lam[(j - jlo) * nx + i];
-              s4.x = fmaf(tw, l.x, s4.x); s4.y = fmaf(tw, l.y, s4.y);
-              s4.z = fmaf(tw, l.z, s4.z); s4.w = fmaf(tw, l.w, s4.w);
+              sxy = __ffma2_rn(tw, make_float2(l.x, l.y), sxy);
+              szw = __ffma2_rn(tw, make_float2(l.z, l.w), szw);
             }
           }
         }
         const float X = fmaf((float)qx, pk, mc.X0);
         const float Y = fmaf((float)y, pk, mc.Y0);
-        point_vjp<NQ, ND>(mc, X, Y, s4, acc, tab, a.table_T, nodew);
+        point_vjp<NQ, ND>(mc, X, Y, make_float4(sxy.x, sxy.y, szw.x, szw.y), acc, tab, a.table_T, nodew);
       }
     }
     // float64 block reduction of the adjoints, then theta-space gradient (one thread)
@@ -665,7 +669,7 @@ int adjoint_threads() { return kAdjThreads; }
 size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d, int table_T) {
   const int ntaps = psf2d ? L * L : L;
   const int nj_max = (G + L - 1) / os + 2;
-  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)nj_max * nx * 16 + (psf2d ? 0 : (size_t)G * nx * 16) +
+  return (((size_t)ntaps * 8 + 15) / 16) * 16 + (size_t)nj_max * nx * 16 + (psf2d ? 0 : (size_t)G * nx * 16) +
          (table_T > 0 ? sizeof(float) * (size_t)(kTabHdr + 8 * table_T) : 0);
 }
 

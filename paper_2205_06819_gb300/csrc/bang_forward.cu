@@ -139,9 +139,10 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     __syncthreads();
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx;
     const int NA = (L + os - 1) / os;                       // open spaxel rows
-    float* taps = reinterpret_cast<float*>(smem_raw);
+    // taps stored twice, (t, t): a 64-bit load gives the pair the packed two-lane FMAs need
+    float2* taps = reinterpret_cast<float2*>(smem_raw);
     const int ntaps = PSF == 0 ? L : L * L;
-    float4* acc = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 4 + 15) / 16) * 16);
+    float4* acc = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 8 + 15) / 16) * 16);
     float4* stage = acc + (size_t)NA * nx;
     float* tab = a.tables ? reinterpret_cast<float*>(stage + 2 * (size_t)a.G * W) : nullptr;
     float* out = nullptr;
@@ -182,7 +183,10 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       continue;
     }
 
-    for (int t = tid; t < ntaps; t += kThreads) taps[t] = __ldg(gs.taps + t);
+    for (int t = tid; t < ntaps; t += kThreads) {
+      const float tv = __ldg(gs.taps + t);
+      taps[t] = make_float2(tv, tv);
+    }
     for (int t = tid; t < NA * nx; t += kThreads) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tab) {   // this row's radial table: header, values and log-ratios of Sigma and Q
       const float* src = a.tables + (size_t)w.b * a.table_stride;
@@ -238,22 +242,23 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           for (int gr = 0; gr < G; ++gr) {
             const int y = y0 + gr;
             const float4* srow = stage_c + gr * W + i * os;
-            float4 hs = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 hxy = make_float2(0.f, 0.f), hzw = hxy;   // (B, v) and (sigma, <L/M>) lanes
             for (int k = 0; k < L; ++k) {
-              const float tw = taps[k];
+              const float2 tw = taps[k];
               const float4 v = srow[k];
-              hs.x = fmaf(tw, v.x, hs.x); hs.y = fmaf(tw, v.y, hs.y);
-              hs.z = fmaf(tw, v.z, hs.z); hs.w = fmaf(tw, v.w, hs.w);
+              hxy = __ffma2_rn(tw, make_float2(v.x, v.y), hxy);
+              hzw = __ffma2_rn(tw, make_float2(v.z, v.w), hzw);
             }
             int jlo = y - L + 1 <= 0 ? 0 : (y - L + os) / os;  // ceil((y - L + 1) / os)
             jlo = max(jlo, w.j0);
             const int jhi = min(y / os, w.j1 - 1);
             for (int j = jlo; j <= jhi; ++j) {
               if (!BANG_IN(y - j * os, L, kSiteFwdTap)) continue;
-              const float tv = taps[y - j * os];
+              const float2 tv = taps[y - j * os];
               float4& A = acc[(j % NA) * nx + i];
-              A.x = fmaf(tv, hs.x, A.x); A.y = fmaf(tv, hs.y, A.y);
-              A.z = fmaf(tv, hs.z, A.z); A.w = fmaf(tv, hs.w, A.w);
+              const float2 axy = __ffma2_rn(tv, hxy, make_float2(A.x, A.y));
+              const float2 azw = __ffma2_rn(tv, hzw, make_float2(A.z, A.w));
+              A = make_float4(axy.x, axy.y, azw.x, azw.y);
             }
             const int yl = y - L + 1;                             // spaxel row ending here
             if (yl >= 0 && yl % os == 0) {
@@ -283,14 +288,16 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           const int gb = min(G - 1, j * os + L - 1 - y0);
           for (int gr = ga; gr <= gb; ++gr) {
             if (!BANG_IN(y0 + gr - j * os, L, kSiteFwdTap)) continue;
-            const float* wrow = taps + (y0 + gr - j * os) * L;
+            const float2* wrow = taps + (y0 + gr - j * os) * L;
             const float4* srow = stage_c + gr * W + i * os;
+            float2 axy = make_float2(A.x, A.y), azw = make_float2(A.z, A.w);
             for (int k = 0; k < L; ++k) {
-              const float tw = wrow[k];
+              const float2 tw = wrow[k];
               const float4 v = srow[k];
-              A.x = fmaf(tw, v.x, A.x); A.y = fmaf(tw, v.y, A.y);
-              A.z = fmaf(tw, v.z, A.z); A.w = fmaf(tw, v.w, A.w);
+              axy = __ffma2_rn(tw, make_float2(v.x, v.y), axy);
+              azw = __ffma2_rn(tw, make_float2(v.z, v.w), azw);
             }
+            A = make_float4(axy.x, axy.y, azw.x, azw.y);
           }
           if (j * os + L - 1 <= ylast) {
             float lam_v;
@@ -402,7 +409,7 @@ int forward_threads() { return kThreads; }
 size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d, int table_T) {
   const int ntaps = psf2d ? L * L : L;
   const int NA = (L + os - 1) / os;
-  return (((size_t)ntaps * 4 + 15) / 16) * 16 + (size_t)NA * nx * 16 + 2 * (size_t)G * W * 16 +
+  return (((size_t)ntaps * 8 + 15) / 16) * 16 + (size_t)NA * nx * 16 + 2 * (size_t)G * W * 16 +
          (table_T > 0 ? sizeof(float) * (size_t)(kTabHdr + 4 * table_T) : 0);
 }
 
