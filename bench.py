@@ -41,15 +41,17 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # chains of each PTX instruction (ex2.approx issues at twice the rate of lg2.approx).
 MUFU_EX2_PER_CLK_SM = 32.0
 MUFU_LG2_PER_CLK_SM = 16.0
-FP32_PER_CLK_SM = 122.0          # measured FFMA issue (128 nominal)
+# measured FFMA rate, lane operations per clock per SM (128 nominal); a packed two-lane
+# FMA does two lane operations in two FMA-pipe cycles, so the lane rate is the same
+FP32_PER_CLK_SM = 122.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "3b2a0e9d9660b132", "bytes_per_launch": 668928}
+NCU_TRAFFIC = {"stamp": "feb1777fd34c8e0e", "bytes_per_launch": 520448}
 # Pipe activity of the forward kernel from the same kind of capture (ncu --set full on 456
 # rows of the benchmark batch): SFU (xu) and FMA pipes, issue active, thread instructions
 # per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "3b2a0e9d9660b132", "pipe_xu_pct": 46.7, "pipe_fma_pct": 40.9, "issue_active_pct": 70.4,
-             "thread_instr_per_point": 944}
+NCU_PIPES = {"stamp": "feb1777fd34c8e0e", "pipe_xu_pct": 49.1, "pipe_fma_pct": 26.7, "pipe_fma_cycles_pct": 43.7,
+             "issue_active_pct": 58.2, "thread_instr_per_point": 742}
 
 
 def kernel_stamp() -> str:
@@ -532,7 +534,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SFU op/s", "frac": achieved / peak,
                      "traffic": traffic,
-                     "fp32": {"achieved": fp32_achieved, "peak": fp32_peak, "unit": "G FP32 instr/s",
+                     "fp32": {"achieved": fp32_achieved, "peak": fp32_peak, "unit": "G FP32 lane-op/s",
                               "frac": fp32_achieved / fp32_peak},
                      "t_roof_over_t_meas": t_roof / step_s,
                      "ncu_pipes": pipes,

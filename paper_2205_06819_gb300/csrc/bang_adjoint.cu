@@ -424,10 +424,12 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
     }
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx, ny = gs.ny, n = nx * ny;
     const float* seed = a.seed + a.out_off[w.b];
-    // taps stored twice, (t, t): a 64-bit load gives the pair the packed two-lane FMAs need
+    // separable taps stored twice, (t, t): a 64-bit load gives the pair the packed
+    // two-lane FMAs need; the L x L two-dimensional taps once (shared memory)
     float2* taps = reinterpret_cast<float2*>(smem_raw);
+    float* taps2d = reinterpret_cast<float*>(smem_raw);
     const int ntaps = PSF == 0 ? L : L * L;
-    float4* lam = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 8 + 15) / 16) * 16);
+    float4* lam = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * (PSF == 0 ? 8 : 4) + 15) / 16) * 16);
     const int nj_max = (a.G + L - 1) / os + 2;
     float4* V = lam + (size_t)nj_max * nx;
     float* tab = a.tables ? reinterpret_cast<float*>(V + (PSF == 0 ? (size_t)a.G * nx : 0)) : nullptr;
@@ -445,7 +447,8 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
     }
     for (int t = tid; t < ntaps; t += kAdjThreads) {
       const float tv = __ldg(gs.taps + t);
-      taps[t] = make_float2(tv, tv);
+      if (PSF == 0) taps[t] = make_float2(tv, tv);
+      else taps2d[t] = tv;
     }
     if (tab) {
       const float* src = a.tables + (size_t)w.b * a.table_stride;
@@ -517,10 +520,10 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
           const int j1 = min(ny - 1, y / os);
           for (int j = j0; j <= j1; ++j) {
             if (!BANG_IN(y - j * os, L, kSiteAdjTap) || !BANG_IN(j - jlo, nj, kSiteAdjLam)) continue;
-            const float2* wrow = taps + (y - j * os) * L;
+            const float* wrow = taps2d + (y - j * os) * L;
             for (int i = i0; i <= i1; ++i) {
               if (!BANG_IN(qx - i * os, L, kSiteAdjTap)) continue;
-              const float2 tw = wrow[qx - i * os];
+              const float2 tw = make_float2(wrow[qx - i * os], wrow[qx - i * os]);
               const float4 l = lam[(j - jlo) * nx + i];
               sxy = __ffma2_rn(tw, make_float2(l.x, l.y), sxy);
               szw = __ffma2_rn(tw, make_float2(l.z, l.w), szw);
@@ -669,7 +672,7 @@ int adjoint_threads() { return kAdjThreads; }
 size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d, int table_T) {
   const int ntaps = psf2d ? L * L : L;
   const int nj_max = (G + L - 1) / os + 2;
-  return (((size_t)ntaps * 8 + 15) / 16) * 16 + (size_t)nj_max * nx * 16 + (psf2d ? 0 : (size_t)G * nx * 16) +
+  return (((size_t)ntaps * (psf2d ? 4 : 8) + 15) / 16) * 16 + (size_t)nj_max * nx * 16 + (psf2d ? 0 : (size_t)G * nx * 16) +
          (table_T > 0 ? sizeof(float) * (size_t)(kTabHdr + 8 * table_T) : 0);
 }
 

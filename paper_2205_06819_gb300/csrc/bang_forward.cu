@@ -139,10 +139,12 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     __syncthreads();
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx;
     const int NA = (L + os - 1) / os;                       // open spaxel rows
-    // taps stored twice, (t, t): a 64-bit load gives the pair the packed two-lane FMAs need
+    // separable taps stored twice, (t, t): a 64-bit load gives the pair the packed
+    // two-lane FMAs need; the L x L two-dimensional taps once (shared memory)
     float2* taps = reinterpret_cast<float2*>(smem_raw);
+    float* taps2d = reinterpret_cast<float*>(smem_raw);
     const int ntaps = PSF == 0 ? L : L * L;
-    float4* acc = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * 8 + 15) / 16) * 16);
+    float4* acc = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * (PSF == 0 ? 8 : 4) + 15) / 16) * 16);
     float4* stage = acc + (size_t)NA * nx;
     float* tab = a.tables ? reinterpret_cast<float*>(stage + 2 * (size_t)a.G * W) : nullptr;
     float* out = nullptr;
@@ -185,7 +187,8 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
 
     for (int t = tid; t < ntaps; t += kThreads) {
       const float tv = __ldg(gs.taps + t);
-      taps[t] = make_float2(tv, tv);
+      if (PSF == 0) taps[t] = make_float2(tv, tv);
+      else taps2d[t] = tv;
     }
     for (int t = tid; t < NA * nx; t += kThreads) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tab) {   // this row's radial table: header, values and log-ratios of Sigma and Q
@@ -288,11 +291,11 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           const int gb = min(G - 1, j * os + L - 1 - y0);
           for (int gr = ga; gr <= gb; ++gr) {
             if (!BANG_IN(y0 + gr - j * os, L, kSiteFwdTap)) continue;
-            const float2* wrow = taps + (y0 + gr - j * os) * L;
+            const float* wrow = taps2d + (y0 + gr - j * os) * L;
             const float4* srow = stage_c + gr * W + i * os;
             float2 axy = make_float2(A.x, A.y), azw = make_float2(A.z, A.w);
             for (int k = 0; k < L; ++k) {
-              const float2 tw = wrow[k];
+              const float2 tw = make_float2(wrow[k], wrow[k]);
               const float4 v = srow[k];
               axy = __ffma2_rn(tw, make_float2(v.x, v.y), axy);
               azw = __ffma2_rn(tw, make_float2(v.z, v.w), azw);
@@ -409,7 +412,7 @@ int forward_threads() { return kThreads; }
 size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d, int table_T) {
   const int ntaps = psf2d ? L * L : L;
   const int NA = (L + os - 1) / os;
-  return (((size_t)ntaps * 8 + 15) / 16) * 16 + (size_t)NA * nx * 16 + 2 * (size_t)G * W * 16 +
+  return (((size_t)ntaps * (psf2d ? 4 : 8) + 15) / 16) * 16 + (size_t)NA * nx * 16 + 2 * (size_t)G * W * 16 +
          (table_T > 0 ? sizeof(float) * (size_t)(kTabHdr + 4 * table_T) : 0);
 }
 
