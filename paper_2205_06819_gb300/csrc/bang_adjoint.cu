@@ -389,8 +389,11 @@ __device__ void constants_to_theta(const float* __restrict__ th, const double* T
   g[3] = gi;
 }
 
-template <int NQ, int ND, int PSF>
-__global__ void __launch_bounds__(kAdjThreads, 3) adjoint_kernel(AdjArgs a) {
+// MINB blocks per SM: 4 (64 registers) for the one-disc quadrature form, whose spills cost
+// less than the extra warps gain; 3 (80 registers) for two discs and for the radial-table
+// mode, whose shared memory holds 3 blocks per SM anyway.
+template <int NQ, int ND, int PSF, int MINB>
+__global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
   constexpr int NACC = A_D0 + kPerDisc * ND;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ModelConst mc;
@@ -658,10 +661,18 @@ __global__ void table_kernel(const ModelConst* __restrict__ consts, const GalDev
   }
 }
 
+constexpr int adj_min_blocks(int nd, bool table) { return nd == 1 && !table ? 4 : 3; }
+
 template <int NQ, int ND>
 cudaError_t launch_nd(const AdjArgs& a, int psf2d, int grid, size_t smem, cudaStream_t st) {
-  if (psf2d) adjoint_kernel<NQ, ND, 1><<<grid, kAdjThreads, smem, st>>>(a);
-  else adjoint_kernel<NQ, ND, 0><<<grid, kAdjThreads, smem, st>>>(a);
+  constexpr int kQuad = adj_min_blocks(ND, false), kTab = adj_min_blocks(ND, true);
+  if (a.tables) {
+    if (psf2d) adjoint_kernel<NQ, ND, 1, kTab><<<grid, kAdjThreads, smem, st>>>(a);
+    else adjoint_kernel<NQ, ND, 0, kTab><<<grid, kAdjThreads, smem, st>>>(a);
+  } else {
+    if (psf2d) adjoint_kernel<NQ, ND, 1, kQuad><<<grid, kAdjThreads, smem, st>>>(a);
+    else adjoint_kernel<NQ, ND, 0, kQuad><<<grid, kAdjThreads, smem, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -678,9 +689,11 @@ size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d, int table_T) 
 
 int64_t table_row_floats(int T, int derivs) { return kTabHdr + (int64_t)(derivs ? 8 : 4) * T; }
 
-const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d) {
-#define BANG_PICK(NQ, ND, PSF) \
-  if (n_quad == NQ && n_discs == ND && psf2d == PSF) return (const void*)adjoint_kernel<NQ, ND, PSF>;
+const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d, int table) {
+#define BANG_PICK(NQ, ND, PSF)                                                                        \
+  if (n_quad == NQ && n_discs == ND && psf2d == PSF)                                                  \
+    return table ? (const void*)adjoint_kernel<NQ, ND, PSF, adj_min_blocks(ND, true)>                 \
+                 : (const void*)adjoint_kernel<NQ, ND, PSF, adj_min_blocks(ND, false)>;
   BANG_PICK(64, 1, 0) BANG_PICK(64, 1, 1) BANG_PICK(64, 2, 0) BANG_PICK(64, 2, 1)
   BANG_PICK(128, 1, 0) BANG_PICK(128, 1, 1) BANG_PICK(128, 2, 0) BANG_PICK(128, 2, 1)
 #undef BANG_PICK

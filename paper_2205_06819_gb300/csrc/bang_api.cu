@@ -502,7 +502,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
       asmem = std::max(asmem, bang::adjoint_smem_bytes(G.L, G.os, G.nx, p->adj_G, psf2d, m->opts.bulge_table));
     }
     p->adj_smem = asmem;
-    const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d);
+    const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, m->opts.bulge_table > 0);
     cudaFuncAttributes afa;
     BANG_CUDA(cudaFuncGetAttributes(&afa, ak));
     if (asmem + afa.sharedSizeBytes > (size_t)m->smem_optin)

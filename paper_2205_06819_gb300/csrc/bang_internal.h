@@ -115,7 +115,8 @@ size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d, int table_T =
 int64_t table_row_floats(int T, int derivs);
 cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int n_gal, int B, int n_quad,
                           int T, int derivs, float* tables, int64_t stride, cudaStream_t st);
-const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d);
+// The adjoint kernel a launch uses (its blocks-per-SM bound depends on the radial-table mode).
+const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d, int table);
 cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
                            cudaStream_t st);
 cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind,
