@@ -64,12 +64,14 @@ struct ModelConst {
   // bulge (Dehnen): a, gamma
   float inv_a, ngam, g4, g3, three_mg;
   float cS, cQ, vb_c;      // Sigma = cS x pS S; Sigma sigma^2 = cQ pQ Q; vb^2 = vb_c u^(3-g) / (r/a)
+  float vb_r;              // G M_b: vb^2 = vb_r u^(3-g) / r (the forward's form, with 1/r at hand)
   float Lb;                // 1e-6 / (M/L)_b
   // halo (NFW)
   float inv_rs, vh_c;      // x = r / rs; NFW vh^2 = vh_c m(x) / r; Hernquist vh^2 = vh_c x / (1 + x)^2
   int hern;                // halo kind: 0 NFW, 1 Hernquist
   // discs
   float inv_Rd[2], half_inv_Rd[2], vd_c[2], Sd_c[2], Ld[2], ks[2], omk[2];
+  float two_Rd[2];         // 2 R_d: 1 / y = 2 R_d / r for the disc's velocity fit
   float vsys;
   int flux;                // the galaxy's flux-weighted PSF mode (GalDev::flux)
   int bulge_fit;           // GalDev::bulge_kind: 0 radial rule, 1 / 2 closed-form fits
@@ -93,6 +95,11 @@ __device__ __forceinline__ float lg2_approx(float x) {
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float sqrt_approx(float x) {
@@ -178,6 +185,7 @@ __device__ inline void decode_finish(const float* __restrict__ th, const double*
   m.cS = (float)((3.0 - gam) * Mb / (2.0 * kPi * a * a));
   m.cQ = (float)(kG * (3.0 - gam) * Mb * Mb / (2.0 * kPi * a * a * a));
   m.vb_c = (float)(kG * Mb / a);
+  m.vb_r = (float)(kG * Mb);
   m.bulge_fit = g.bulge_kind;
   if (g.bulge_kind != 0) {   // closed-form fits: Sigma = (M / a^2) F_S, Sigma sigma^2 = (G M^2 / a^3) F_Q
     m.cS = (float)(Mb / (a * a));
@@ -198,7 +206,7 @@ __device__ inline void decode_finish(const float* __restrict__ th, const double*
   // discs
   for (int j = 0; j < 2; ++j) {
     if (j >= nd) {
-      m.inv_Rd[j] = m.half_inv_Rd[j] = m.vd_c[j] = m.Sd_c[j] = m.Ld[j] = m.ks[j] = m.omk[j] = 0.f;
+      m.inv_Rd[j] = m.half_inv_Rd[j] = m.vd_c[j] = m.Sd_c[j] = m.Ld[j] = m.ks[j] = m.omk[j] = m.two_Rd[j] = 0.f;
       continue;
     }
     const int o = j == 0 ? 7 : 15;
@@ -206,6 +214,7 @@ __device__ inline void decode_finish(const float* __restrict__ th, const double*
     const double ml = j == 0 ? th[11] : th[18];
     m.inv_Rd[j] = (float)(1.0 / Rd);
     m.half_inv_Rd[j] = (float)(0.5 / Rd);
+    m.two_Rd[j] = (float)(2.0 * Rd);
     m.vd_c[j] = (float)(2.0 * kG * Md / Rd);
     m.Sd_c[j] = (float)(Md / (2.0 * kPi * Rd * Rd * ci));
     m.Ld[j] = (float)(1e-6 / ml);
@@ -228,7 +237,8 @@ __device__ inline int decode_model(const float* __restrict__ th, int nd, int hal
 }
 
 // F(y) = y^2 [I0 K0 - I1 K1](y) from the generated float32 fits (see disc_fit.h).
-__device__ __forceinline__ float disc_F(float y) {
+// u = 1 / y, used for y > 1 (the caller may have it from a reciprocal it already holds).
+__device__ __forceinline__ float disc_F(float y, float u) {
   if (y <= 1.0f) {
     const float s = y * y;
     float P = kDiscP[BANG_DISC_DEG_A], Q = kDiscQ[BANG_DISC_DEG_A];
@@ -239,7 +249,6 @@ __device__ __forceinline__ float disc_F(float y) {
     }
     return s * (P - lg2_approx(y) * 0.693147181f * Q);
   }
-  const float u = rcp_approx(y);
   const int e = (int)((__float_as_uint(u) >> 23) & 0xff) - 127;   // u in [2^e, 2^(e+1))
   int k = -e - 1;
   k = k < 0 ? 0 : (k > BANG_DISC_NPIECE_B - 1 ? BANG_DISC_NPIECE_B - 1 : k);
@@ -249,6 +258,8 @@ __device__ __forceinline__ float disc_F(float y) {
   for (int i = BANG_DISC_DEG_B - 1; i >= 0; --i) gv = fmaf(gv, t, kDiscG[k][i]);
   return gv * (0.25f * u);
 }
+
+__device__ __forceinline__ float disc_F(float y) { return disc_F(y, y > 1.0f ? rcp_approx(y) : 0.f); }
 
 // F(y) and dF/dy from the same fits (Horner carries the derivative along).
 //   y <= 1: F = s (P - ln y Q)  ->  F' = 2y [P + s P' - ln y (Q + s Q') - Q/2]
@@ -500,8 +511,9 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
   const float yd = yr * m.inv_ci;
   const float r2 = fmaf(xr, xr, yd * yd);
   const float R = sqrt_approx(fmaxf(R2, kR2Floor));
-  const float r = sqrt_approx(fmaxf(r2, kR2Floor));
-  const float inv_r = rcp_approx(r);
+  const float r2c = fmaxf(r2, kR2Floor);
+  const float inv_r = rsqrt_approx(r2c);   // r and 1 / r from one SFU operation
+  const float r = r2c * inv_r;
   const float cphi = xr * inv_r;
 
   float Sb, SbS2;
@@ -520,12 +532,12 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
   // circular velocities in the disc plane (Eq. 10)
   const float xa = r * m.inv_a;
   const float ub = xa * rcp_approx(xa + 1.0f);
-  float vint2 = __fdividef(m.vb_c * ex2_approx(m.three_mg * lg2_approx(ub)), xa);
+  float vint2 = m.vb_r * ex2_approx(m.three_mg * lg2_approx(ub)) * inv_r;   // vb_c u^(3-g) / (r / a)
   vint2 += halo_v2(m, r, inv_r);
   float Sd[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    vint2 += m.vd_c[j] * disc_F(r * m.half_inv_Rd[j]);
+    vint2 += m.vd_c[j] * disc_F(r * m.half_inv_Rd[j], m.two_Rd[j] * inv_r);
     Sd[j] = m.Sd_c[j] * ex2_approx(-r * m.inv_Rd[j] * 1.44269504f);
   }
   const float vint = sqrt_approx(vint2);
