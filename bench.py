@@ -46,12 +46,12 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 122.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "feb1777fd34c8e0e", "bytes_per_launch": 520448}
+NCU_TRAFFIC = {"stamp": "9d435d97d26259a1", "bytes_per_launch": 467968}
 # Pipe activity of the forward kernel from the same kind of capture (ncu --set full on 456
 # rows of the benchmark batch): SFU (xu) and FMA pipes, issue active, thread instructions
 # per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "feb1777fd34c8e0e", "pipe_xu_pct": 49.1, "pipe_fma_pct": 26.7, "pipe_fma_cycles_pct": 43.7,
-             "issue_active_pct": 58.2, "thread_instr_per_point": 742}
+NCU_PIPES = {"stamp": "9d435d97d26259a1", "pipe_xu_pct": 48.9, "pipe_fma_pct": 27.1, "pipe_fma_cycles_pct": 44.3,
+             "issue_active_pct": 58.6, "thread_instr_per_point": 737}
 
 
 def kernel_stamp() -> str:
