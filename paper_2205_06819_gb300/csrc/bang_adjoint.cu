@@ -218,8 +218,9 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float r2 = fmaf(xr, xr, yd * yd);
   const bool Rfree = R2 > kR2Floor, rfree = r2 > kR2Floor;
   const float R = sqrt_approx(fmaxf(R2, kR2Floor));
-  const float r = sqrt_approx(fmaxf(r2, kR2Floor));
-  const float inv_r = rcp_approx(r);
+  const float r2c = fmaxf(r2, kR2Floor);
+  const float inv_r = rsqrt_approx(r2c);   // r and 1 / r from one SFU operation
+  const float r = r2c * inv_r;
   const float cphi = xr * inv_r;
 
   const BulgeDer bd = tab ? bulge_table_vjp(m, tab, T, R)
@@ -228,7 +229,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float xa = r * m.inv_a;
   const float ub = xa * rcp_approx(xa + 1.0f);
   const float lub = lg2_approx(ub);
-  const float vb2 = __fdividef(m.vb_c * ex2_approx(m.three_mg * lub), xa);
+  const float vb2 = m.vb_r * ex2_approx(m.three_mg * lub) * inv_r;   // vb_c u^(3-g) / (r / a)
   const float xh = r * m.inv_rs;
   const float ixh1 = rcp_approx(1.0f + xh);
   // NFW: vh2 = vh_c m(x) / r; Hernquist: vh2 = vh_c h(x), h = x / (1 + x)^2
@@ -238,7 +239,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   float Fd[ND], dFd[ND], ex[ND], Sd[ND];
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    disc_F_d(r * m.half_inv_Rd[j], Fd[j], dFd[j]);
+    disc_F_d(r * m.half_inv_Rd[j], m.two_Rd[j] * inv_r, Fd[j], dFd[j]);
     vint2 = fmaf(m.vd_c[j], Fd[j], vint2);
     ex[j] = ex2_approx(-r * m.inv_Rd[j] * 1.44269504f);
     Sd[j] = m.Sd_c[j] * ex[j];

@@ -264,7 +264,8 @@ __device__ __forceinline__ float disc_F(float y) { return disc_F(y, y > 1.0f ? r
 // F(y) and dF/dy from the same fits (Horner carries the derivative along).
 //   y <= 1: F = s (P - ln y Q)  ->  F' = 2y [P + s P' - ln y (Q + s Q') - Q/2]
 //   y >  1: F = g(t) u / 4      ->  F' = -(u^2 / 4) [g + u g'(t) invhalf]
-__device__ __forceinline__ void disc_F_d(float y, float& F, float& dF) {
+// u = 1 / y, used for y > 1 (as in disc_F).
+__device__ __forceinline__ void disc_F_d(float y, float u, float& F, float& dF) {
   if (y <= 1.0f) {
     const float s = y * y;
     float P = kDiscP[BANG_DISC_DEG_A], Q = kDiscQ[BANG_DISC_DEG_A], dP = 0.f, dQ = 0.f;
@@ -280,7 +281,6 @@ __device__ __forceinline__ void disc_F_d(float y, float& F, float& dF) {
     dF = 2.0f * y * (P + s * dP - ly * (Q + s * dQ) - 0.5f * Q);
     return;
   }
-  const float u = rcp_approx(y);
   const int e = (int)((__float_as_uint(u) >> 23) & 0xff) - 127;
   int k = -e - 1;
   k = k < 0 ? 0 : (k > BANG_DISC_NPIECE_B - 1 ? BANG_DISC_NPIECE_B - 1 : k);
