@@ -46,11 +46,11 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 122.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "9d435d97d26259a1", "bytes_per_launch": 467968}
+NCU_TRAFFIC = {"stamp": "5f321c2e9dfcac65", "bytes_per_launch": 582400}
 # Pipe activity of the forward kernel from the same kind of capture (ncu --set full on 456
 # rows of the benchmark batch): SFU (xu) and FMA pipes, issue active, thread instructions
 # per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "9d435d97d26259a1", "pipe_xu_pct": 48.9, "pipe_fma_pct": 27.1, "pipe_fma_cycles_pct": 44.3,
+NCU_PIPES = {"stamp": "5f321c2e9dfcac65", "pipe_xu_pct": 48.9, "pipe_fma_pct": 27.1, "pipe_fma_cycles_pct": 44.3,
              "issue_active_pct": 58.6, "thread_instr_per_point": 737}
 
 
