@@ -212,6 +212,19 @@ bang_status bang_loglike_grids(bang_model *m, const float *theta, int B, const i
 bang_status bang_loglike_batch_noalloc(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
                                        double *logL, void *stream);
 
+/* Float64 check path: logL of B rows computed with every step in float64 (Sec. 2.1-2.4,
+ * Eq. 18, Eq. 21) in the plainest form (one kernel per step: fine points, spaxels, sum),
+ * on the same discretisation as bang_loglike_batch: padded fine grid, the fixed radial
+ * rule in float64 (n_quad nodes, t in [0, 16]), the float64 PSF (x) box taps, 1/delta^2 in
+ * float64, the data maps as given.  The disc velocity uses the modified Bessel functions
+ * themselves (valid for r / (2 R_d) < ~700).  For comparisons with a float64 reference,
+ * not for speed.  theta [B][P] float64 and logL [B] float64 may each be host or device
+ * memory; gal_idx is a host array [B] or NULL.  Rows outside the parameter domain give
+ * -inf.  Supported: bulge_kind 0 (radial rule; bulge_table is ignored), psf_mode without
+ * BANG_PSF_FLUX; otherwise BANG_E_UNSUPPORTED.  Synchronous on `stream`. */
+bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t *gal_idx, int B, double *logL,
+                              void *stream);
+
 /* Chooses launch parameters (rows of the fine grid per block step, blocks per SM) for
  * batches like (gal_idx, B) by timing candidates on the device; the choice is cached in the
  * model.  gal_idx as in bang_loglike_batch.  Synchronous. */

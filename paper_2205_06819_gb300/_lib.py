@@ -59,6 +59,7 @@ _SIGNATURES = {
     "bang_loglike_plain": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "bang_loglike_grids": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP, _VP]),
     "bang_loglike_batch_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
+    "bang_loglike_fp64": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "bang_model_tune": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "bang_last_error": (ctypes.c_char_p, []),
     "bang_checked_build": (ctypes.c_int, []),

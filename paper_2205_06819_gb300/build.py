@@ -28,7 +28,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 BUILD_DIR_CHECKED = os.path.join(HERE, "_build_checked")
 CHECKED_FLAGS = ["-DBANG_CHECKED"]
 
-SOURCES = ["bang_api.cu", "bang_forward.cu", "bang_adjoint.cu", "bang_plain.cu"]
+SOURCES = ["bang_api.cu", "bang_forward.cu", "bang_adjoint.cu", "bang_plain.cu", "bang_fp64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

@@ -109,6 +109,26 @@ void node_tables(std::vector<float>& cm1, std::vector<float>& lc, std::vector<fl
   }
 }
 
+// The same rule in float64 for the check path: cosh t_k, tanh^2 t_k, w_k, rows as above.
+void node_tables64(std::vector<double>& ch, std::vector<double>& th2, std::vector<double>& w64) {
+  ch.assign(192, 0.0);
+  th2.assign(192, 0.0);
+  w64.assign(192, 0.0);
+  const double T = 16.0;
+  int base = 0;
+  for (int n : {64, 128}) {
+    std::vector<double> x, w;
+    legendre_rule(n, x, w);
+    for (int k = 0; k < n; ++k) {
+      const double t = 0.5 * T * (x[k] + 1.0), th = std::tanh(t);
+      ch[base + k] = std::cosh(t);
+      th2[base + k] = th * th;
+      w64[base + k] = 0.5 * T * w[k];
+    }
+    base += n;
+  }
+}
+
 int psf_halfwidth(double fwhm, double pitch) {
   if (!(fwhm > 0.0)) return 0;
   const double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
@@ -128,7 +148,8 @@ int psf_halfwidth(double fwhm, double pitch) {
 //    centre (|offset| <= 1/2), which alone are used (equal weights) without a PSF.
 // Separable ([L], the two-axis weight is T[cy] T[cx]) for a Gaussian with the square
 // window; otherwise the two-dimensional table W2[cy][cx] ([L][L]).
-std::vector<float> make_taps(int kind, double fwhm, double beta, int os, int h, double pitch, int mode) {
+// (float64; the kernels take them rounded to float32, the float64 check path as they are)
+std::vector<double> make_taps_d(int kind, double fwhm, double beta, int os, int h, double pitch, int mode) {
   const int L = os + 2 * h;
   const bool circle = (mode & BANG_PSF_CIRCLE) != 0, centre = (mode & BANG_PSF_CENTRE) != 0;
   const bool two_d = kind == 1 || circle;
@@ -167,7 +188,7 @@ std::vector<float> make_taps(int kind, double fwhm, double beta, int os, int h, 
         t[c] /= os;
       }
     }
-    return std::vector<float>(t.begin(), t.end());
+    return t;
   }
   std::vector<double> W2((size_t)L * L, 0.0);
   double tot = 0.0;
@@ -201,7 +222,12 @@ std::vector<float> make_taps(int kind, double fwhm, double beta, int os, int h, 
         W2[(size_t)cy * L + cx] = acc / ((double)os * os);
       }
   }
-  return std::vector<float>(W2.begin(), W2.end());
+  return W2;
+}
+
+std::vector<float> make_taps(int kind, double fwhm, double beta, int os, int h, double pitch, int mode) {
+  const std::vector<double> t = make_taps_d(kind, fwhm, beta, os, h, pitch, mode);
+  return std::vector<float>(t.begin(), t.end());
 }
 
 // Device memory the library allocates while serving calls (plans, staging, scratch), with
@@ -322,6 +348,13 @@ struct bang_model {
   cudaStream_t capture_stream = nullptr;
   cudaEvent_t last_work = nullptr;   // recorded after each call's device work (see CallOrder)
   bool use_graphs = true;
+  // float64 check path (bang_loglike_fp64): float64 taps and 1/delta^2 kept from create,
+  // uploaded with the float64 node rule on the first call
+  std::vector<std::vector<double>> taps64, iv64;
+  std::vector<double> pitch64;
+  std::vector<bang::Gal64> g64;
+  DevBuf nodes64, fp64_scratch, fp64_theta, fp64_out;
+  std::mutex fp64_mu;
 };
 
 namespace {
@@ -743,13 +776,15 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
     G.yoff_kpa = d.spaxel_arcsec * ((0.5 - G.h) / d.oversample - 0.5 * d.ny) * d.kpc_per_arcsec;
     const size_t n = (size_t)4 * d.nx * d.ny;
     std::vector<float> data(n), iv(n);
+    std::vector<double> iv64(n, 0.0);
     double nc = 0.0;
     for (size_t s = 0; s < n; ++s) {
       const bool used = !d.mask || d.mask[s];
       data[s] = used ? d.data[s] : 0.f;
       if (used) {
         const double e = (double)d.err[s];
-        iv[s] = (float)(1.0 / (e * e));
+        iv64[s] = 1.0 / (e * e);
+        iv[s] = (float)iv64[s];
         nc += std::log(std::sqrt(2.0 * kPiD) * e);
       } else {
         iv[s] = 0.f;
@@ -765,6 +800,9 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
     m->gals.push_back(G);
     m->desc.push_back(d);
     m->h_of.push_back(G.h);
+    m->iv64.push_back(std::move(iv64));
+    m->taps64.push_back(make_taps_d(d.psf_kind, d.psf_fwhm_arcsec, d.moffat_beta, G.os, G.h, pitch, opts->psf_mode));
+    m->pitch64.push_back(pitch * d.kpc_per_arcsec);
   }
   BANG_CUDA(copy_vec(m->d_gals, m->gals));
   BANG_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
@@ -1036,6 +1074,124 @@ bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t*
   }
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   if (!th_dev || !l_dev) BANG_CUDA(cudaStreamSynchronize(st));
+  return bang::check_faults(st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The parameter domain of theta_in_domain (bang_device.cuh), in float64, for the radial-rule
+// bulge.
+bool in_domain64(const double* th, int nd, int halo_kind) {
+  const int np = nd == 2 ? 19 : 15;
+  for (int i = 0; i < np; ++i)
+    if (!std::isfinite(th[i])) return false;
+  if (!(th[3] >= 0.0 && th[3] < 0.5 * kPiD)) return false;
+  if (!(th[6] >= 0.0 && th[6] < 3.0)) return false;
+  if (!(std::fabs(th[9]) <= 1.0)) return false;
+  if (!(th[10] > 0.0 && th[11] > 0.0)) return false;
+  if (halo_kind == 0 && !(th[13] > 0.0)) return false;
+  if (nd == 2 && !(std::fabs(th[17]) <= 1.0 && th[18] > 0.0)) return false;
+  return true;
+}
+
+// Device copies of the float64 check path's tables (first call only).
+bang_status fp64_prepare(bang_model* m) {
+  if (!m->g64.empty()) return BANG_OK;
+  std::vector<double> ch, th2, w;
+  node_tables64(ch, th2, w);
+  std::vector<double> all(ch);
+  all.insert(all.end(), th2.begin(), th2.end());
+  all.insert(all.end(), w.begin(), w.end());
+  BANG_CUDA(copy_vec(m->nodes64, all));
+  std::vector<bang::Gal64> g64;
+  for (size_t gi = 0; gi < m->gals.size(); ++gi) {
+    const bang::GalDev& G = m->gals[gi];
+    bang::Gal64 g{};
+    g.nx = G.nx;
+    g.ny = G.ny;
+    g.os = G.os;
+    g.h = G.h;
+    g.L = G.L;
+    g.W = G.W;
+    g.H = G.H;
+    g.psf2d = G.psf_kind;
+    g.pitch = m->pitch64[gi];
+    g.xoff = G.xoff_kpa;
+    g.yoff = G.yoff_kpa;
+    g.norm_const = G.norm_const;
+    g.data = G.data;
+    bang_status s;
+    if ((s = upload(m, m->taps64[gi], &g.taps)) != BANG_OK) return s;
+    if ((s = upload(m, m->iv64[gi], &g.iv)) != BANG_OK) return s;
+    g64.push_back(g);
+  }
+  m->g64 = std::move(g64);
+  return BANG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bang_status bang_loglike_fp64(bang_model* m, const double* theta, const int32_t* gal_idx, int B, double* logL,
+                              void* stream) {
+  bang::NvtxRange nvtx("bang_loglike_fp64");
+  g_last_error.clear();
+  if (!m) return fail(BANG_E_INVALID_ARG, "null model");
+  if (!theta || !logL || B < 1) return fail(BANG_E_INVALID_ARG, "theta or logL is null, or B < 1");
+  if (m->opts.bulge_kind != 0)
+    return fail(BANG_E_UNSUPPORTED, "bang_loglike_fp64: radial-rule bulge only (bulge_kind 0)");
+  if (m->opts.psf_mode & BANG_PSF_FLUX) return fail(BANG_E_UNSUPPORTED, "bang_loglike_fp64: no flux-weighted PSF mode");
+  for (int b = 0; b < B; ++b) {
+    const int g = gal_idx ? gal_idx[b] : 0;
+    if (g < 0 || g >= (int)m->gals.size()) return fail(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
+  }
+  std::lock_guard<std::mutex> lock(m->fp64_mu);
+  BANG_CUDA(cudaSetDevice(m->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bang_status s = fp64_prepare(m);
+  if (s != BANG_OK) return s;
+  const int P = m->P;
+  const size_t th_bytes = sizeof(double) * (size_t)B * P;
+  std::vector<double> th((size_t)B * P), out((size_t)B, 0.0);
+  if (is_device_pointer(theta)) {
+    BANG_CUDA(cudaMemcpyAsync(th.data(), theta, th_bytes, cudaMemcpyDeviceToHost, st));
+    BANG_CUDA(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(th.data(), theta, th_bytes);
+  }
+  size_t need = 16;
+  for (int b = 0; b < B; ++b) {
+    const bang::Gal64& g = m->g64[gal_idx ? gal_idx[b] : 0];
+    need = std::max(need, bang::fp64_scratch_bytes(g.W * g.H, g.nx * g.ny));
+  }
+  BANG_CUDA(m->fp64_scratch.reserve(need));
+  BANG_CUDA(m->fp64_theta.reserve(th_bytes));
+  BANG_CUDA(m->fp64_out.reserve(sizeof(double) * B));
+  BANG_CUDA(cudaMemcpyAsync(m->fp64_theta.p, th.data(), th_bytes, cudaMemcpyHostToDevice, st));
+  const int base = m->opts.n_quad == 64 ? 0 : 64;
+  const double* nd64 = m->nodes64.as<double>();
+  const bang::Nodes64 nodes{nd64 + base, nd64 + 192 + base, nd64 + 384 + base, m->opts.n_quad};
+  std::vector<char> ok((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    ok[b] = in_domain64(th.data() + (size_t)b * P, m->opts.n_discs, m->opts.halo_kind);
+    if (!ok[b]) continue;
+    BANG_CUDA(bang::launch_fp64_row(m->fp64_theta.as<double>() + (size_t)b * P, m->opts.n_discs, m->opts.halo_kind,
+                                    nodes, m->g64[gal_idx ? gal_idx[b] : 0], m->fp64_scratch.p,
+                                    m->fp64_out.as<double>() + b, st));
+  }
+  BANG_CUDA(cudaMemcpyAsync(out.data(), m->fp64_out.p, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  BANG_CUDA(cudaStreamSynchronize(st));
+  for (int b = 0; b < B; ++b)
+    if (!ok[b]) out[b] = -INFINITY;
+  if (is_device_pointer(logL)) {
+    BANG_CUDA(cudaMemcpyAsync(logL, out.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    BANG_CUDA(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(logL, out.data(), sizeof(double) * B);
+  }
   return bang::check_faults(st);
 }
 

@@ -138,6 +138,28 @@ bang_status check_faults(cudaStream_t st);
 // Checked build: one in-range check of i against n run on the device (the selftest site).
 cudaError_t launch_check_selftest(long long i, long long n, cudaStream_t st);
 
+// Float64 check path (bang_loglike_fp64): one galaxy as that path reads it.
+struct Gal64 {
+  int nx, ny, os, h, L, W, H;
+  int psf2d;                // taps: 0 separable [L], 1 two-dimensional [L][L]
+  double pitch, xoff, yoff; // kpc: x of padded fine column q is xoff + q pitch
+  double norm_const;
+  const double* taps;       // float64 taps (the float32 kernels' taps before rounding)
+  const float* data;        // [4][ny][nx], the model's data maps
+  const double* iv;         // [4][ny][nx], mask / delta^2 in float64
+};
+// Radial rule in float64: cosh t_k, tanh^2 t_k and the weights w_k of n_quad nodes.
+struct Nodes64 {
+  const double* ch;
+  const double* th2;
+  const double* w;
+  int n;
+};
+size_t fp64_scratch_bytes(int N, int n);
+// logL of one row (theta float64 [P] on the device, already inside the parameter domain).
+cudaError_t launch_fp64_row(const double* theta, int nd, int halo_kind, const Nodes64& nodes, const Gal64& g,
+                            void* scratch, double* logL, cudaStream_t st);
+
 size_t plain_scratch_bytes(int N, int n);
 int plain_launches_per_row();
 cudaError_t launch_plain_row(const float* theta, int P, int n_quad, int n_discs, int halo_kind, const GalDev* d_gal,

@@ -152,6 +152,20 @@ class Model:
                                                  _stream_handle(theta.device) if theta.is_cuda else None))
         return out
 
+    def loglike_fp64(self, theta: torch.Tensor, gal_idx=None) -> torch.Tensor:
+        """logL [B] through the float64 check path (bang_loglike_fp64) for theta [B, P]
+        float64 (device or host tensor): every step in float64, for comparisons with a
+        float64 reference."""
+        if theta.dim() != 2 or theta.shape[1] != self.nparams or theta.dtype != torch.float64:
+            raise ValueError(f"theta must be float64 [B, {self.nparams}]")
+        theta = theta.contiguous()
+        B = theta.shape[0]
+        out = torch.empty(B, dtype=torch.float64, device=theta.device)
+        gi, gptr = self._gal_idx(gal_idx, B)
+        _lib.check(_lib.lib().bang_loglike_fp64(self._h, _ptr(theta), gptr, B, _ptr(out),
+                                                _stream_handle(theta.device) if theta.is_cuda else None))
+        return out
+
     def maps(self, theta: torch.Tensor, gal_idx=None):
         """Model maps: a list of [4, ny, nx] float32 tensors, one per row."""
         theta = self._check_theta(theta)
