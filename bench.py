@@ -8,8 +8,10 @@ chi-square accumulation.  One step = logL of the whole batch (one persistent lau
 
 Prints one JSON line: device-timed evals/s (`value`), end-to-end evals/s through the C
 ABI with host buffers (`e2e`), the roofline of the dominant kernel, SM clocks sampled
-during the timed region, and the FP64 CPU oracle timed on a bounded sample
-(`cpu_baseline`).  ``--impl reference`` times the oracle alone in the same format.
+during the timed region, the GPU, its SM count and the host's cores (`device`), and the
+FP64 CPU oracle timed on a bounded sample (`cpu_baseline`, whose `parity` compares the
+oracle's chi^2 of the rows it evaluated with the timed batch's logL).  ``--impl
+reference`` times the oracle alone in the same format.
 
 Multi-GPU: launched by torchrun, every rank evaluates its own batch (weak scaling, no
 collective on the data path); the timing is the maximum over ranks.
