@@ -85,7 +85,27 @@ def parse():
                     help="1 Hernquist / 2 Jaffe closed-form bulge instead of the Dehnen quadrature")
     ap.add_argument("--psf-mode", type=int, default=0,
                     help="PSF mode bits: 1 circular window, 2 centre sampling, 4 flux-weighted moments")
+    ap.add_argument("--list-workloads", action="store_true",
+                    help="print the five workloads as JSON lines (no GPU) and exit")
     return ap.parse_args()
+
+
+def workload_json(name: str) -> dict:
+    """One workload as plain data: its galaxies (grid, oversampling, PSF), rows, model and
+    the padded fine points per evaluation."""
+    import dataclasses
+    wl = synth.workload(name)
+    gals = [dataclasses.asdict(g) for g in wl.galaxies]
+    if len(gals) > 1:   # the uneven batch: distinct galaxy specs with their counts
+        uniq = {}
+        for g in gals:
+            key = json.dumps(g, sort_keys=True)
+            uniq.setdefault(key, [g, 0])[1] += 1
+        gals = [dict(g, count=n) for g, n in uniq.values()]
+    return {"workload": wl.name, "description": wl.description, "galaxies": gals,
+            "rows_per_galaxy": wl.rows_per_galaxy, "rows": wl.batch, "n_discs": wl.n_discs, "n_quad": wl.n_quad,
+            "nparams": wl.nparams, "gamma_fixed": wl.gamma_fixed, "gradient": wl.grad,
+            "padded_fine_points_per_row": points_per_eval(wl.galaxies[0]) if len(wl.galaxies) == 1 else "per galaxy"}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -568,6 +588,10 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.list_workloads:
+        for name in synth.WORKLOADS:
+            print(json.dumps(workload_json(name)))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -77,3 +77,21 @@ def test_cpu_baseline_parity_sample():
     assert ok["parity"]["max_rel_chi2_err"] < 1e-12
     bad = bench.cpu_oracle_sample(WL, Gal, theta, 0.05, logL + 0.5e-4 * chi2)
     assert not bad["parity"]["pass"]
+
+
+def test_list_workloads_prints_the_five_configurations():
+    """``bench.py --list-workloads`` prints each workload as plain data (no GPU needed)."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                       "bench.py"), "--list-workloads"],
+                         capture_output=True, text=True, check=True).stdout.strip().splitlines()
+    rows = [json.loads(line) for line in out]
+    assert [r["workload"] for r in rows] == list(synth.WORKLOADS)
+    by = {r["workload"]: r for r in rows}
+    assert by["batched"]["rows"] == 1024 and by["batched"]["padded_fine_points_per_row"] == 430 * 430
+    assert by["adjoint"]["gradient"] and by["adjoint"]["rows"] == 256
+    assert by["largest"]["n_discs"] == 2 and by["largest"]["n_quad"] == 128 and by["largest"]["rows"] == 4096
+    assert by["largest"]["padded_fine_points_per_row"] == 940 * 940
+    assert by["uneven"]["rows"] == 64 * 64 and sum(g["count"] for g in by["uneven"]["galaxies"]) == 64
+    assert by["single"]["rows"] == 1 and by["single"]["gamma_fixed"] == 1.0
