@@ -61,3 +61,11 @@ def test_loader_picks_the_checked_build_from_the_environment(monkeypatch):
     assert _lib.library_path() == _lib.LIB_CHECKED_PATH
     monkeypatch.setenv("BANG_CHECKED", "0")
     assert _lib.library_path() == _lib.LIB_PATH
+
+
+def test_new_entry_points_validate_before_touching_the_gpu(libpath):
+    L = _lib.lib()
+    assert L.bang_loglike_fp64(None, None, None, 1, None, None) == 1        # BANG_E_INVALID_ARG
+    assert b"null model" in L.bang_last_error()
+    assert L.bang_check_selftest(0, 5, 3) == 4                               # normal build: BANG_E_UNSUPPORTED
+    assert b"checked build" in L.bang_last_error()
