@@ -92,7 +92,7 @@ def synthetic_data(spec: synth.GalaxySpec, truth: np.ndarray, seed: int, n_quad:
 
 
 def run_model(model_name: str, spec, data, err, truth, n_live: int, batch: int, seed: int,
-              free_geometry: bool = False, frac: float = 0.01, n_quad: int = 64, slice_steps=None):
+              free_geometry: bool = False, frac: float = 0.01, n_quad: int = 64, slice_steps=None, speculate: int = 1):
     from .model import Model
     box = selection_box(model_name, truth, free_geometry)
     prior = BoxPrior(box, sin_slot=SLOT["inc"] if free_geometry else None)
@@ -100,7 +100,7 @@ def run_model(model_name: str, spec, data, err, truth, n_live: int, batch: int, 
     try:
         t0 = time.perf_counter()
         res = NestedSampler(gpu_loglike(m), prior, n_live=n_live, batch=batch, seed=seed, frac=frac,
-                            slice_steps=slice_steps).run()
+                            slice_steps=slice_steps, speculate=speculate).run()
         wall = time.perf_counter() - t0
     finally:
         m.close()
@@ -159,13 +159,16 @@ def main(argv=None):
     ap.add_argument("--frac", type=float, default=0.01)
     ap.add_argument("--free-geometry", action="store_true")
     ap.add_argument("--models", default="BD1D2,BD,BD_rot")
+    ap.add_argument("--speculate", type=int, default=1,
+                    help="slice-sampling positions per chain and likelihood call (NestedSampler)")
     a = ap.parse_args(argv)
     spec = synth.GalaxySpec(a.nx, a.ny or a.nx, a.oversample, a.psf_fwhm)
     truth = truth_two_discs()
     data, err, _ = synthetic_data(spec, truth, seed=a.seed)
     out = {}
     for name in a.models.split(","):
-        _, row = run_model(name, spec, data, err, truth, a.n_live, a.batch, a.seed, a.free_geometry, a.frac)
+        _, row = run_model(name, spec, data, err, truth, a.n_live, a.batch, a.seed, a.free_geometry, a.frac,
+                           speculate=a.speculate)
         out[name] = row
         print(json.dumps(row), flush=True)
     if "BD1D2" in out:

@@ -139,11 +139,19 @@ class NestedSampler:
                  ln Z high when K is a large share of N
     frac         stop once L_max X < frac Z (the remaining live points can change Z by less
                  than this fraction)
+    speculate    positions per chain evaluated in one likelihood call during step-out and
+                 shrinking (1: one at a time).  With m > 1 each chain's next m step-out
+                 positions, and its next m shrink candidates drawn as if each earlier one
+                 were rejected, go into one call and the first outcome that ends the search
+                 is taken: the same sequence the one-at-a-time procedure draws, so the
+                 chain's distribution is unchanged; the candidates after it are evaluated
+                 and discarded.  Fewer, larger calls: worth it when a call's latency, not
+                 its rows, sets its cost.
     """
 
     def __init__(self, loglike, prior, n_live: int = 400, batch: int = 40, slice_steps: int | None = None,
                  frac: float = 0.01, seed: int = 0, max_iter: int = 1_000_000,
-                 max_steps_out: int = 16, max_shrink: int = 64):
+                 max_steps_out: int = 16, max_shrink: int = 64, speculate: int = 1):
         if not 1 <= batch < n_live:
             raise ValueError("need 1 <= batch < n_live")
         if prior.ndim < 1:
@@ -153,6 +161,9 @@ class NestedSampler:
         self.slice_steps = slice_steps if slice_steps is not None else max(10, 3 * prior.ndim)
         self.frac, self.max_iter = frac, max_iter
         self.max_steps_out, self.max_shrink = max_steps_out, max_shrink
+        if speculate < 1:
+            raise ValueError("need speculate >= 1")
+        self.speculate = int(speculate)
         self.rng = np.random.Generator(np.random.PCG64(seed))
         self.n_like = 0
         self.it = 0
@@ -191,6 +202,8 @@ class NestedSampler:
 
     # -- replacement chains ------------------------------------------------------------
     def _chains(self, u: np.ndarray, lu: np.ndarray, lstar: float, chol: np.ndarray):
+        if self.speculate > 1:
+            return self._chains_speculative(u, lu, lstar, chol)
         K, D = u.shape
         width = 0.5 * math.sqrt(D + 2.0)
         for _ in range(self.slice_steps):
@@ -228,6 +241,72 @@ class NestedSampler:
                 lo[neg], hi[pos] = t[neg], t[pos]
                 if done.all():
                     break
+        return u, lu
+
+    def _chains_speculative(self, u: np.ndarray, lu: np.ndarray, lstar: float, chol: np.ndarray):
+        """_chains with ``speculate`` positions per chain and call (see the class notes)."""
+        K, D = u.shape
+        m = self.speculate
+        width = 0.5 * math.sqrt(D + 2.0)
+        for _ in range(self.slice_steps):
+            z = self.rng.standard_normal((K, D))
+            z /= np.linalg.norm(z, axis=1, keepdims=True)
+            d = (z @ chol.T) * width
+            r = self.rng.random(K)
+            lo, hi = -r, 1.0 - r
+            # step out: positions lo, lo - 1, ..., lo - (m - 1) (and hi upwards) at once; an
+            # end stops at its first position outside the contour
+            act_lo, act_hi = np.ones(K, bool), np.ones(K, bool)
+            used = 0
+            while used < self.max_steps_out and (act_lo.any() or act_hi.any()):
+                mm = min(m, self.max_steps_out - used)
+                il, ih = np.flatnonzero(act_lo), np.flatnonzero(act_hi)
+                offs = np.arange(mm, dtype=np.float64)
+                pl = lo[il, None] - offs[None, :]
+                ph = hi[ih, None] + offs[None, :]
+                pts = np.concatenate([(u[il, None, :] + pl[..., None] * d[il, None, :]).reshape(-1, D),
+                                      (u[ih, None, :] + ph[..., None] * d[ih, None, :]).reshape(-1, D)])
+                ok, _ = self._above(pts, lstar)
+                okl = ok[:len(il) * mm].reshape(len(il), mm)
+                okh = ok[len(il) * mm:].reshape(len(ih), mm)
+                fl = np.where(okl.all(axis=1), mm, np.argmin(okl, axis=1))
+                fh = np.where(okh.all(axis=1), mm, np.argmin(okh, axis=1))
+                lo[il] -= fl
+                hi[ih] += fh
+                act_lo = np.zeros(K, bool)
+                act_hi = np.zeros(K, bool)
+                act_lo[il[fl == mm]] = True
+                act_hi[ih[fh == mm]] = True
+                used += mm
+            # shrink: the next m candidates of each open chain, each drawn from the interval
+            # the earlier ones would leave if rejected; the first inside the contour is taken
+            done = np.zeros(K, bool)
+            used = 0
+            while used < self.max_shrink and not done.all():
+                mm = min(m, self.max_shrink - used)
+                idx = np.flatnonzero(~done)
+                n = len(idx)
+                lo_c, hi_c = lo[idx].copy(), hi[idx].copy()
+                draws = self.rng.random((n, mm))
+                ts = np.empty((n, mm))
+                for j in range(mm):
+                    t = lo_c + draws[:, j] * (hi_c - lo_c)
+                    ts[:, j] = t
+                    neg = t < 0.0
+                    lo_c = np.where(neg, t, lo_c)
+                    hi_c = np.where(neg, hi_c, t)
+                cand = u[idx, None, :] + ts[..., None] * d[idx, None, :]
+                ok, lp = self._above(cand.reshape(-1, D), lstar)
+                ok, lp = ok.reshape(n, mm), lp.reshape(n, mm)
+                hit = ok.any(axis=1)
+                first = np.argmax(ok, axis=1)
+                acc = idx[hit]
+                u[acc] = cand[hit, first[hit]]
+                lu[acc] = lp[hit, first[hit]]
+                done[acc] = True
+                miss = idx[~hit]
+                lo[miss], hi[miss] = lo_c[~hit], hi_c[~hit]
+                used += mm
         return u, lu
 
     # -- iteration ---------------------------------------------------------------------
@@ -291,8 +370,8 @@ class NestedSampler:
                             samples=self.prior(u), log_weights=lw - logz_f, log_l=ll)
 
     # -- checkpoint / resume -----------------------------------------------------------
-    _STATE = ("n_live", "batch", "slice_steps", "frac", "max_steps_out", "max_shrink", "n_like", "it",
-              "plateau", "logz", "h", "logx", "dead_u", "dead_l", "dead_lw", "u", "lv")
+    _STATE = ("n_live", "batch", "slice_steps", "frac", "max_steps_out", "max_shrink", "speculate", "n_like",
+              "it", "plateau", "logz", "h", "logx", "dead_u", "dead_l", "dead_lw", "u", "lv")
 
     def state_dict(self) -> dict:
         s = {k: getattr(self, k) for k in self._STATE}
@@ -301,7 +380,7 @@ class NestedSampler:
 
     def load_state_dict(self, s: dict):
         for k in self._STATE:
-            setattr(self, k, s[k])
+            setattr(self, k, s.get(k, 1) if k == "speculate" else s[k])   # older states: one at a time
         self.ndim = self.u.shape[1]
         self.rng.bit_generator.state = s["rng"]
 

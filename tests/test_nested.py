@@ -180,3 +180,73 @@ def test_model_selection_boxes():
     assert BoxPrior(b2).ndim == 11 and BoxPrior(b1).ndim == 7
     g = fit.selection_box("BD1D2", t, free_geometry=True)
     assert BoxPrior(g).ndim == 13 and g[S["inc"], 0] == pytest.approx(30 * synth.DEG)
+
+
+def test_speculative_slice_step_has_the_same_distribution():
+    """One hit-and-run slice step from the same start, one position per call against four:
+    the new points follow the same distribution (two-sample KS on the radius and the
+    angle), all inside the contour."""
+    from scipy.stats import ks_2samp
+    D = 2
+
+    def ll(th):
+        return -np.sum((th - 0.5) ** 2, axis=1)
+    lstar = -0.2 ** 2
+    start = np.tile([0.55, 0.48], (20000, 1))
+    out = {}
+    for m in (1, 4):
+        s = NestedSampler(ll, _cube(D), n_live=10, batch=5, seed=11 + m, slice_steps=1, speculate=m)
+        u, lu = s._chains(start.copy(), ll(start), lstar, np.eye(D) * 0.15)
+        assert np.all(lu > lstar) and np.allclose(lu, ll(u))
+        out[m] = u
+    rad = {m: np.hypot(out[m][:, 0] - 0.5, out[m][:, 1] - 0.5) for m in out}
+    ang = {m: np.arctan2(out[m][:, 1] - 0.5, out[m][:, 0] - 0.5) for m in out}
+    assert ks_2samp(rad[1], rad[4]).pvalue > 1e-3
+    assert ks_2samp(ang[1], ang[4]).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("speculate", [3, 8])
+def test_speculative_chains_keep_the_evidence_with_fewer_calls(speculate):
+    D, s = 4, 0.04
+    exact = _gauss_logz(D, s)
+    calls = {1: 0, speculate: 0}
+    zs = []
+    for m in (1, speculate):
+        for seed in range(3):
+            base = _gauss(np.full(D, 0.5), s)
+
+            def ll(th, m=m):
+                calls[m] += 1
+                return base(th)
+            r = NestedSampler(ll, _cube(D), n_live=200, batch=20, seed=seed, speculate=m).run()
+            if m == speculate:
+                z = (r.logz - exact) / r.logz_err
+                zs.append(z)
+                assert abs(z) < 3.5, (seed, r.logz, exact, r.logz_err)
+                mu, c = r.mean_cov()
+                assert np.all(np.abs(mu - 0.5) < 0.25 * s)
+                assert np.all(np.abs(np.sqrt(np.diag(c)) / s - 1.0) < 0.15)
+    assert abs(np.mean(zs)) < 2.0
+    assert calls[speculate] < 0.6 * calls[1]
+
+
+def test_speculative_two_modes_and_checkpoint(tmp_path):
+    D, s = 3, 0.03
+    a, b = _gauss(np.full(D, 0.3), s), _gauss(np.full(D, 0.7), s, math.log(0.5))
+
+    def ll(th):
+        return np.logaddexp(a(th), b(th))
+    exact = math.log(1.5) + D * math.log(s * math.sqrt(2 * math.pi))
+    r = NestedSampler(ll, _cube(D), n_live=300, batch=30, seed=0, speculate=4).run()
+    assert abs(r.logz - exact) < 3.5 * r.logz_err
+    w = np.exp(r.log_weights)
+    assert abs(w[r.samples[:, 0] > 0.5].sum() - 1.0 / 3.0) < 0.15
+    # the setting travels with a checkpoint; resuming is bit for bit
+    full = NestedSampler(ll, _cube(D), n_live=60, batch=6, seed=2, speculate=4).run()
+    path = str(tmp_path / "spec.pkl")
+    part = NestedSampler(ll, _cube(D), n_live=60, batch=6, seed=2, speculate=4)
+    part.run(checkpoint=path, every=4, max_iter=8)
+    resumed = NestedSampler.resume(path, ll, _cube(D)).run()
+    assert resumed.logz == full.logz and np.array_equal(resumed.samples, full.samples)
+    with pytest.raises(ValueError):
+        NestedSampler(ll, _cube(D), n_live=60, batch=6, speculate=0)
