@@ -250,3 +250,27 @@ def test_speculative_two_modes_and_checkpoint(tmp_path):
     assert resumed.logz == full.logz and np.array_equal(resumed.samples, full.samples)
     with pytest.raises(ValueError):
         NestedSampler(ll, _cube(D), n_live=60, batch=6, speculate=0)
+
+
+def test_speculative_limits_and_edges():
+    """Search limits that m does not divide (max_steps_out 3, max_shrink 5 with m = 4), a
+    slice so thin that shrinking runs out (the chain keeps its point), and chains at the
+    cube's edge: every returned point is inside the contour and its logL is its own."""
+    D = 3
+
+    def ll(th):
+        return -np.sum(((th - 0.02) / 0.3) ** 2, axis=1)   # mode near a corner of the cube
+    for m, steps_out, shrink in ((4, 3, 5), (3, 16, 64), (8, 1, 1)):
+        s = NestedSampler(ll, _cube(D), n_live=20, batch=5, seed=m, slice_steps=3, speculate=m,
+                          max_steps_out=steps_out, max_shrink=shrink)
+        start = np.vstack([np.full(D, 0.02), np.full(D, 0.001), np.array([0.3, 0.02, 0.5])])
+        lstar = float(ll(start).min()) - 0.5
+        u, lu = s._chains(start.copy(), ll(start), lstar, np.eye(D) * 0.2)
+        assert np.all((u >= 0.0) & (u <= 1.0))
+        assert np.all(lu > lstar) and np.allclose(lu, ll(u))
+    # a thin slice: the contour sits just below the start's logL, shrinking is cut off
+    s = NestedSampler(ll, _cube(D), n_live=20, batch=5, seed=1, slice_steps=1, speculate=4, max_shrink=2)
+    start = np.full((4, D), 0.02)
+    lstar = float(ll(start[:1])[0]) - 1e-12
+    u, lu = s._chains(start.copy(), ll(start), lstar, np.eye(D) * 0.5)
+    assert np.all(lu > lstar)
