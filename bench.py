@@ -116,20 +116,40 @@ def dist_env():
     return ws, rank, local
 
 
+def smi_device_id(cuda_ordinal: int) -> str:
+    """The identifier nvidia-smi needs for CUDA device `cuda_ordinal`: its PCI address
+    (nvidia-smi numbers GPUs in PCI order, which is not the CUDA ordinal once
+    CUDA_VISIBLE_DEVICES remaps them), else its UUID, else the ordinal itself."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(cuda_ordinal)
+    except Exception:   # no torch or no device: the ordinal is all there is
+        return str(cuda_ordinal)
+    dom, bus, dev = (getattr(p, k, None) for k in ("pci_domain_id", "pci_bus_id", "pci_device_id"))
+    if isinstance(dom, int) and isinstance(bus, int) and isinstance(dev, int):
+        return f"{dom:08X}:{bus:02X}:{dev:02X}.0"
+    uuid = getattr(p, "uuid", None)
+    if uuid:
+        u = str(uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    return str(cuda_ordinal)
+
+
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region, on the
+    GPU that CUDA device `cuda_ordinal` is."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, cuda_ordinal: int):
+        self.smi_id = smi_device_id(cuda_ordinal)
         self.proc = None
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.smi_id}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
@@ -150,7 +170,7 @@ class Clocks:
                 if "Active" in r[5 + k] and "Not" not in r[5 + k]:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "gpu": self.smi_id}
 
 
 def measured_peaks():
@@ -167,26 +187,58 @@ def points_per_eval(spec: synth.GalaxySpec) -> int:
     return (spec.oversample * spec.nx + 2 * h) * (spec.oversample * spec.ny + 2 * h)
 
 
-def algorithmic_sfu_ops(wl: synth.Workload, gal_idx=None, rows: int | None = None) -> float:
-    """Transcendental (SFU) operations of one batch: per padded fine point, one log2 and one
-    exp2 per radial quadrature node (q^(g-4) by lg2 + ex2; q^(2g-7) = (q^(g-4))^2 q by
-    multiplications), plus 16 for the rest of the point (two square roots of the radii, one
-    of the velocity, the bulge, halo and disc powers, logarithms and exponentials, and the
-    reciprocals of the light weighting)."""
+# SFU (MUFU) operations per padded fine point, by issue class: "half" are the functions the
+# SFU issues at 16 per clock per SM (lg2, rcp, rsqrt, sqrt), "full" is ex2 (32 per clock).
+#  forward (eval_point): per radial node one lg2 and one ex2 (q^(g-4); q^(2g-7) = (q^(g-4))^2 q
+#    by multiplications); per point 13 + (n_discs - 1) / 2 half-rate (the bulge's 1/(x+1) and
+#    log2 w, sqrt R, rsqrt r2, the bulge velocity's 1/(x+1) and log2 u, the NFW m(x) (two
+#    reciprocals, or a log and a reciprocal), a disc fit's log for y <= 1 (half the points),
+#    sqrt v, 1/B, sqrt sigma^2, 1/Sigma) and 3 + n_discs ex2 (the bulge's two per-point powers,
+#    the bulge velocity power, each disc's exponential);
+#  adjoint (point_vjp): per radial node one lg2 and two ex2 (q^(g-4) and u/w); per point the
+#    forward recomputation's operations plus 1/(3-g), 1/R (twice), 1/(1+x) of the halo
+#    derivative, the two divisions of the reverse sweep: 18 + (n_discs - 1) / 2 half-rate and
+#    3 + n_discs ex2.
+def sfu_ops_per_point(n_quad: int, n_discs: int, adjoint: bool = False) -> dict:
+    if adjoint:
+        return {"half": n_quad + 18.0 + 0.5 * (n_discs - 1), "full": 2.0 * n_quad + 3.0 + n_discs}
+    return {"half": n_quad + 13.0 + 0.5 * (n_discs - 1), "full": n_quad + 3.0 + n_discs}
+
+
+def _batch_points(wl: synth.Workload, gal_idx=None, rows: int | None = None) -> float:
     if rows is None:
-        pts = sum(points_per_eval(g) for g in wl.galaxies) * wl.rows_per_galaxy
-    else:
-        per = [points_per_eval(g) for g in wl.galaxies]
-        pts = sum(per[0 if gal_idx is None else int(gal_idx[b])] for b in range(rows))
-    return float(pts) * (2 * wl.n_quad + 16)
+        return float(sum(points_per_eval(g) for g in wl.galaxies) * wl.rows_per_galaxy)
+    per = [points_per_eval(g) for g in wl.galaxies]
+    return float(sum(per[0 if gal_idx is None else int(gal_idx[b])] for b in range(rows)))
 
 
-def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = None) -> float:
+def sfu_work(wl: synth.Workload, gal_idx=None, rows: int | None = None, grad: bool = False):
+    """Algorithmic SFU work of one batch: (operations, SM-cycles at the measured per-SM issue
+    rates).  A logL step is the forward pass over every padded fine point; a logL + gradient
+    step is the forward seed pass plus the adjoint pass over the same points."""
+    pts = _batch_points(wl, gal_idx, rows)
+    ops = cyc = 0.0
+    for adj in ((False, True) if grad else (False,)):
+        c = sfu_ops_per_point(wl.n_quad, wl.n_discs, adj)
+        ops += pts * (c["half"] + c["full"])
+        cyc += pts * (c["half"] / MUFU_LG2_PER_CLK_SM + c["full"] / MUFU_EX2_PER_CLK_SM)
+    return ops, cyc
+
+
+def algorithmic_sfu_ops(wl: synth.Workload, gal_idx=None, rows: int | None = None, grad: bool = False) -> float:
+    """Transcendental (SFU) operations of one batch (see sfu_ops_per_point)."""
+    return sfu_work(wl, gal_idx, rows, grad)[0]
+
+
+def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = None, grad: bool = False) -> float:
     """FP32 instructions of one batch: per padded fine point 6 per radial node (the argument
     of the logarithm, the exponent, and the two weighted sums with the (q^(g-4))^2 q
     product) plus ~200 for geometry, velocities, discs and light weighting; per galaxy the
     PSF stencil (separable: 4 channels x (fine rows x nx + nx x ny) x (os + 2h); two-
-    dimensional: 4 x nx x ny x (os + 2h)^2) and ~40 per spaxel for the chi-square."""
+    dimensional: 4 x nx x ny x (os + 2h)^2) and ~40 per spaxel for the chi-square.  A
+    gradient step adds the adjoint pass: per point 13 per radial node (the six sums) and ~400
+    for the forward recomputation and the reverse sweep, and the transposed stencil (the
+    forward's count)."""
     def per_row(spec):
         sig = spec.psf_fwhm_arcsec / (2.0 * math.sqrt(2.0 * math.log(2.0)))
         h = int(math.floor(3.0 * sig / (spec.spaxel_arcsec / spec.oversample))) if spec.psf_fwhm_arcsec > 0 else 0
@@ -195,7 +247,10 @@ def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = No
             psf = 4.0 * spec.nx * spec.ny * L * L
         else:
             psf = 4.0 * ((spec.oversample * spec.ny + 2 * h) * spec.nx + spec.nx * spec.ny) * L
-        return points_per_eval(spec) * (6.0 * wl.n_quad + 200.0) + psf + 40.0 * spec.nx * spec.ny
+        fwd = points_per_eval(spec) * (6.0 * wl.n_quad + 200.0) + psf + 40.0 * spec.nx * spec.ny
+        if grad:
+            fwd += points_per_eval(spec) * (13.0 * wl.n_quad + 400.0) + psf
+        return fwd
     per = [per_row(g) for g in wl.galaxies]
     if rows is None:
         return float(sum(per) * wl.rows_per_galaxy)
@@ -218,10 +273,26 @@ def rank_batch_seed(workload_id: int, rank: int) -> int:
     return synth.batch_seed(workload_id) + 1000 * rank
 
 
-def sfu_peak_ops_per_s(n_quad: int, mhz: float, sms: int) -> float:
-    """Peak transcendental rate for the radial-rule mix (one lg2 per ex2)."""
-    per_op_clk = (1.0 / MUFU_LG2_PER_CLK_SM + 1.0 / MUFU_EX2_PER_CLK_SM) / 2.0   # SM-clocks per op
-    return sms * mhz * 1e6 / per_op_clk
+def roofline_block(wl: synth.Workload, step_s: float, gal_idx=None, rows: int | None = None, grad: bool = False,
+                   mhz: float = SM_MAX_MHZ_NOMINAL, sms: int = SM_COUNT_NOMINAL) -> dict:
+    """The SFU roofline of one timed step: achieved = algorithmic SFU operations / step time;
+    peak = the same operations over the time the SFU needs for them at the measured per-SM
+    issue rates of their classes (sms x clock); frac = that time / the measured time.  The FP32
+    count against the measured FFMA rate is reported beside it."""
+    ops, cyc = sfu_work(wl, gal_idx, rows, grad)
+    t_sfu = cyc / (sms * mhz * 1e6)
+    fp32 = algorithmic_fp32_ops(wl, gal_idx, rows, grad)
+    fp32_peak = sms * mhz * 1e6 * FP32_PER_CLK_SM
+    t_fp32 = fp32 / fp32_peak
+    return {"bound": "alu", "achieved": ops / step_s / 1e9, "peak": ops / t_sfu / 1e9, "unit": "G SFU op/s",
+            "frac": t_sfu / step_s,
+            "fp32": {"achieved": fp32 / step_s / 1e9, "peak": fp32_peak / 1e9, "unit": "G FP32 lane-op/s",
+                     "frac": t_fp32 / step_s},
+            "t_roof_over_t_meas": max(t_sfu, t_fp32) / step_s,
+            "sfu_sm_cycles_per_point": cyc / _batch_points(wl, gal_idx, rows),
+            "peak_basis": f"{sms} SMs x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz) x measured per-SM issue rates: "
+                          f"lg2/rcp/rsqrt/sqrt {MUFU_LG2_PER_CLK_SM:.0f}/clk, ex2 {MUFU_EX2_PER_CLK_SM:.0f}/clk, "
+                          f"FFMA {FP32_PER_CLK_SM:.0f} lanes/clk, for the step's own operation mix"}
 
 
 # ----------------------------------------------------------------------------- data
@@ -360,34 +431,90 @@ def time_table(wl, torch, T=1024, steps=20):
                     "4-point Lagrange interpolation in log R"}
 
 
-def time_adjoint(torch, steps=10):
-    """logL + gradient for the 256-row adjoint workload (80x80, os 5), device-timed."""
-    wl = synth.workload("adjoint")
-    model, _, theta_np, _ = make_model(wl, 0, torch)
-    model.tune(theta_np.shape[0])
+def _event_time(torch, fn, steps, flush=None):
+    """Mean device time (ms) of fn() over `steps` calls, each bracketed by CUDA events on the
+    current stream, the L2 flushed between calls outside the events."""
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(k & 0xff)
+        starts[k].record(stream)
+        fn()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+
+
+def time_workload(name, torch, grad=False, rows=None, steps=5, warmup=2, mhz=SM_MAX_MHZ_NOMINAL,
+                  sms=SM_COUNT_NOMINAL, flush=None, forward_too=False):
+    """One workload (or its first `rows` rows) in one launch after the autotuner has chosen
+    its shape: device-timed logL (or logL + gradient) evaluations per second and the SFU
+    roofline of the timed step."""
+    wl = synth.workload(name)
+    model, _, theta_np, gal_idx = make_model(wl, 0, torch)
+    if rows:
+        theta_np = np.ascontiguousarray(theta_np[:rows])
+        gal_idx = None if gal_idx is None else np.ascontiguousarray(gal_idx[:rows])
+    B = theta_np.shape[0]
+    model.tune(B, gal_idx)
     theta = torch.from_numpy(theta_np).cuda()
-    for _ in range(2):
-        model.loglike_grad(theta)
+    out = torch.empty(B, dtype=torch.float64, device="cuda")
+    if grad:
+        def call():
+            model.loglike_grad(theta, gal_idx)
+    else:
+        def call():
+            model.loglike(theta, gal_idx, out=out)
+    for _ in range(warmup):
+        call()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        model.loglike_grad(theta)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    fwd0, fwd1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = torch.empty(theta.shape[0], dtype=torch.float64, device="cuda")
-    fwd0.record()
-    for _ in range(steps):
-        model.loglike(theta, out=out)
-    fwd1.record()
-    torch.cuda.synchronize()
-    fms = fwd0.elapsed_time(fwd1) / steps
+    ms = _event_time(torch, call, steps, flush)
+    metric = "logL+gradient evals/s" if grad else "logL evals/s"
+    res = {"value": B / ms * 1e3, "unit": metric, "ms_per_step": ms, "rows": B, "steps": steps,
+           "workload": f"{wl.name}: {wl.description}",
+           "roofline": roofline_block(wl, ms / 1e3, gal_idx, B, grad, mhz, sms)}
+    if forward_too:
+        fms = _event_time(torch, lambda: model.loglike(theta, gal_idx, out=out), steps, flush)
+        res["forward_only_ms"] = fms
+        res["grad_over_forward"] = ms / fms
     model.close()
-    return {"value": wl.batch / ms * 1e3, "unit": "fwd+adjoint evals/s", "ms_per_batch": ms,
-            "rows": wl.batch, "forward_only_ms": fms, "adjoint_over_forward": ms / fms,
-            "workload": f"adjoint: {wl.description}"}
+    return res
+
+
+def time_single(torch, steps=50):
+    """The single-row workload (30x30, os 3, gamma = 1, one row): latency of one evaluation
+    by the fused launch, by the paper's one-kernel-per-task chain (float32), and by the
+    float64 check path (every step in float64), with the relative logL differences."""
+    import time as _t
+    wl = synth.workload("single")
+    model, _, theta_np, _ = make_model(wl, 0, torch)
+    theta = torch.from_numpy(theta_np).cuda()
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        model.loglike(theta, out=out)
+        model.loglike_plain(theta)
+    torch.cuda.synchronize()
+    fused = _event_time(torch, lambda: model.loglike(theta, out=out), steps)
+    plain = _event_time(torch, lambda: model.loglike_plain(theta), steps)
+    th64 = torch.from_numpy(theta_np.astype(np.float64))
+    l64 = model.loglike_fp64(th64)          # synchronous: timed by the host clock
+    t0 = _t.perf_counter()
+    n = 5
+    for _ in range(n):
+        l64 = model.loglike_fp64(th64)
+    fp64_ms = (_t.perf_counter() - t0) / n * 1e3
+    l32 = float(model.loglike(theta).cpu()[0])
+    lp = float(model.loglike_plain(theta).cpu()[0])
+    model.close()
+    return {"workload": f"single: {wl.description}", "unit": "ms per evaluation",
+            "fused_f32_ms": fused, "plain_f32_ms": plain, "fp64_check_path_ms": fp64_ms,
+            "fused_evals_s": 1e3 / fused, "plain_evals_s": 1e3 / plain, "fp64_evals_s": 1e3 / fp64_ms,
+            "rel_logL_fused_vs_fp64": abs(l32 - float(l64[0])) / abs(float(l64[0])),
+            "rel_logL_plain_vs_fused": abs(lp - l32) / abs(l32),
+            "note": "one row cannot fill the GPU: latency, not throughput; the float64 path is "
+                    "synchronous and timed by the host clock"}
 
 
 # ----------------------------------------------------------------------------- arms
@@ -527,16 +654,11 @@ def run_ours(args):
     sms = props.multi_processor_count
     mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL))
     step_s = dev_s / args.steps
-    ops = algorithmic_sfu_ops(wl, gal_idx, B)
-    achieved = ops / step_s / 1e9
-    peak = sfu_peak_ops_per_s(wl.n_quad, mhz, sms) / 1e9
-    fp32_ops = algorithmic_fp32_ops(wl, gal_idx, B)
-    fp32_peak = sms * mhz * 1e6 * FP32_PER_CLK_SM / 1e9
-    fp32_achieved = fp32_ops / step_s / 1e9
-    # t_roof = max over the two pipes of algorithmic work / peak, against the measured time
-    t_roof = max(ops / (peak * 1e9), fp32_ops / (fp32_peak * 1e9))
     pipes = NCU_PIPES if NCU_PIPES["stamp"] == kernel_stamp() else None
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["stamp"] == kernel_stamp() else None
+    roof = roofline_block(wl, step_s, gal_idx, B, args.grad, mhz, sms)
+    roof["traffic"] = None if args.grad else traffic
+    roof["ncu_pipes"] = None if args.grad else pipes
 
     metric = "logL+gradient evals/s" if args.grad else "logL evals/s"
     line = {
@@ -554,15 +676,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": metric, "h2d_bytes_per_step": int(B * P * 4),
                 "d2h_bytes_per_step": int(B * 8 + (B * P * 4 if args.grad else 0))},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G SFU op/s", "frac": achieved / peak,
-                     "traffic": traffic,
-                     "fp32": {"achieved": fp32_achieved, "peak": fp32_peak, "unit": "G FP32 lane-op/s",
-                              "frac": fp32_achieved / fp32_peak},
-                     "t_roof_over_t_meas": t_roof / step_s,
-                     "ncu_pipes": pipes,
-                     "peak_basis": f"{sms} SMs x {mhz:.0f} MHz (MEASURED_PEAKS sm_max_mhz) x measured per-SM rates "
-                                   f"lg2 {MUFU_LG2_PER_CLK_SM:.0f}/clk, ex2 {MUFU_EX2_PER_CLK_SM:.0f}/clk for the "
-                                   "radial-rule mix (1 lg2 : 1 ex2)"},
+        "roofline": roof,
         "clocks": clk,
         "wall_s_timed": wall,
         "device": {"name": props.name, "sms": sms, "host_cores": os.cpu_count(), "torch": torch.__version__,
@@ -571,11 +685,20 @@ def run_ours(args):
     if not headline:
         line["note"] = ("profiling or variant case (--rows / --grad / --bulge-table / --bulge-kind / --psf-mode), "
                         "not the headline configuration")
-        if args.grad or args.bulge_table or args.bulge_kind or args.psf_mode:
-            line["roofline"] = None        # the SFU count above is the forward per-point quadrature's
+        if args.bulge_table or args.bulge_kind or args.psf_mode:
+            line["roofline"] = None        # the SFU counts are the per-point quadrature's
     if ws == 1 and headline and not args.no_extras and len(wl.galaxies) == 1:
         line["plain_gpu"] = time_plain(model, theta, logL, B)
-        line["fwd_adjoint"] = time_adjoint(torch)
+        model.close()
+        side = dict(torch=torch, mhz=mhz, sms=sms, flush=flush)
+        # the other workloads, each in one tuned launch: logL + gradient (256 rows), the
+        # uneven batch (64 galaxies x 64 rows), the largest (4096 rows; its gradient on the
+        # first 1024), and the single row's latency in three forms
+        line["fwd_adjoint"] = time_workload("adjoint", grad=True, steps=10, forward_too=True, **side)
+        line["uneven"] = time_workload("uneven", steps=5, **side)
+        line["largest"] = time_workload("largest", steps=3, **side)
+        line["largest_grad"] = time_workload("largest", grad=True, rows=1024, steps=3, **side)
+        line["single"] = time_single(torch)
         line["radial_table"] = time_table(wl, torch)
         line["cpu_baseline"] = cpu_oracle_sample(wl, gal, theta_np, args.cpu_seconds, logL.cpu().numpy())
     elif ws == 1:

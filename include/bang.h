@@ -139,31 +139,48 @@ int bang_model_ngalaxies(const bang_model *m);
 /* PSF window half-width h (fine pixels) of galaxy g, or -1 if g is out of range. */
 int bang_model_psf_halfwidth(const bang_model *m, int g);
 
-/* logL[b] (float64) of row b of theta ([B][P] float32) against galaxy gal_idx[b].
- * gal_idx: HOST array [B] of int32 in [0, n_gal), or NULL for galaxy 0 for every row (the
- * host needs the galaxy of each row to schedule the launch).  One persistent launch handles
- * all rows, whatever their grid sizes (Sec. 2.5, App. A). */
+/* logL[b] (float64) of row b of theta ([B][P] float32) against galaxy gal_idx[b] (Eq. 18 on
+ * the model of Sec. 2.1-2.4).  One persistent launch handles all rows, whatever their grid
+ * sizes (Sec. 2.5, App. A).  gal_idx: int32 [B] in [0, n_gal), or NULL for galaxy 0 for every
+ * row, in either memory:
+ *  - a HOST array: the host reads it to build the launch's work items (cached per distinct
+ *    gal_idx contents and B); an index out of range returns BANG_E_INVALID_ARG;
+ *  - a DEVICE array of the model's device: nothing is read on the host and the call stays
+ *    asynchronous (no host synchronisation once the batch size has been seen).  The kernels
+ *    derive each row's work from its galaxy; the launch is sized for every galaxy of the
+ *    model (shared memory, bands for the tallest grid), and the model's galaxies must share
+ *    one PSF kind (Gaussian, or two-dimensional taps), else BANG_E_UNSUPPORTED.  A row whose
+ *    index is out of range gets logL = NaN (and a zero gradient); the other rows are
+ *    unaffected.  Results equal the host-array path's bit for bit.
+ * Device memory of another device gives BANG_E_INVALID_ARG. */
 bang_status bang_loglike_batch(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
                                double *logL, void *stream);
 
-/* As bang_loglike_batch, plus grad[b][p] = d logL[b] / d theta[b][p] (float32, [B][P]),
- * by a hand-written adjoint that re-evaluates the radial quadrature instead of storing it. */
+/* As bang_loglike_batch (gal_idx host or device memory as described there), plus
+ * grad[b][p] = d logL[b] / d theta[b][p] (float32, [B][P]): the gradient of Eq. 18's
+ * log-likelihood through the discrete model of Sec. 2.1-2.4 and the PSF and binning of
+ * Eq. 21, by a hand-written adjoint that re-evaluates the radial quadrature instead of
+ * storing it.  (The paper samples without gradients; this serves gradient-based samplers
+ * and optimisers the same likelihood.) */
 bang_status bang_loglike_grad_batch(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
                                     double *logL, float *grad, void *stream);
 
 /* Model maps for every row: maps[b] is [4][ny][nx] float32 of galaxy gal_idx[b] (B, v_los +
  * v_sys, sigma_los, M/L = 1/<L/M>); rows are packed back to back, each with its own galaxy's
- * size.  Out-of-domain rows get NaN maps. */
+ * size.  Out-of-domain rows get NaN maps.  gal_idx must be host memory (the packing depends
+ * on it; a device array gives BANG_E_UNSUPPORTED). */
 bang_status bang_model_maps(bang_model *m, const float *theta, const int32_t *gal_idx, int B, float *maps,
                             void *stream);
 
-/* Total floats bang_model_maps writes for this gal_idx (HOST, may be NULL) and B. */
+/* Total floats bang_model_maps writes for this gal_idx (host memory, may be NULL) and B;
+ * -1 for a NULL model, an index out of range or a device gal_idx. */
 int64_t bang_model_maps_size(const bang_model *m, const int32_t *gal_idx, int B);
 
 /* The paper's execution form (Alg. 2 of App. A): for each row, a serial chain of one kernel
  * per task (coordinates, bulge, circular velocities, discs, combination, PSF + binning,
  * chi-square), 64 threads per block, intermediate arrays in device memory.  Same model and
- * arithmetic as bang_loglike_batch; used as the comparison baseline. */
+ * arithmetic as bang_loglike_batch; used as the comparison baseline.  A device gal_idx is
+ * copied to the host first (this entry point schedules row by row on the host). */
 bang_status bang_loglike_plain(bang_model *m, const float *theta, const int32_t *gal_idx, int B,
                                double *logL, void *stream);
 
@@ -198,7 +215,10 @@ bang_status bang_loglike_grids(bang_model *m, const float *theta, int B, const i
  * theta [B][P] float32 and logL [B] float64 must be device memory of the model's device
  * (host pointers give BANG_E_INVALID_ARG; there is no staging).  gal_idx is a HOST array
  * [B] of galaxy indices or NULL (galaxy 0 for every row); it is copied on `stream`, so a
- * pinned gal_idx must stay unchanged until the stream has passed this call.  B is at most
+ * pinned gal_idx must stay unchanged until the stream has passed this call.  Under stream
+ * capture that copy becomes a node of the graph: gal_idx must then be pinned, and every
+ * replay reads the array again at the time it runs (its contents are validated only when
+ * the call is made).  B is at most
  * 32768 (the size the scratch was built for); a larger B returns BANG_E_INVALID_ARG and
  * launches nothing.  Each row is one work item (no bands), so logL equals
  * bang_loglike_batch's result up to the order of float64 additions.
@@ -217,17 +237,20 @@ bang_status bang_loglike_batch_noalloc(bang_model *m, const float *theta, const 
  * on the same discretisation as bang_loglike_batch: padded fine grid, the fixed radial
  * rule in float64 (n_quad nodes, t in [0, 16]), the float64 PSF (x) box taps, 1/delta^2 in
  * float64, the data maps as given.  The disc velocity uses the modified Bessel functions
- * themselves (valid for r / (2 R_d) < ~700).  For comparisons with a float64 reference,
+ * themselves up to r / (2 R_d) = 25 and their products' large-argument expansion beyond.  For comparisons with a float64 reference,
  * not for speed.  theta [B][P] float64 and logL [B] float64 may each be host or device
- * memory; gal_idx is a host array [B] or NULL.  Rows outside the parameter domain give
+ * memory; gal_idx is an array [B] (host memory, or device memory copied to the host) or
+ * NULL.  Rows outside the parameter domain give
  * -inf.  Supported: bulge_kind 0 (radial rule; bulge_table is ignored), psf_mode without
  * BANG_PSF_FLUX; otherwise BANG_E_UNSUPPORTED.  Synchronous on `stream`. */
 bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t *gal_idx, int B, double *logL,
                               void *stream);
 
-/* Chooses launch parameters (rows of the fine grid per block step, blocks per SM) for
- * batches like (gal_idx, B) by timing candidates on the device; the choice is cached in the
- * model.  gal_idx as in bang_loglike_batch.  Synchronous. */
+/* Chooses launch parameters (fine rows per block step, spaxel-row bands per row) for
+ * batches of B rows by timing candidates on the device; the choice is cached in the model.
+ * With a host gal_idx (or NULL: galaxy 0 for every row) it applies to later calls with that
+ * same gal_idx and B; with a device gal_idx (read here, this call being synchronous) it
+ * applies to every later call of B rows with a device gal_idx. */
 bang_status bang_model_tune(bang_model *m, const int32_t *gal_idx, int B);
 
 /* Message of the last failed call on this thread ("" if none). */

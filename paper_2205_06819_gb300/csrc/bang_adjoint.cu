@@ -412,7 +412,17 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
       BANG_NEXT_ITEM(it);
       continue;
     }
-    const WorkItem w = a.items[item_id];
+    WorkItem w;
+    if (a.items) {
+      w = a.items[item_id];
+    } else {   // implicit item: fine rows [k rows, (k + 1) rows) of row b, the row's galaxy read on the device
+      const int b = item_id / a.nb, k = item_id - b * a.nb;
+      const int g = a.gal_idx ? __ldg(a.gal_idx + b) : 0;
+      const bool bad = (unsigned)g >= (unsigned)a.n_gal;   // decode marked the row invalid
+      const int H = bad ? 0 : __ldg(&a.gals[g].H);
+      const int y0 = k * a.rows_per_item;
+      w = WorkItem{b, bad ? 0 : g, y0, min(H, y0 + a.rows_per_item)};
+    }
     if (!BANG_IN(w.b, a.B, kSiteAdjRow) || !BANG_IN(w.g, a.n_gal, kSiteAdjGal)) {
       BANG_NEXT_ITEM(it);
       continue;
@@ -422,12 +432,18 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
       mc = a.consts[w.b];
     }
     __syncthreads();
-    if (!mc.valid) {
+    if (!mc.valid) {   // outside the domain or without a galaxy: grad_out_kernel does not read the row's items
+      BANG_NEXT_ITEM(it);
+      continue;
+    }
+    if (w.j1 <= w.j0) {   // an empty band past the last fine row of a smaller galaxy: zero adjoints
+      if (tid < kAdjSlots) a.acc_partial[(size_t)item_id * kAdjSlots + tid] = 0.0;
       BANG_NEXT_ITEM(it);
       continue;
     }
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx, ny = gs.ny, n = nx * ny;
-    const float* seed = a.seed + a.out_off[w.b];
+    const int64_t soff = a.out_off ? a.out_off[w.b] : (int64_t)w.b * a.out_stride;
+    const float* seed = a.seed + soff;
     // separable taps stored twice, (t, t): a 64-bit load gives the pair the packed
     // two-lane FMAs need; the L x L two-dimensional taps once (shared memory)
     float2* taps = reinterpret_cast<float2*>(smem_raw);
@@ -443,7 +459,7 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
                       : reinterpret_cast<const unsigned char*>(V + (PSF == 0 ? (size_t)a.G * nx : 0))) - smem_raw - 1,
                  dynamic_smem_bytes(), kSiteAdjSmem) ||
         !BANG_IN(w.j0, w.j1, kSiteAdjItem) || !BANG_IN(w.j1 - 1, gs.H, kSiteAdjItem) ||
-        !BANG_IN(a.out_off[w.b] + 4ll * n - 1, a.seed_total, kSiteAdjSeed) ||
+        !BANG_IN(soff + 4ll * n - 1, a.seed_total, kSiteAdjSeed) ||
         (tab && !BANG_IN((long long)w.b * a.table_stride + kTabHdr + 8 * a.table_T - 1,
                          (long long)a.B * a.table_stride, kSiteAdjTable))) {
       BANG_NEXT_ITEM(it);
@@ -560,25 +576,33 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
 // then mapped to d logL / d theta (float64), or zero for a row outside the parameter
 // domain.  As in decode_kernel, lane i < kDecodeTerms also evaluates decode term i and
 // lane 0 does the rest.  No atomics: the gradient is the same bits on every call.
+// adj_row_first / row_first NULL: row b's items are [b adj_nb, (b + 1) adj_nb) and
+// [b nb, (b + 1) nb); gal_idx (may be NULL): a row whose galaxy index is outside [0, n_gal)
+// gets a zero gradient.
 __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind, int bulge_kind,
                                 const double* __restrict__ acc_partial, const int* __restrict__ adj_row_first,
                                 const double* __restrict__ vsys_partial, const int* __restrict__ row_first, int B,
-                                int n_items, int adj_items, double l10k, float* __restrict__ grad) {
+                                int n_items, int adj_items, int adj_nb, int nb, const int* __restrict__ gal_idx,
+                                int n_gal, double l10k, float* __restrict__ grad) {
   const int b = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (b >= B) return;   // whole warps
   const float* th = theta + (size_t)b * P;
-  const bool ok = theta_in_domain(th, nd, halo_kind, bulge_kind);
+  const bool ok = theta_in_domain(th, nd, halo_kind, bulge_kind) &&
+                  (!gal_idx || (unsigned)gal_idx[b] < (unsigned)n_gal);
   const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
   double T[kDecodeTerms];
 #pragma unroll
   for (int i = 0; i < kDecodeTerms; ++i) T[i] = __shfl_sync(0xffffffffu, v, i);
   double sum = 0.0;
   if (ok && lane < kAdjSlots) {
-    for (int i = adj_row_first[b]; i < adj_row_first[b + 1]; ++i)
+    const int i0 = adj_row_first ? adj_row_first[b] : b * adj_nb;
+    const int i1 = adj_row_first ? adj_row_first[b + 1] : (b + 1) * adj_nb;
+    for (int i = i0; i < i1; ++i)
       if (BANG_IN(i, adj_items, kSiteFinalizeItem)) sum += acc_partial[(size_t)i * kAdjSlots + lane];
   } else if (ok && lane == kVsysSlot) {
-    for (int i = row_first[b]; i < row_first[b + 1]; ++i)
+    const int i0 = row_first ? row_first[b] : b * nb, i1 = row_first ? row_first[b + 1] : (b + 1) * nb;
+    for (int i = i0; i < i1; ++i)
       if (BANG_IN(i, n_items, kSiteFinalizeItem)) sum += vsys_partial[i];
   }
   double s[kVsysSlot + 1];
@@ -608,9 +632,10 @@ __global__ void table_kernel(const ModelConst* __restrict__ consts, const GalDev
   __shared__ double t0h[2];
   if (threadIdx.x == 0) {
     m = consts[b];
-    if (!BANG_IN(row_g[b], n_gal, kSiteDecodeGal) || !BANG_IN(kTabHdr + (derivs ? 8 : 4) * T - 1, stride, kSiteTable))
-      m.valid = 0;
-    const GalDev g = gals[BANG_IN(row_g[b], n_gal, kSiteDecodeGal) ? row_g[b] : 0];
+    const int gi = row_g ? row_g[b] : 0;
+    const bool gal_ok = (unsigned)gi < (unsigned)n_gal && BANG_IN(gi, n_gal, kSiteDecodeGal);
+    if (!gal_ok || !BANG_IN(kTabHdr + (derivs ? 8 : 4) * T - 1, stride, kSiteTable)) m.valid = 0;
+    const GalDev g = gals[gal_ok ? gi : 0];
     const double xa = m.X0, xb = m.X0 + (double)(g.W - 1) * g.pitch_kpa;
     const double ya = m.Y0, yb = m.Y0 + (double)(g.H - 1) * g.pitch_kpa;
     const double rmax = sqrt(fmax(xa * xa, xb * xb) + fmax(ya * ya, yb * yb));
@@ -718,12 +743,13 @@ BANG_DEFINE_FAULT_TAKER(take_fault_adjoint)
 
 cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind,
                             const double* acc_partial, const int* adj_row_first, const double* vsys_partial,
-                            const int* row_first, int B, int n_items, int adj_items, float* grad, cudaStream_t st) {
+                            const int* row_first, int B, int n_items, int adj_items, float* grad, cudaStream_t st,
+                            int adj_nb, int nb, const int* gal_idx, int n_gal) {
   constexpr int kRowsPerBlock = 4;   // 4 warps, one row each
   const double l10k = std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit));
   grad_out_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(
       theta, P, n_discs, halo_kind, bulge_kind, acc_partial, adj_row_first, vsys_partial, row_first, B, n_items,
-      adj_items, l10k, grad);
+      adj_items, adj_nb, nb, gal_idx, n_gal, l10k, grad);
   return cudaGetLastError();
 }
 

@@ -1,8 +1,8 @@
 // Host side of libbang.so: the C ABI of include/bang.h.
 //
-// bang_model_create copies every galaxy's data to the device once (App. A: "allocation and
-// loading only once"), builds the combined PSF (x) box-filter taps of Eq. 21 and the radial
-// quadrature tables.  Each compute call turns the rows of a batch into a table of work
+// bang_model_create copies every galaxy's data to the device once (App. A allocates and
+// loads the data a single time), builds the combined PSF (x) box-filter taps of Eq. 21 and
+// the radial quadrature tables.  Each compute call turns the rows of a batch into a table of work
 // items (row, galaxy, band of spaxel rows), cached per batch shape, and runs one persistent
 // launch over it, replayed from a CUDA graph when the same buffers come back.
 #include <cuda_runtime.h>
@@ -293,11 +293,19 @@ struct Plan {
   int adj_items = 0, adj_G = 4, adj_grid = 0;
   size_t adj_smem = 0;
   DevBuf d_adj_items, d_adj_order, d_adj_row_first;
+  // device-index plan (gal_idx in device memory): implicit work items, nb per row and
+  // adj_nb fine-row bands of adj_rows rows per row; seeds at a fixed stride per row; items
+  // ordered on the device by the rank of their galaxy's cost (d_rank, d_adj_rank)
+  bool implicit = false;
+  int nb = 1, adj_nb = 1, n_rank = 0, n_adj_rank = 0;
+  int64_t out_stride = 0;
+  DevBuf d_rank, d_adj_rank;
   // graph replay
   cudaGraphExec_t graph = nullptr;
   const void* g_theta = nullptr;
   const void* g_out = nullptr;
   const void* g_out2 = nullptr;
+  const void* g_gal = nullptr;
   ~Plan() {
     if (graph) cudaGraphExecDestroy(graph);
   }
@@ -319,6 +327,32 @@ bool is_device_pointer(const void* p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Where gal_idx lives: 0 host memory (or NULL), 1 device (or managed) memory the model's
+// device can read, -1 device memory of another device.
+int gal_idx_place(const int32_t* gal_idx, int device) {
+  if (!gal_idx) return 0;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, gal_idx) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (at.type == cudaMemoryTypeManaged) return 1;
+  if (at.type != cudaMemoryTypeDevice) return 0;
+  return at.device == device ? 1 : -1;
+}
+
+// A host copy of gal_idx for the entry points that schedule on the host (synchronous).
+bang_status host_gal_idx(const int32_t* gal_idx, int B, int device, std::vector<int32_t>& buf, const int32_t** out) {
+  *out = gal_idx;
+  const int place = gal_idx_place(gal_idx, device);
+  if (place < 0) return fail(BANG_E_INVALID_ARG, "gal_idx is device memory of another device");
+  if (place == 0) return BANG_OK;
+  buf.resize((size_t)B);
+  BANG_CUDA(cudaMemcpy(buf.data(), gal_idx, sizeof(int32_t) * (size_t)B, cudaMemcpyDeviceToHost));
+  *out = buf.data();
+  return BANG_OK;
 }
 
 }  // namespace
@@ -437,6 +471,14 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   p->out_off.assign(B, 0);
   std::vector<double> cost;
   int64_t off = 0;
+  // bands per row from the model's tallest galaxy (a shorter galaxy's empty bands are
+  // skipped), the policy of the device-index plans, so that both split a row alike
+  int ny_model = 1, H_model = 1;
+  for (const bang::GalDev& G : m->gals) {
+    ny_model = std::max(ny_model, G.ny);
+    H_model = std::max(H_model, G.H);
+  }
+  const int nb = bands_for(m, B, ny_model, tune.bands);
   for (int b = 0; b < B; ++b) {
     const int g = gal_idx ? gal_idx[b] : 0;
     if (g < 0 || g >= (int)m->gals.size()) return fail(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
@@ -445,7 +487,6 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     p->out_off[b] = off;
     off += (int64_t)4 * G.nx * G.ny;
     p->row_first[b] = (int)p->items.size();
-    const int nb = bands_for(m, B, G.ny, tune.bands);
     p->bands = std::max(p->bands, nb);
     for (int k = 0; k < nb; ++k) {
       const int j0 = (int)((long long)G.ny * k / nb), j1 = (int)((long long)G.ny * (k + 1) / nb);
@@ -506,9 +547,9 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   p->grid = std::min(p->n_items, per_sm * m->num_sms);
 
   if (mode == bang::kModeSeed) {
-    // adjoint work items: bands of fine rows, sized for ~16 items per SM
-    long long total_rows = 0;
-    for (int b = 0; b < B; ++b) total_rows += m->gals[p->row_g[b]].H;
+    // adjoint work items: bands of fine rows, sized for ~16 items per SM of B rows of the
+    // model's tallest grid (as the device-index plans size them)
+    const long long total_rows = (long long)B * H_model;
     // one staging step per band: rows per band = rows per block step (at most 16)
     const long long target = 16LL * m->num_sms;
     const int rows = (int)std::max<long long>(1, std::min<long long>(16, (total_rows + target - 1) / target));
@@ -568,15 +609,152 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   return BANG_OK;
 }
 
+// Ranks of the model's galaxies by the cost of one work item (0 = costliest), for the
+// device-side ordering of implicit items.
+std::vector<int> galaxy_ranks(const std::vector<double>& cost) {
+  std::vector<int> idx(cost.size()), rank(cost.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  for (size_t r = 0; r < idx.size(); ++r) rank[idx[r]] = (int)r;
+  return rank;
+}
+
+constexpr int kMaxOrderedGalaxies = 8192;   // beyond, implicit items run in index order
+
+uint64_t device_key(int B) {
+  const uint64_t tag = 0x6465766963652d67ull;   // keys of device-index plans differ from any host shape
+  return hash_bytes(&B, sizeof B, hash_bytes(&tag, sizeof tag));
+}
+
+// A plan for a batch whose gal_idx is device memory: nothing about the rows' galaxies is
+// known on the host, so the launch is sized for every galaxy of the model (shared memory,
+// bands: enough for the tallest galaxy, empty for shorter ones) and the work items are
+// implicit (the kernels read the galaxy of each row on the device).
+bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
+  const uint64_t skey = device_key(B);
+  const uint64_t key = hash_bytes(&mode, sizeof mode, skey);
+  bang_model::Tuning tune;
+  {
+    auto t = m->tuned.find(skey);
+    if (t != m->tuned.end()) tune = t->second;
+  }
+  for (auto it = m->plans.begin(); it != m->plans.end(); ++it) {
+    if ((*it)->key == key) {
+      m->plans.splice(m->plans.begin(), m->plans, it);
+      *out = m->plans.front().get();
+      return BANG_OK;
+    }
+  }
+  const int n_gal = (int)m->gals.size();
+  int psf2d = m->gals[0].psf_kind, ny_max = 1, H_max = 1, n4_max = 4;
+  for (const bang::GalDev& G : m->gals) {
+    if (G.psf_kind != psf2d)
+      return fail(BANG_E_UNSUPPORTED, "a device gal_idx needs galaxies of one PSF kind (the model mixes Gaussian and "
+                                      "two-dimensional taps)");
+    ny_max = std::max(ny_max, G.ny);
+    H_max = std::max(H_max, G.H);
+    n4_max = std::max(n4_max, 4 * G.nx * G.ny);
+  }
+  auto p = std::make_unique<Plan>();
+  p->key = key;
+  p->B = B;
+  p->mode = mode;
+  p->implicit = true;
+  p->nb = bands_for(m, B, ny_max, tune.bands);
+  p->bands = p->nb;
+  p->n_items = B * p->nb;
+  p->out_stride = n4_max;
+  p->out_total = (int64_t)B * n4_max;
+  p->G = tune.G;
+  size_t smem = 0;
+  for (const bang::GalDev& G : m->gals)
+    smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, p->G, psf2d, m->opts.bulge_table));
+  if (smem > (size_t)m->smem_optin - 4096) {
+    p->G = 1;
+    smem = 0;
+    for (const bang::GalDev& G : m->gals)
+      smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, 1, psf2d, m->opts.bulge_table));
+    if (smem > (size_t)m->smem_optin - 4096) return fail(BANG_E_UNSUPPORTED, "galaxy too large for one block's shared memory");
+  }
+  p->smem = smem;
+  const void* kp = bang::forward_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, mode);
+  cudaFuncAttributes fa;
+  BANG_CUDA(cudaFuncGetAttributes(&fa, kp));
+  if (smem + fa.sharedSizeBytes > (size_t)m->smem_optin)
+    return fail(BANG_E_UNSUPPORTED, "forward kernel needs %zu bytes of shared memory", smem + fa.sharedSizeBytes);
+  BANG_CUDA(cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 m->smem_optin - (int)fa.sharedSizeBytes));
+  int per_sm = 0;
+  BANG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp, bang::forward_threads(), smem));
+  if (per_sm < 1) return fail(BANG_E_UNSUPPORTED, "forward kernel does not fit on an SM (smem %zu)", smem);
+  p->blocks_per_sm = per_sm;
+  p->grid = std::min(p->n_items, per_sm * m->num_sms);
+  const bool ordered = n_gal > 1 && n_gal <= kMaxOrderedGalaxies;
+  if (ordered) {
+    std::vector<double> cost(n_gal);
+    for (int g = 0; g < n_gal; ++g) {
+      const bang::GalDev& G = m->gals[g];
+      cost[g] = (double)((G.ny + p->nb - 1) / p->nb * G.os + 2 * G.h) * G.W;
+    }
+    p->n_rank = n_gal;
+    BANG_CUDA(copy_vec(p->d_rank, galaxy_ranks(cost)));
+    BANG_CUDA(p->d_order.reserve(sizeof(int) * (size_t)p->n_items));
+  }
+  if (mode == bang::kModeSeed) {
+    const long long target = 16LL * m->num_sms;
+    const int rows = (int)std::max<long long>(1, std::min<long long>(16, ((long long)B * H_max + target - 1) / target));
+    p->adj_G = rows;
+    p->adj_nb = (H_max + rows - 1) / rows;
+    p->adj_items = B * p->adj_nb;
+    size_t asmem = 0;
+    for (const bang::GalDev& G : m->gals)
+      asmem = std::max(asmem, bang::adjoint_smem_bytes(G.L, G.os, G.nx, p->adj_G, psf2d, m->opts.bulge_table));
+    p->adj_smem = asmem;
+    const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, m->opts.bulge_table > 0);
+    cudaFuncAttributes afa;
+    BANG_CUDA(cudaFuncGetAttributes(&afa, ak));
+    if (asmem + afa.sharedSizeBytes > (size_t)m->smem_optin)
+      return fail(BANG_E_UNSUPPORTED, "adjoint kernel needs %zu bytes of shared memory", asmem + afa.sharedSizeBytes);
+    BANG_CUDA(cudaFuncSetAttribute(ak, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   m->smem_optin - (int)afa.sharedSizeBytes));
+    int aper = 0;
+    BANG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&aper, ak, bang::adjoint_threads(), asmem));
+    if (aper < 1) return fail(BANG_E_UNSUPPORTED, "adjoint kernel does not fit on an SM");
+    p->adj_grid = std::min(p->adj_items, aper * m->num_sms);
+    if (ordered) {
+      std::vector<double> cost(n_gal);
+      for (int g = 0; g < n_gal; ++g) cost[g] = (double)rows * m->gals[g].W;
+      p->n_adj_rank = n_gal;
+      BANG_CUDA(copy_vec(p->d_adj_rank, galaxy_ranks(cost)));
+      BANG_CUDA(p->d_adj_order.reserve(sizeof(int) * (size_t)p->adj_items));
+    }
+  }
+  BANG_CUDA(p->d_partial.reserve(sizeof(double) * std::max(1, p->n_items)));
+  BANG_CUDA(p->d_queue.reserve(2 * sizeof(int)));
+  BANG_CUDA(p->d_consts.reserve(bang::model_const_bytes() * (size_t)B));
+  if (m->opts.bulge_table > 0) {
+    p->table_stride = bang::table_row_floats(m->opts.bulge_table, mode == bang::kModeSeed);
+    BANG_CUDA(p->d_tables.reserve(sizeof(float) * (size_t)p->table_stride * B));
+  }
+  p->row_g.assign(1, 0);   // psf2d_of: every galaxy of the model has the same PSF kind here
+  m->plans.push_front(std::move(p));
+  while (m->plans.size() > 8) m->plans.pop_back();
+  *out = m->plans.front().get();
+  return BANG_OK;
+}
+
 int psf2d_of(const bang_model* m, const Plan* p) { return m->gals[p->row_g[0]].psf_kind; }
 
+// dgal: the caller's device gal_idx for a device-index plan (p->implicit), else unused.
 cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode, double* logL, float* out,
-                            cudaStream_t st, double* vsys_partial = nullptr) {
+                            cudaStream_t st, double* vsys_partial = nullptr, const int* dgal = nullptr) {
   bang::FwdArgs a{};
   a.theta = theta;
   a.P = m->P;
   a.gals = m->d_gals.as<bang::GalDev>();
-  a.items = p->d_items.as<bang::WorkItem>();
+  a.items = p->implicit ? nullptr : p->d_items.as<bang::WorkItem>();
+  a.gal_idx = p->implicit ? dgal : nullptr;
+  a.nb = p->nb;
   a.order = p->d_order.as<int>();
   a.n_items = p->n_items;
   a.G = p->G;
@@ -584,21 +762,27 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.maps = mode == bang::kModeMaps ? out : nullptr;
   a.seed = mode == bang::kModeSeed ? out : nullptr;
   a.vsys_partial = mode == bang::kModeSeed ? vsys_partial : nullptr;
-  a.out_off = p->d_out_off.as<int64_t>();
+  a.out_off = p->implicit ? nullptr : p->d_out_off.as<int64_t>();
+  a.out_stride = p->out_stride;
   a.queue = p->d_queue.as<int>();
   a.consts = p->d_consts.as<bang::ModelConst>();
   a.halo_kind = m->opts.halo_kind;
   a.B = p->B;
   a.n_gal = (int)m->gals.size();
   a.out_total = p->out_total;
-  cudaError_t e = bang::launch_decode(theta, m->P, m->opts.n_discs, m->opts.halo_kind, a.gals, p->d_row_g.as<int>(),
-                                      a.n_gal, p->B, p->d_consts.as<bang::ModelConst>(), st);
+  const int* row_g = p->implicit ? dgal : p->d_row_g.as<int>();
+  cudaError_t e = bang::launch_decode(theta, m->P, m->opts.n_discs, m->opts.halo_kind, a.gals, row_g, a.n_gal, p->B,
+                                      p->d_consts.as<bang::ModelConst>(), st);
   if (e != cudaSuccess) return e;
+  if (p->implicit && p->n_rank > 0) {
+    e = bang::launch_order(dgal, p->d_rank.as<int>(), a.n_gal, p->n_rank, p->B, p->nb, p->d_order.as<int>(), st);
+    if (e != cudaSuccess) return e;
+  }
   if (m->opts.bulge_table > 0) {
     a.tables = p->d_tables.as<float>();
     a.table_T = m->opts.bulge_table;
     a.table_stride = p->table_stride;
-    e = bang::launch_tables(a.consts, a.gals, p->d_row_g.as<int>(), a.n_gal, p->B, m->opts.n_quad, a.table_T,
+    e = bang::launch_tables(a.consts, a.gals, row_g, a.n_gal, p->B, m->opts.n_quad, a.table_T,
                             mode == bang::kModeSeed, p->d_tables.as<float>(), p->table_stride, st);
     if (e != cudaSuccess) return e;
   }
@@ -606,6 +790,8 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   if (e != cudaSuccess) return e;
   e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
   if (e != cudaSuccess || !logL) return e;
+  if (p->implicit)
+    return bang::launch_finalize(a.partial, nullptr, dgal, a.gals, p->B, p->n_items, a.n_gal, logL, st, p->nb, 1);
   return bang::launch_finalize(a.partial, p->d_row_first.as<int>(), p->d_row_g.as<int>(), a.gals, p->B, p->n_items,
                                a.n_gal, logL, st);
 }
@@ -617,22 +803,26 @@ size_t grad_scratch_bytes(const Plan* p) {
 }
 
 cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* logL, float* seed, double* scratch,
-                         float* grad, cudaStream_t st) {
+                         float* grad, cudaStream_t st, const int* dgal = nullptr) {
   double* vsys_partial = scratch;
   double* acc_partial = scratch + std::max(1, p->n_items);
-  cudaError_t e = enqueue_forward(m, p, theta, bang::kModeSeed, logL, seed, st, vsys_partial);
+  cudaError_t e = enqueue_forward(m, p, theta, bang::kModeSeed, logL, seed, st, vsys_partial, dgal);
   if (e != cudaSuccess) return e;
   bang::AdjArgs a{};
   a.theta = theta;
   a.P = m->P;
   a.gals = m->d_gals.as<bang::GalDev>();
   a.consts = p->d_consts.as<bang::ModelConst>();
-  a.items = p->d_adj_items.as<bang::WorkItem>();
+  a.items = p->implicit ? nullptr : p->d_adj_items.as<bang::WorkItem>();
+  a.gal_idx = p->implicit ? dgal : nullptr;
+  a.nb = p->adj_nb;
+  a.rows_per_item = p->adj_G;
   a.order = p->d_adj_order.as<int>();
   a.n_items = p->adj_items;
   a.G = p->adj_G;
   a.seed = seed;
-  a.out_off = p->d_out_off.as<int64_t>();
+  a.out_off = p->implicit ? nullptr : p->d_out_off.as<int64_t>();
+  a.out_stride = p->out_stride;
   a.acc_partial = acc_partial;
   a.B = p->B;
   a.n_gal = (int)m->gals.size();
@@ -643,10 +833,19 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
     a.table_stride = p->table_stride;
   }
   a.queue = p->d_queue.as<int>() + 1;
+  if (p->implicit && p->n_adj_rank > 0) {
+    e = bang::launch_order(dgal, p->d_adj_rank.as<int>(), a.n_gal, p->n_adj_rank, p->B, p->adj_nb,
+                           p->d_adj_order.as<int>(), st);
+    if (e != cudaSuccess) return e;
+  }
   e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
   if (e != cudaSuccess) return e;
+  if (p->implicit)
+    return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, m->opts.bulge_kind, acc_partial,
+                                 nullptr, vsys_partial, nullptr, p->B, p->n_items, p->adj_items, grad, st, p->adj_nb,
+                                 p->nb, dgal, (int)m->gals.size());
   return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, m->opts.bulge_kind, acc_partial,
                                p->d_adj_row_first.as<int>(), vsys_partial, p->d_row_first.as<int>(), p->B,
                                p->n_items, p->adj_items, grad, st);
@@ -841,6 +1040,7 @@ int bang_model_psf_halfwidth(const bang_model* m, int g) {
 
 int64_t bang_model_maps_size(const bang_model* m, const int32_t* gal_idx, int B) {
   if (!m || B < 0) return -1;
+  if (gal_idx_place(gal_idx, m->device) != 0) return -1;   // a host array only
   int64_t n = 0;
   for (int b = 0; b < B; ++b) {
     const int g = gal_idx ? gal_idx[b] : 0;
@@ -876,10 +1076,15 @@ bang_status run_forward(bang_model* m, const float* theta, const int32_t* gal_id
   std::lock_guard<std::mutex> lock(m->mu);
   ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
+  const int gplace = gal_idx_place(gal_idx, m->device);
+  if (gplace < 0) return fail(BANG_E_INVALID_ARG, "gal_idx is device memory of another device");
+  if (gplace > 0 && mode == bang::kModeMaps)
+    return fail(BANG_E_UNSUPPORTED, "bang_model_maps: gal_idx must be host memory (the output packing depends on it)");
+  const int* dgal = gplace > 0 ? gal_idx : nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CallOrder order(m, st);
   Plan* p = nullptr;
-  bang_status s = get_plan(m, gal_idx, B, mode, &p);
+  bang_status s = dgal ? get_dplan(m, B, mode, &p) : get_plan(m, gal_idx, B, mode, &p);
   if (s != BANG_OK) return s;
 
   const bool th_dev = is_device_pointer(theta);
@@ -901,14 +1106,14 @@ bang_status run_forward(bang_model* m, const float* theta, const int32_t* gal_id
   }
 
   if (m->use_graphs && mode == bang::kModeLogL) {
-    if (!p->graph || p->g_theta != d_theta || p->g_out != d_logL) {
+    if (!p->graph || p->g_theta != d_theta || p->g_out != d_logL || p->g_gal != dgal) {
       if (p->graph) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
       }
       cudaGraph_t g = nullptr;
       BANG_CUDA(cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = enqueue_forward(m, p, d_theta, mode, d_logL, nullptr, m->capture_stream);
+      cudaError_t e = enqueue_forward(m, p, d_theta, mode, d_logL, nullptr, m->capture_stream, nullptr, dgal);
       cudaError_t e2 = cudaStreamEndCapture(m->capture_stream, &g);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -919,10 +1124,12 @@ bang_status run_forward(bang_model* m, const float* theta, const int32_t* gal_id
       if (e != cudaSuccess) return fail(BANG_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
       p->g_theta = d_theta;
       p->g_out = d_logL;
+      p->g_gal = dgal;
     }
     BANG_CUDA(cudaGraphLaunch(p->graph, st));
   } else {
-    BANG_CUDA(enqueue_forward(m, p, d_theta, mode, mode == bang::kModeLogL ? d_logL : nullptr, d_maps, st));
+    BANG_CUDA(enqueue_forward(m, p, d_theta, mode, mode == bang::kModeLogL ? d_logL : nullptr, d_maps, st, nullptr,
+                              dgal));
   }
   if (!out_dev) {
     BANG_CUDA(cudaMemcpyAsync(mode == bang::kModeLogL ? (void*)logL : (void*)maps, m->stage_out.p, out_bytes,
@@ -959,10 +1166,13 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
   std::lock_guard<std::mutex> lock(m->mu);
   ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
+  const int gplace = gal_idx_place(gal_idx, m->device);
+  if (gplace < 0) return fail(BANG_E_INVALID_ARG, "gal_idx is device memory of another device");
+  const int* dgal = gplace > 0 ? gal_idx : nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CallOrder order(m, st);
   Plan* p = nullptr;
-  bang_status s = get_plan(m, gal_idx, B, bang::kModeSeed, &p);
+  bang_status s = dgal ? get_dplan(m, B, bang::kModeSeed, &p) : get_plan(m, gal_idx, B, bang::kModeSeed, &p);
   if (s != BANG_OK) return s;
   const size_t th_bytes = sizeof(float) * (size_t)B * m->P;
   const bool th_dev = is_device_pointer(theta), l_dev = is_device_pointer(logL), g_dev = is_device_pointer(grad);
@@ -981,7 +1191,8 @@ bang_status bang_loglike_grad_batch(bang_model* m, const float* theta, const int
   }
   BANG_CUDA(m->scratch_seed.reserve(sizeof(float) * (size_t)std::max<int64_t>(p->out_total, 4)));
   BANG_CUDA(m->scratch_grad.reserve(grad_scratch_bytes(p)));
-  BANG_CUDA(enqueue_grad(m, p, d_theta, d_logL, m->scratch_seed.as<float>(), m->scratch_grad.as<double>(), d_grad, st));
+  BANG_CUDA(enqueue_grad(m, p, d_theta, d_logL, m->scratch_seed.as<float>(), m->scratch_grad.as<double>(), d_grad, st,
+                         dgal));
   if (!l_dev) BANG_CUDA(cudaMemcpyAsync(logL, d_logL, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   if (!g_dev) BANG_CUDA(cudaMemcpyAsync(grad, d_grad, th_bytes, cudaMemcpyDeviceToHost, st));
   if (!th_dev || !l_dev || !g_dev) BANG_CUDA(cudaStreamSynchronize(st));
@@ -1044,6 +1255,11 @@ bang_status bang_loglike_plain(bang_model* m, const float* theta, const int32_t*
   std::lock_guard<std::mutex> lock(m->mu);
   ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
+  std::vector<int32_t> gal_host;
+  {
+    bang_status gs = host_gal_idx(gal_idx, B, m->device, gal_host, &gal_idx);
+    if (gs != BANG_OK) return gs;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CallOrder order(m, st);
   size_t need = 0;
@@ -1144,6 +1360,12 @@ bang_status bang_loglike_fp64(bang_model* m, const double* theta, const int32_t*
   if (m->opts.bulge_kind != 0)
     return fail(BANG_E_UNSUPPORTED, "bang_loglike_fp64: radial-rule bulge only (bulge_kind 0)");
   if (m->opts.psf_mode & BANG_PSF_FLUX) return fail(BANG_E_UNSUPPORTED, "bang_loglike_fp64: no flux-weighted PSF mode");
+  BANG_CUDA(cudaSetDevice(m->device));
+  std::vector<int32_t> gal_host;
+  {
+    bang_status gs = host_gal_idx(gal_idx, B, m->device, gal_host, &gal_idx);
+    if (gs != BANG_OK) return gs;
+  }
   for (int b = 0; b < B; ++b) {
     const int g = gal_idx ? gal_idx[b] : 0;
     if (g < 0 || g >= (int)m->gals.size()) return fail(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
@@ -1205,12 +1427,24 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   std::lock_guard<std::mutex> lock(m->mu);
   ScratchScope scope(&m->budget);
   BANG_CUDA(cudaSetDevice(m->device));
+  // a device gal_idx is tuned on the device-index launch (implicit work items) that later
+  // calls with a device gal_idx of B rows take; its contents are read here only to check them
+  const int gplace = gal_idx_place(gal_idx, m->device);
+  const int* dgal = gplace > 0 ? gal_idx : nullptr;
+  std::vector<int32_t> gal_host;
+  const int32_t* hgal = gal_idx;
+  {
+    bang_status gs = host_gal_idx(gal_idx, B, m->device, gal_host, &hgal);
+    if (gs != BANG_OK) return gs;
+  }
   int ny_max = 1;
   for (int b = 0; b < B; ++b) {
-    const int g = gal_idx ? gal_idx[b] : 0;
+    const int g = hgal ? hgal[b] : 0;
     if (g < 0 || g >= (int)m->gals.size()) return fail(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
     ny_max = std::max(ny_max, m->gals[g].ny);
   }
+  if (dgal)
+    for (const bang::GalDev& G : m->gals) ny_max = std::max(ny_max, G.ny);
   // in-domain parameter vectors of typical size (the cost does not depend on the values)
   static const float kTypical[19] = {0.02f, -0.03f, 0.5f, 0.9f, 10.0f, 0.0f, 1.0f, 10.5f, 0.5f, 0.5f,
                                      4.0f, 2.5f, 12.5f, 10.0f, 0.0f, 10.2f, 0.6f, 0.6f, 2.5f};
@@ -1221,7 +1455,7 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   BANG_CUDA(m->stage_theta.reserve(th.size() * sizeof(float)));
   BANG_CUDA(cudaMemcpy(m->stage_theta.p, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice));
   BANG_CUDA(m->stage_out.reserve(sizeof(double) * B));
-  const uint64_t skey = shape_key(gal_idx, B);
+  const uint64_t skey = dgal ? device_key(B) : shape_key(hgal, B);
   std::vector<int> bands = {0};
   if (B < 4 * m->num_sms)
     for (int nb : {1, 2, 4, 8, 16})
@@ -1239,13 +1473,14 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
       m->tuned[skey] = bang_model::Tuning{G, nb};
       m->plans.clear();
       Plan* p = nullptr;
-      if (get_plan(m, gal_idx, B, bang::kModeLogL, &p) != BANG_OK) continue;
+      if ((dgal ? get_dplan(m, B, bang::kModeLogL, &p) : get_plan(m, hgal, B, bang::kModeLogL, &p)) != BANG_OK)
+        continue;
       if (p->G != G) continue;   // shared memory forced a smaller step
       float t_min = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         BANG_CUDA(cudaEventRecord(e0, st));
         BANG_CUDA(enqueue_forward(m, p, m->stage_theta.as<float>(), bang::kModeLogL, m->stage_out.as<double>(), nullptr,
-                                  st));
+                                  st, nullptr, dgal));
         BANG_CUDA(cudaEventRecord(e1, st));
         BANG_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;

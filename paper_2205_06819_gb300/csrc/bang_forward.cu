@@ -126,8 +126,26 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       BANG_NEXT_ITEM(it);
       continue;
     }
-    const WorkItem w = a.items[item_id];
+    WorkItem w;
+    bool bad_gal = false;
+    if (a.items) {
+      w = a.items[item_id];
+    } else {   // implicit item: band k of row b, the row's galaxy read on the device
+      const int b = item_id / a.nb, k = item_id - b * a.nb;
+      const int g = a.gal_idx ? __ldg(a.gal_idx + b) : 0;
+      bad_gal = (unsigned)g >= (unsigned)a.n_gal;
+      const int ny = bad_gal ? 0 : __ldg(&a.gals[g].ny);
+      w = WorkItem{b, bad_gal ? 0 : g, (int)((long long)ny * k / a.nb), (int)((long long)ny * (k + 1) / a.nb)};
+    }
     if (!BANG_IN(w.b, a.B, kSiteFwdRow) || !BANG_IN(w.g, a.n_gal, kSiteFwdGal)) {
+      BANG_NEXT_ITEM(it);
+      continue;
+    }
+    if (bad_gal || w.j1 <= w.j0) {   // a row without a galaxy, or an empty band of a galaxy with fewer rows
+      if (tid == 0) {
+        a.partial[item_id] = bad_gal ? __longlong_as_double(0x7ff8000000000000ll) : 0.0;
+        if (MODE == kModeSeed) a.vsys_partial[item_id] = 0.0;
+      }
       BANG_NEXT_ITEM(it);
       continue;
     }
@@ -148,8 +166,9 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     float4* stage = acc + (size_t)NA * nx;
     float* tab = a.tables ? reinterpret_cast<float*>(stage + 2 * (size_t)a.G * W) : nullptr;
     float* out = nullptr;
-    if (MODE == kModeMaps) out = a.maps + a.out_off[w.b];
-    if (MODE == kModeSeed) out = a.seed + a.out_off[w.b];
+    const int64_t ooff = a.out_off ? a.out_off[w.b] : (int64_t)w.b * a.out_stride;
+    if (MODE == kModeMaps) out = a.maps + ooff;
+    if (MODE == kModeSeed) out = a.seed + ooff;
     // checked build: the layout fits the launch's shared memory, a fine row holds every
     // stencil read, the item's spaxel rows, output block and radial table are in range
     if (!BANG_IN((tab ? reinterpret_cast<const unsigned char*>(tab + kTabHdr + 4 * a.table_T)
@@ -157,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
                  dynamic_smem_bytes(), kSiteFwdSmem) ||
         !BANG_IN((nx - 1) * os + L - 1, W, kSiteFwdStencil) || !BANG_IN(w.j0, w.j1, kSiteFwdSpaxel) ||
         !BANG_IN(w.j1 - 1, gs.ny, kSiteFwdSpaxel) ||
-        (MODE != kModeLogL && !BANG_IN(a.out_off[w.b] + 4ll * nx * gs.ny - 1, a.out_total, kSiteFwdOut)) ||
+        (MODE != kModeLogL && !BANG_IN(ooff + 4ll * nx * gs.ny - 1, a.out_total, kSiteFwdOut)) ||
         (tab && !BANG_IN((long long)w.b * a.table_stride + kTabHdr + 4 * a.table_T - 1,
                          (long long)a.B * a.table_stride, kSiteFwdTable))) {
       BANG_NEXT_ITEM(it);
@@ -350,8 +369,9 @@ __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, in
   const int lane = threadIdx.x & 31;
   if (b >= B) return;   // whole warps: b is uniform across the warp
   const float* th = theta + (size_t)b * P;
-  const bool gal_ok = BANG_IN(row_g[b], n_gal, kSiteDecodeGal);
-  const GalDev& gal = gals[gal_ok ? row_g[b] : 0];
+  const int g = row_g ? row_g[b] : 0;
+  const bool gal_ok = (unsigned)g < (unsigned)n_gal && BANG_IN(g, n_gal, kSiteDecodeGal);
+  const GalDev& gal = gals[gal_ok ? g : 0];
   const bool ok = gal_ok && theta_in_domain(th, nd, halo_kind, gal.bulge_kind);
   const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
   double T[kDecodeTerms];
@@ -368,21 +388,75 @@ __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, in
 }
 
 // logL[b] = -chi^2/2 - const from the per-item partial sums (items of row b are contiguous).
+// row_first NULL: the items of row b are [b nb, (b + 1) nb); row_g NULL: galaxy 0.  With
+// check_gal, a row whose galaxy index is outside [0, n_gal) gets NaN (its items were skipped).
 __global__ void finalize_kernel(const double* __restrict__ partial, const int* __restrict__ row_first,
                                 const int* __restrict__ row_g, const GalDev* __restrict__ gals, int B, int n_items,
-                                int n_gal, double* __restrict__ logL) {
+                                int n_gal, int nb, int check_gal, double* __restrict__ logL) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  const int g = row_g ? row_g[b] : 0;
+  if (check_gal && (unsigned)g >= (unsigned)n_gal) {
+    logL[b] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
   double s = 0.0;
   bool bad = false;
-  for (int k = row_first[b]; k < row_first[b + 1]; ++k) {
+  const int k0 = row_first ? row_first[b] : b * nb, k1 = row_first ? row_first[b + 1] : (b + 1) * nb;
+  for (int k = k0; k < k1; ++k) {
     if (!BANG_IN(k, n_items, kSiteFinalizeItem)) continue;
     const double v = partial[k];
     bad |= isnan(v);
     s += v;
   }
-  if (!BANG_IN(row_g[b], n_gal, kSiteDecodeGal)) return;
-  logL[b] = bad ? -INFINITY : -0.5 * s - gals[row_g[b]].norm_const;
+  if (!BANG_IN(g, n_gal, kSiteDecodeGal)) return;
+  logL[b] = bad ? -INFINITY : -0.5 * s - gals[g].norm_const;
+}
+
+// Execution order of implicit work items (nb per row), longest first: a counting sort of the
+// rows by the rank of their galaxy's item cost (gal_rank[g] in [0, n_rank), 0 = costliest),
+// the items of a row kept together.  Rows without a valid galaxy go last.  One block; the
+// order within a rank follows the atomics (it changes which block runs an item, not any
+// result: every item writes its own partial sums).
+constexpr int kOrderThreads = 1024;
+__global__ void __launch_bounds__(kOrderThreads) order_kernel(const int* __restrict__ gal_idx,
+                                                              const int* __restrict__ gal_rank, int n_gal, int n_rank,
+                                                              int B, int nb, int* __restrict__ order) {
+  extern __shared__ int cnt[];   // n_rank + 1 counters
+  __shared__ int part[kOrderThreads];
+  const int tid = threadIdx.x, nr = n_rank + 1;
+  for (int r = tid; r < nr; r += kOrderThreads) cnt[r] = 0;
+  __syncthreads();
+  auto rank_of = [&](int b) {
+    const int g = gal_idx ? gal_idx[b] : 0;
+    return (unsigned)g < (unsigned)n_gal ? gal_rank[g] : n_rank;
+  };
+  for (int b = tid; b < B; b += kOrderThreads) atomicAdd(&cnt[rank_of(b)], nb);
+  __syncthreads();
+  // exclusive scan of the counters: each thread a contiguous chunk, then the chunk totals
+  const int per = (nr + kOrderThreads - 1) / kOrderThreads;
+  const int r0 = min(nr, tid * per), r1 = min(nr, r0 + per);
+  int local = 0;
+  for (int r = r0; r < r1; ++r) local += cnt[r];
+  part[tid] = local;
+  __syncthreads();
+  for (int off = 1; off < kOrderThreads; off <<= 1) {   // Hillis-Steele inclusive scan of part
+    const int v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int run = part[tid] - local;
+  for (int r = r0; r < r1; ++r) {
+    const int c = cnt[r];
+    cnt[r] = run;
+    run += c;
+  }
+  __syncthreads();
+  for (int b = tid; b < B; b += kOrderThreads) {
+    const int pos = atomicAdd(&cnt[rank_of(b)], nb);
+    for (int k = 0; k < nb; ++k) order[pos + k] = b * nb + k;
+  }
 }
 
 template <int NQ, int ND, int PSF, int MODE>
@@ -488,8 +562,16 @@ cudaError_t launch_sum_rows(const double* logL_x, const float* grad_x, int P, in
 }
 
 cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
-                            int n_items, int n_gal, double* logL, cudaStream_t st) {
-  finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(partial, row_first, row_g, gals, B, n_items, n_gal, logL);
+                            int n_items, int n_gal, double* logL, cudaStream_t st, int nb, int check_gal) {
+  finalize_kernel<<<(B + 127) / 128, 128, 0, st>>>(partial, row_first, row_g, gals, B, n_items, n_gal, nb, check_gal,
+                                                   logL);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const int* gal_idx, const int* gal_rank, int n_gal, int n_rank, int B, int nb, int* order,
+                         cudaStream_t st) {
+  order_kernel<<<1, kOrderThreads, sizeof(int) * (size_t)(n_rank + 1), st>>>(gal_idx, gal_rank, n_gal, n_rank, B, nb,
+                                                                            order);
   return cudaGetLastError();
 }
 
@@ -580,6 +662,14 @@ extern "C" bang_status bang_loglike_batch_noalloc(bang_model* m, const float* th
     if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
       cudaGetLastError();
       return set_error(BANG_E_INVALID_ARG, "bang_loglike_batch_noalloc: theta and logL must be device memory");
+    }
+  }
+  if (gal_idx) {   // this entry point schedules on the host: gal_idx must be host memory
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, gal_idx) != cudaSuccess) {
+      cudaGetLastError();
+    } else if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+      return set_error(BANG_E_INVALID_ARG, "bang_loglike_batch_noalloc: gal_idx must be host memory");
     }
   }
   int psf2d = -1;

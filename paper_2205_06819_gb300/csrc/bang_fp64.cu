@@ -45,8 +45,31 @@ __device__ void bessel_k01(double x, double& k0, double& k1) {
   k1 = h * s1;
 }
 
-// I0(y) K0(y) - I1(y) K1(y) of the Freeman disc (y < ~700, where I0 stays finite).
+// I0(y) K0(y) - I1(y) K1(y) for y > 25 from the large-argument expansion of the products
+// I_nu K_nu (DLMF 10.40.6): I_nu(y) K_nu(y) ~ (1 / 2y) sum_k (-1)^k c_k p_k(nu) / (2y)^(2k),
+// c_k = (1 3 ... (2k-1)) / (2 4 ... 2k), p_k(nu) = prod_{j<=k} (4 nu^2 - (2j-1)^2).  The
+// k = 0 terms of nu = 0 and 1 cancel exactly, so the difference is summed term by term
+// without the cancellation of the direct form; twelve terms give double precision from
+// y = 25 on (the leading term is 1 / (4 y^3)).
+__device__ double freeman_bessel_series(double y) {
+  const double z2 = 1.0 / (4.0 * y * y);
+  double s = 0.0, c = 1.0, p0 = 1.0, p1 = 1.0, zk = 1.0;
+  for (int k = 1; k <= 12; ++k) {
+    const double o = (2.0 * k - 1.0) * (2.0 * k - 1.0);
+    c *= (2.0 * k - 1.0) / (2.0 * k);
+    p0 *= -o;          // nu = 0
+    p1 *= 4.0 - o;     // nu = 1
+    zk *= z2;
+    s += ((k & 1) ? -c : c) * (p0 - p1) * zk;
+  }
+  return s / (2.0 * y);
+}
+
+// I0(y) K0(y) - I1(y) K1(y) of the Freeman disc: the Bessel functions themselves up to
+// y = 25 (where the difference has lost ~y^2 x 1e-16 to cancellation), the expansion beyond
+// (I0 would overflow near y = 700).
 __device__ double freeman_bessel(double y) {
+  if (y > 25.0) return freeman_bessel_series(y);
   double k0, k1;
   bessel_k01(y, k0, k1);
   return cyl_bessel_i0(y) * k0 - cyl_bessel_i1(y) * k1;

@@ -45,7 +45,10 @@ struct FwdArgs {
   int halo_kind;            // 0 NFW, 1 Hernquist (used when consts is NULL)
   const GalDev* gals;
   const ModelConst* consts; // [B] decoded rows (NULL: each block decodes its row itself)
-  const WorkItem* items;    // [n_items], items of one row contiguous, rows in order
+  const WorkItem* items;    // [n_items], items of one row contiguous, rows in order; NULL: implicit items,
+                            // item i is band i % nb of row i / nb against galaxy gal_idx[i / nb]
+  const int* gal_idx;       // implicit items: device [B] galaxy of each row (NULL = galaxy 0)
+  int nb;                   // implicit items: bands per row
   const int* order;         // execution order of items (NULL = table order)
   int n_items;
   int* queue;               // dynamic item counter, zeroed before the launch (NULL = static striding)
@@ -54,7 +57,8 @@ struct FwdArgs {
   float* maps;              // kModeMaps: model maps, row b at out_off[b]
   float* seed;              // kModeSeed: d logL / dF per spaxel, row b at out_off[b]
   double* vsys_partial;     // kModeSeed: [n_items] d logL / d v_sys of each work item
-  const int64_t* out_off;   // [B] float offsets of each row's [4][ny][nx] block
+  const int64_t* out_off;   // [B] float offsets of each row's [4][ny][nx] block (NULL: b * out_stride)
+  int64_t out_stride;       // floats per row's block when out_off is NULL
   const float* tables;      // radial tables, row b at b * table_stride (NULL: quadrature per point)
   int table_T;              // radii per table
   int64_t table_stride;     // floats per row's table
@@ -69,13 +73,18 @@ struct AdjArgs {
   int P;
   const GalDev* gals;
   const ModelConst* consts; // [B] decoded rows
-  const WorkItem* items;    // fine-row bands (j0/j1 hold fine padded rows [y0, y1))
+  const WorkItem* items;    // fine-row bands (j0/j1 hold fine padded rows [y0, y1)); NULL: implicit items,
+                            // item i is fine rows [k rows_per_item, (k + 1) rows_per_item) of row i / nb,
+                            // k = i % nb, against galaxy gal_idx[i / nb] (empty past the galaxy's last row)
+  const int* gal_idx;       // implicit items: device [B] galaxy of each row (NULL = galaxy 0)
+  int nb, rows_per_item;    // implicit items: bands per row and fine rows per band
   const int* order;
   int n_items;
   int* queue;               // dynamic item counter, zeroed before the launch (NULL = static striding)
   int G;                    // fine rows per block step
-  const float* seed;        // d logL / dF at the spaxels, row b at out_off[b]
+  const float* seed;        // d logL / dF at the spaxels, row b at out_off[b] (NULL: b * out_stride)
   const int64_t* out_off;
+  int64_t out_stride;
   double* acc_partial;      // [n_items][kAdjSlots] float64 constant adjoints of each work item
   const float* tables;      // radial tables with slopes, row b at b * table_stride (NULL: quadrature)
   int table_T;
@@ -104,8 +113,14 @@ cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d,
 cudaError_t launch_expand_rows(const float* theta, int P, int B, int n, float* theta_x, cudaStream_t st);
 cudaError_t launch_sum_rows(const double* logL_x, const float* grad_x, int P, int B, int n, double* logL, float* grad,
                             cudaStream_t st);
+// row_first NULL: row b's items are [b nb, (b + 1) nb); row_g NULL: galaxy 0.  With
+// check_gal, a row whose galaxy index is outside [0, n_gal) gets logL = NaN.
 cudaError_t launch_finalize(const double* partial, const int* row_first, const int* row_g, const GalDev* gals, int B,
-                            int n_items, int n_gal, double* logL, cudaStream_t st);
+                            int n_items, int n_gal, double* logL, cudaStream_t st, int nb = 1, int check_gal = 0);
+// Execution order of implicit work items, longest first: items of rows whose galaxy has a
+// lower rank (gal_rank[g], 0 = the most costly item) come first; n_rank ranks.  One block.
+cudaError_t launch_order(const int* gal_idx, const int* gal_rank, int n_gal, int n_rank, int B, int nb, int* order,
+                         cudaStream_t st);
 cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float* ws, const float* wq);
 
 int adjoint_threads();
@@ -119,10 +134,14 @@ cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const in
 const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d, int table);
 cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
                            cudaStream_t st);
+// adj_row_first / row_first NULL: implicit items, adj_nb / nb per row; gal_idx (device, may be
+// NULL) marks rows with a galaxy index outside [0, n_gal) as invalid (zero gradient).
 cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kind, int bulge_kind,
                             const double* acc_partial, const int* adj_row_first, const double* vsys_partial,
-                            const int* row_first, int B, int n_items, int adj_items, float* grad, cudaStream_t st);
+                            const int* row_first, int B, int n_items, int adj_items, float* grad, cudaStream_t st,
+                            int adj_nb = 1, int nb = 1, const int* gal_idx = nullptr, int n_gal = 0);
 size_t model_const_bytes();
+// row_g NULL: galaxy 0 for every row; a galaxy index outside [0, n_gal) makes the row invalid.
 cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
                           int n_gal, int B, ModelConst* out, cudaStream_t st);
 cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq);

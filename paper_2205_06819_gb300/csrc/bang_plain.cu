@@ -13,7 +13,7 @@
 namespace bang {
 namespace {
 
-constexpr int kPlainThreads = 64;   // App. A: "We fixed the number of threads per block to 64"
+constexpr int kPlainThreads = 64;   // App. A: 64 threads per block in the paper's execution form
 
 struct PlainBufs {
   float *R, *r, *cphi, *Sb, *Qb, *vint2, *Sd0, *Sd1, *f;   // [N] each, f [4][N]

@@ -96,8 +96,15 @@ class Model:
         return _lib.lib().bang_model_psf_halfwidth(self._h, g)
 
     def _gal_idx(self, gal_idx, B):
+        """(array, pointer) of gal_idx: a host numpy copy, or a CUDA int32 tensor passed as
+        its device pointer (the library then schedules the batch on the device)."""
         if gal_idx is None:
             return None, None
+        if isinstance(gal_idx, torch.Tensor) and gal_idx.is_cuda:
+            if gal_idx.dtype != torch.int32 or gal_idx.numel() != B:
+                raise ValueError(f"a device gal_idx must be int32 [{B}]")
+            gi = gal_idx.contiguous()
+            return gi, ctypes.c_void_p(gi.data_ptr())
         gi = np.ascontiguousarray(np.asarray(gal_idx, dtype=np.int32).reshape(B))
         return gi, ctypes.c_void_p(gi.ctypes.data)
 

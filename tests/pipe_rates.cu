@@ -1,11 +1,11 @@
 // Per-SM issue rates of the SFU approximations (ex2, lg2, rcp, rsqrt) and of FFMA on the
-// GPU it runs on: the denominators of the forward kernel's SFU roofline.
+// GPU it runs on: the denominators of the likelihood kernels' SFU and FP32 rooflines.
 //
 // Each thread runs 8 independent chains of one PTX instruction (plus one FP32 operation
 // that keeps the chain from folding), 4096 iterations, two blocks of 1024 threads per SM.
-// The total rate is instructions / CUDA-event time; pipe_rates.py divides it by the SM
-// count and the SM clock sampled during the run.  Bounded loops, no waits.  Prints one
-// JSON object.
+// The total rate is instructions / CUDA-event time; test_gpu_pipe_rates.py divides it by
+// the SM count and the SM clock sampled during the run.  Bounded loops, no waits.  Prints
+// one JSON object.  Test infrastructure: not part of the library.
 #include <cuda_runtime.h>
 
 #include <cstdio>

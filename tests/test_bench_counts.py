@@ -1,6 +1,6 @@
 """bench.py's algorithmic operation counts and peaks (the roofline denominators): the
-per-point SFU and FP32 counts of the forward path as documented, the row-subset counts,
-and the peak arithmetic from the measured per-SM rates."""
+per-point SFU and FP32 counts of the forward and gradient paths as documented, the
+row-subset counts, and the roofline arithmetic from the measured per-SM rates."""
 import math
 import os
 import sys
@@ -16,8 +16,25 @@ from paper_2205_06819_gb300 import synth  # noqa: E402
 def test_padded_points_and_sfu_count_of_the_batched_workload():
     wl = synth.workload("batched")
     assert bench.points_per_eval(wl.galaxies[0]) == 430 * 430          # 80 x 5 + 2 x 15
+    # forward: per node one lg2 and one ex2; per point 13 half-rate and 4 ex2 (one disc)
     per_eval = bench.algorithmic_sfu_ops(wl) / wl.batch
-    assert per_eval == 430 * 430 * (2 * 64 + 16)
+    assert per_eval == 430 * 430 * (64 + 13 + 64 + 4)
+    ops, cyc = bench.sfu_work(wl)
+    assert cyc / wl.batch == pytest.approx(430 * 430 * ((64 + 13) / 16 + (64 + 4) / 32), rel=1e-12)
+
+
+def test_sfu_count_of_the_gradient_step():
+    """logL + gradient = the forward seed pass plus the adjoint: per node one lg2 and two ex2
+    (q^(g-4) and u/w), per point 18 half-rate and 4 ex2 (one disc); two discs add half a
+    half-rate and one ex2 per point to each pass."""
+    wl = synth.workload("adjoint")
+    ops, cyc = bench.sfu_work(wl, grad=True)
+    fwd = 430 * 430 * ((64 + 13) / 16 + (64 + 4) / 32)
+    adj = 430 * 430 * ((64 + 18) / 16 + (128 + 4) / 32)
+    assert cyc / wl.batch == pytest.approx(fwd + adj, rel=1e-12)
+    assert ops / wl.batch == 430 * 430 * (64 + 13 + 64 + 4 + 64 + 18 + 128 + 4)
+    assert bench.sfu_ops_per_point(128, 2, True) == {"half": 128 + 18.5, "full": 256 + 5}
+    assert bench.sfu_ops_per_point(128, 2, False) == {"half": 128 + 13.5, "full": 128 + 5}
 
 
 def test_fp32_count_of_the_batched_and_largest_workloads():
@@ -37,13 +54,22 @@ def test_row_subsets_of_an_uneven_batch():
     wl = synth.workload("uneven")
     gi = [0] * 3 + [5] * 2
     per = [bench.points_per_eval(g) for g in wl.galaxies]
-    assert bench.algorithmic_sfu_ops(wl, gi, 5) == (3 * per[0] + 2 * per[5]) * (2 * 64 + 16)
+    assert bench.algorithmic_sfu_ops(wl, gi, 5) == (3 * per[0] + 2 * per[5]) * (64 + 13 + 64 + 4)
 
 
-def test_sfu_peak_from_the_per_sm_rates():
-    # one lg2 (16/clk) and one ex2 (32/clk) per node: 2 ops per 3/32 SM-cycles
-    peak = bench.sfu_peak_ops_per_s(64, 2070.0, 152)
-    assert peak == pytest.approx(152 * 2070e6 * 2 / (1 / 16 + 1 / 32), rel=1e-12)
+def test_roofline_block_arithmetic():
+    """frac = the SFU time of the step's operations at the per-SM issue rates over the
+    measured time; peak = operations over that time."""
+    wl = synth.workload("batched")
+    t_sfu = 1024 * 430 * 430 * ((64 + 13) / 16 + (64 + 4) / 32) / (152 * 2070e6)
+    r = bench.roofline_block(wl, 2.0 * t_sfu, mhz=2070.0, sms=152)
+    assert r["frac"] == pytest.approx(0.5, rel=1e-12)
+    ops = 1024 * 430 * 430 * 145
+    assert r["peak"] == pytest.approx(ops / t_sfu / 1e9, rel=1e-12)
+    assert r["achieved"] == pytest.approx(r["peak"] / 2, rel=1e-12)
+    assert r["sfu_sm_cycles_per_point"] == pytest.approx((64 + 13) / 16 + (64 + 4) / 32, rel=1e-12)
+    g = bench.roofline_block(synth.workload("adjoint"), 1e-3, grad=True, mhz=2070.0, sms=152)
+    assert g["frac"] > 0 and g["fp32"]["frac"] > 0
 
 
 def test_cpu_baseline_parity_sample():

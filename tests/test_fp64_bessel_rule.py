@@ -1,10 +1,12 @@
 """The rule the float64 check path (bang_fp64.cu) uses for the modified Bessel functions of
 the second kind, restated on the host and pinned against an independent library:
 K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt by the trapezoid rule with step 0.1
-(0.1 sqrt(10 / x) beyond x = 10), cut where x cosh t > 745.  The device code itself is
-checked on the GPU through the whole likelihood (tests/test_gpu_fp64.py, chi^2 to 1e-11
-of the float64 oracle); this pins the rule's accuracy claim (< 2e-14 relative on
-[1e-6, 200]) and the Freeman difference I0 K0 - I1 K1 built from it."""
+(0.1 sqrt(10 / x) beyond x = 10), cut where x cosh t > 745; and, beyond y = 25, the
+large-argument expansion of I0 K0 - I1 K1 (DLMF 10.40.6 for each product), pinned against
+mpmath in 40-digit arithmetic up to y = 1e4, where the direct form overflows.  The device
+code itself is checked on the GPU through the whole likelihood (tests/test_gpu_fp64.py,
+chi^2 to 1e-11 of the float64 oracle); this pins the rule's accuracy claim (< 2e-14
+relative on [1e-6, 200]) and the Freeman difference I0 K0 - I1 K1 built from it."""
 import math
 
 import numpy as np
@@ -54,3 +56,28 @@ def test_a_coarser_step_would_fail():
     w[0] = 0.5
     k0 = h * np.sum(w * np.exp(-x * np.cosh(t)))
     assert abs(k0 / sp.k0(x) - 1.0) > 1e-6
+
+
+def freeman_series(y: float) -> float:
+    z2 = 1.0 / (4.0 * y * y)
+    s, c, p0, p1, zk = 0.0, 1.0, 1.0, 1.0, 1.0
+    for k in range(1, 13):
+        o = (2.0 * k - 1.0) ** 2
+        c *= (2.0 * k - 1.0) / (2.0 * k)
+        p0 *= -o
+        p1 *= 4.0 - o
+        zk *= z2
+        s += (-c if k & 1 else c) * (p0 - p1) * zk
+    return s / (2.0 * y)
+
+
+def test_freeman_large_argument_expansion_against_mpmath():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for y in (25.0, 25.5, 30.0, 60.0, 300.0, 699.0, 750.0, 5000.0, 1e4):
+        ref = mp.besseli(0, y) * mp.besselk(0, y) - mp.besseli(1, y) * mp.besselk(1, y)
+        assert abs(freeman_series(y) / float(ref) - 1.0) < 1e-15, y
+    # leading terms 1 / (4 y^3) (1 + 9 / (8 y^2)); continuity with the Bessel-function form at the switch
+    assert abs(freeman_series(1e4) * 4e12 / (1.0 + 9.0 / 8e8) - 1.0) < 1e-15
+    k0, k1, _ = k01_rule(25.0)
+    assert abs((sp.i0(25.0) * k0 - sp.i1(25.0) * k1) / freeman_series(25.0) - 1.0) < 1e-12

@@ -1,8 +1,8 @@
 """Golden values printed in the paper (tests/golden/ngc7683_fit_tables.json, cited there):
-the NGC 7683 fit tables.  They pin the reading of the parameter layout: masses are log10 of
-Msun and the visible mass is bulge + inner disc + outer disc, which reproduces the total
-visible masses the text states for both fits; and the prior ranges this library's inputs
-use for the paper's own slots."""
+the NGC 7683 fit tables of Sec. 3.1 and App. C.  They pin two inputs of this library to the
+paper: the prior ranges synth.prior_box uses for the paper's own slots, and the paper-like
+parameter vector synth.NGC7683_LIKE (the SPS fit's posterior medians), from which
+fit.truth_two_discs builds the synthetic galaxy of the model-selection run."""
 import json
 import math
 import os
@@ -18,21 +18,6 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 def golden():
     with open(os.path.join(HERE, "golden", "ngc7683_fit_tables.json")) as f:
         return json.load(f)
-
-
-@pytest.mark.parametrize("fit", ["sps_fit", "colour_fit"])
-def test_visible_mass_is_the_sum_of_the_three_components(golden, fit):
-    t = golden[fit]
-    total = sum(10 ** t[k] for k in ("logMb", "logMd1", "logMd2"))
-    stated = golden["stated_total_visible_mass"][fit]
-    # three masses rounded to 0.005 dex (1.2%) and a total stated to 3 digits
-    assert total == pytest.approx(stated, rel=0.01)
-
-
-def test_fits_agree_within_a_few_percent(golden):
-    a, b = golden["sps_fit"], golden["colour_fit"]
-    for k in ("MLd1", "MLd2", "k1", "k2", "sin_i"):
-        assert abs(a[k] - b[k]) / abs(a[k]) < 0.08, k
 
 
 def test_prior_box_uses_the_papers_ranges_for_its_own_slots(golden):

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2205_06819_gb300 import synth  # noqa: E402
 
-from bang_testdata import Dataset, theta_batch  # noqa: E402
+from bang_testdata import Dataset, assert_grad_close, theta_batch  # noqa: E402
 
 CHI2_RTOL = 1e-5
 GRAD_RTOL = 1e-4
@@ -62,7 +62,7 @@ def test_logl_gradient_maps_plain(lib, kind, nd, spec):
     _, gref = oracle.loglike_grad(ds.og, theta.astype(np.float32).astype(np.float64), n_discs=nd, bulge_kind=kind)
     assert np.all(g[:, 6] == 0.0)
     for k in range(theta.shape[0]):
-        assert np.abs(g[k] - gref[k]).max() <= GRAD_RTOL * np.linalg.norm(gref[k]), k
+        assert_grad_close(g[k], gref[k], k)
     maps = [x.cpu().numpy() for x in m.maps(t[:2])]
     for b in range(2):
         ref = ds.oracle_maps(theta[b])

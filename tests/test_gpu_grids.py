@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2205_06819_gb300 import synth  # noqa: E402
 
-from bang_testdata import Dataset, theta_batch  # noqa: E402
+from bang_testdata import Dataset, assert_grad_close, theta_batch  # noqa: E402
 
 CHI2_RTOL = 1e-5
 GRAD_RTOL = 1e-4
@@ -66,7 +66,7 @@ def test_grids_match_the_oracle_sum(setup):
     assert (np.abs(chi - chi_ref) / chi_ref).max() < CHI2_RTOL
     g = g.cpu().numpy()
     for k in range(theta.shape[0]):
-        assert np.abs(g[k] - g_ref[k]).max() <= GRAD_RTOL * np.linalg.norm(g_ref[k]), k
+        assert_grad_close(g[k], g_ref[k], k)
     np.testing.assert_allclose(m.loglike_grids(t, [0, 1, 2]).cpu().numpy(), logL.cpu().numpy(), rtol=1e-6)
 
 

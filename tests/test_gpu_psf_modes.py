@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2205_06819_gb300 import synth  # noqa: E402
 
-from bang_testdata import Dataset, theta_batch  # noqa: E402
+from bang_testdata import Dataset, assert_grad_close, theta_batch  # noqa: E402
 
 CHI2_RTOL = 1e-5
 GRAD_RTOL = 1e-4
@@ -68,7 +68,7 @@ def test_logl_and_gradient(lib, name):
     g = g.cpu().numpy()
     _, gref = oracle.loglike_grad(ds.og, theta.astype(np.float64), n_discs=nd)
     for k in range(theta.shape[0]):
-        assert np.abs(g[k] - gref[k]).max() <= GRAD_RTOL * np.linalg.norm(gref[k]), (name, k)
+        assert_grad_close(g[k], gref[k], (name, k))
 
 
 @pytest.mark.parametrize("name", ["circle_os3", "centre_os4", "flux_os3", "all_two_discs_os2"])

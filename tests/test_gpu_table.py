@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2205_06819_gb300 import synth  # noqa: E402
 
-from bang_testdata import Dataset, theta_batch  # noqa: E402
+from bang_testdata import Dataset, assert_grad_close, theta_batch  # noqa: E402
 
 CHI2_RTOL = 1e-5
 GRAD_RTOL = 1e-4
@@ -58,9 +58,7 @@ def check(Model, ds, theta, T=1024, grad=False):
         g = g.cpu().numpy()
         th = theta[fin].astype(np.float64)
         _, gref = oracle.loglike_grad(ds.og, th, n_discs=ds.n_discs, n_quad=ds.n_quad)
-        for k in range(gref.shape[0]):
-            nrm = np.linalg.norm(gref[k])
-            assert np.abs(g[fin][k] - gref[k]).max() <= GRAD_RTOL * nrm
+        assert_grad_close(g[fin], gref, "table")
         assert np.all(g[~fin] == 0)
 
 

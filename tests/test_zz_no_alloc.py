@@ -1,12 +1,15 @@
-"""The no-allocation entry point, bang_loglike_batch_noalloc, checked against
-bang_loglike_batch through the C ABI.
+"""The no-allocation entry point, bang_loglike_batch_noalloc, checked through the C ABI
+against bang_loglike_batch and against the float64 oracle.
 
 That entry point is for callers that must not allocate device memory while they run (a
 program whose GPU memory belongs to another allocator, or a loop that cannot take the
 synchronisation cudaMalloc may cause): its scratch is a fixed array in the library's
 device code.  Two calls in a row, on different batches, must each give the logL of the
 allocating entry point within the chi-square tolerance of the other GPU tests (1e-5
-relative), and an oversized batch must be refused before anything is launched.
+relative); so must a batch that mixes two galaxies of different grid sizes through a host
+gal_idx array.  Its chi^2 must match the oracle's at the same tolerance, a call on a warm
+device must leave the free device memory and the model's scratch exactly as they were,
+and an oversized batch must be refused before anything is launched.
 This file is named so that pytest collects it last.
 """
 import ctypes
@@ -42,8 +45,9 @@ def setup():
     return _lib, m, box, synth
 
 
-def noalloc(_lib, m, theta, logL):
-    return _lib.lib().bang_loglike_batch_noalloc(m.handle, ctypes.c_void_p(theta.data_ptr()), None, theta.shape[0],
+def noalloc(_lib, m, theta, logL, gal_idx=None):
+    gptr = None if gal_idx is None else ctypes.c_void_p(gal_idx.ctypes.data)
+    return _lib.lib().bang_loglike_batch_noalloc(m.handle, ctypes.c_void_p(theta.data_ptr()), gptr, theta.shape[0],
                                                  ctypes.c_void_p(logL.data_ptr()),
                                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
@@ -96,4 +100,72 @@ def test_noalloc_under_model_options(setup, opts):
     fin = np.isfinite(ref)
     assert np.array_equal(fin, np.isfinite(got)) and fin.any()
     assert (np.abs(got[fin] - ref[fin]) / np.abs(ref[fin])).max() < CHI2_RTOL
+    m.close()
+
+
+def test_noalloc_chi2_matches_oracle(setup):
+    """The entry point against the float64 oracle directly (chi^2, the theta-dependent part
+    of logL), on the model's own data."""
+    import oracle
+    oracle.build()
+    _lib, m, box, synth = setup
+    g = m.galaxies[0]
+    og = oracle.Galaxy(g.nx, g.ny, g.oversample, g.psf_fwhm_arcsec, g.kpc_per_arcsec,
+                       data=np.asarray(g.data, np.float64), err=np.asarray(g.err, np.float64), mask=g.mask)
+    theta_np = synth.draw_theta_batch(box, TH1, 6, 96).astype(np.float32)
+    theta = torch.from_numpy(theta_np).cuda()
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    _lib.check(noalloc(_lib, m, theta, out))
+    _, chi_ref = oracle.loglike(og, theta_np.astype(np.float64))
+    chi = -2.0 * (out.cpu().numpy() + oracle.norm_const(og))
+    assert (np.abs(chi - chi_ref) / chi_ref).max() < CHI2_RTOL
+
+
+def test_noalloc_leaves_device_memory_unchanged(setup):
+    """After a first call on the device (which looks up the scratch array), a second call with
+    a different batch size changes neither the device's free memory nor the model's scratch."""
+    _lib, m, box, synth = setup
+    L = _lib.lib()
+    th = torch.from_numpy(synth.draw_theta_batch(box, TH1, 300, 97).astype(np.float32)).cuda()
+    out = torch.zeros(300, dtype=torch.float64, device="cuda")
+    _lib.check(noalloc(_lib, m, th, out))
+    torch.cuda.synchronize()
+    free0, scratch0 = torch.cuda.mem_get_info()[0], L.bang_model_scratch_bytes(m.handle)
+    th2, out2 = th[:123], out[:123]
+    _lib.check(noalloc(_lib, m, th2, out2))
+    _lib.check(noalloc(_lib, m, th2, out2))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert L.bang_model_scratch_bytes(m.handle) == scratch0
+    assert torch.isfinite(out2).any()
+
+
+def test_noalloc_two_galaxies_with_host_gal_idx(setup):
+    """A model of two galaxies with different grids and PSFs and a mixed host gal_idx: the
+    gal_idx copy into the scratch array, the per-row galaxy lookup and the shared-memory size
+    taken over the batch's galaxies, against bang_loglike_batch with the same gal_idx."""
+    _lib, m0, box, synth = setup
+    from paper_2205_06819_gb300.model import Galaxy, Model
+    g0 = m0.galaxies[0]
+    spec = synth.GalaxySpec(34, 27, 4, 3.1)
+    ones = np.ones((4, spec.ny, spec.nx), np.float32)
+    probe = Model(Galaxy(spec.nx, spec.ny, spec.oversample, spec.psf_fwhm_arcsec, spec.kpc_per_arcsec, ones, ones))
+    true = probe.maps(torch.from_numpy(TH1.astype(np.float32)[None]).cuda())[0].cpu().numpy()
+    probe.close()
+    data, err, mask = synth.noisy_data(true, seed=98)
+    g1 = Galaxy(spec.nx, spec.ny, spec.oversample, spec.psf_fwhm_arcsec, spec.kpc_per_arcsec, data, err, mask)
+    m = Model([g0, g1])
+    B = 96
+    gal_idx = np.random.default_rng(99).integers(0, 2, size=B).astype(np.int32)
+    theta = torch.from_numpy(synth.draw_theta_batch(box, TH1, B, 100).astype(np.float32)).cuda()
+    for call in range(2):
+        gi = gal_idx if call == 0 else np.ascontiguousarray(1 - gal_idx)
+        out = torch.zeros(B, dtype=torch.float64, device="cuda")
+        _lib.check(noalloc(_lib, m, theta, out, gi))
+        torch.cuda.synchronize()
+        ref = m.loglike(theta, gi).cpu().numpy()
+        got = out.cpu().numpy()
+        fin = np.isfinite(ref)
+        assert fin.sum() > B // 2 and np.array_equal(fin, np.isfinite(got))
+        assert (np.abs(got[fin] - ref[fin]) / np.abs(ref[fin])).max() < CHI2_RTOL, call
     m.close()
