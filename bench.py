@@ -189,19 +189,32 @@ def points_per_eval(spec: synth.GalaxySpec) -> int:
 
 # SFU (MUFU) operations per padded fine point, by issue class: "half" are the functions the
 # SFU issues at 16 per clock per SM (lg2, rcp, rsqrt, sqrt), "full" is ex2 (32 per clock).
-#  forward (eval_point): per radial node one lg2 and one ex2 (q^(g-4); q^(2g-7) = (q^(g-4))^2 q
-#    by multiplications); per point 13 + (n_discs - 1) / 2 half-rate (the bulge's 1/(x+1) and
-#    log2 w, sqrt R, rsqrt r2, the bulge velocity's 1/(x+1) and log2 u, the NFW m(x) (two
-#    reciprocals, or a log and a reciprocal), a disc fit's log for y <= 1 (half the points),
-#    sqrt v, 1/B, sqrt sigma^2, 1/Sigma) and 3 + n_discs ex2 (the bulge's two per-point powers,
-#    the bulge velocity power, each disc's exponential);
+#  forward (eval_point): per radial node below the series split K (TAIL_SPLIT) one lg2 and
+#    one ex2 (q^(g-4); q^(2g-7) = (q^(g-4))^2 q by multiplications); the nodes from K on as a
+#    series in 1 / w (one reciprocal and the two powers w^(g-4), w^(2g-7)); per point 13 +
+#    (n_discs - 1) / 2 half-rate (the bulge's 1/(x+1) and log2 w, sqrt R, rsqrt r2, the bulge
+#    velocity's 1/(x+1) and log2 u, the NFW m(x) (two reciprocals, or a log and a
+#    reciprocal), a disc fit's log for y <= 1 (half the points), sqrt v, 1/B, sqrt sigma^2,
+#    1/Sigma) and 3 + n_discs ex2 (the bulge's two per-point powers, the bulge velocity power,
+#    each disc's exponential).  The few points within ~0.2 bulge scales of the centre that
+#    take every node one by one are counted as the others;
 #  adjoint (point_vjp): per radial node one lg2 and two ex2 (q^(g-4) and u/w); per point the
 #    forward recomputation's operations plus 1/(3-g), 1/R (twice), 1/(1+x) of the halo
 #    derivative, the two divisions of the reverse sweep: 18 + (n_discs - 1) / 2 half-rate and
 #    3 + n_discs ex2.
+TAIL_SPLIT = {64: 24, 128: 48}   # first radial node of the forward kernel's series (TailRule)
+
+
 def sfu_ops_per_point(n_quad: int, n_discs: int, adjoint: bool = False) -> dict:
     if adjoint:
         return {"half": n_quad + 18.0 + 0.5 * (n_discs - 1), "full": 2.0 * n_quad + 3.0 + n_discs}
+    k = TAIL_SPLIT[n_quad]
+    return {"half": k + 14.0 + 0.5 * (n_discs - 1), "full": k + 5.0 + n_discs}
+
+
+def sfu_ops_per_point_node_by_node(n_quad: int, n_discs: int) -> dict:
+    """The forward pass's SFU operations with every radial node evaluated one by one (the
+    plain form of the same sum)."""
     return {"half": n_quad + 13.0 + 0.5 * (n_discs - 1), "full": n_quad + 3.0 + n_discs}
 
 
@@ -231,9 +244,10 @@ def algorithmic_sfu_ops(wl: synth.Workload, gal_idx=None, rows: int | None = Non
 
 
 def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = None, grad: bool = False) -> float:
-    """FP32 instructions of one batch: per padded fine point 6 per radial node (the argument
-    of the logarithm, the exponent, and the two weighted sums with the (q^(g-4))^2 q
-    product) plus ~200 for geometry, velocities, discs and light weighting; per galaxy the
+    """FP32 instructions of one batch: per padded fine point 6 per radial node below the
+    series split (the argument of the logarithm, the exponent, and the two weighted sums with
+    the (q^(g-4))^2 q product), 16 lane operations for the series (eight two-lane Horner
+    steps) and ~200 for geometry, velocities, discs and light weighting; per galaxy the
     PSF stencil (separable: 4 channels x (fine rows x nx + nx x ny) x (os + 2h); two-
     dimensional: 4 x nx x ny x (os + 2h)^2) and ~40 per spaxel for the chi-square.  A
     gradient step adds the adjoint pass: per point 13 per radial node (the six sums) and ~400
@@ -247,7 +261,7 @@ def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = No
             psf = 4.0 * spec.nx * spec.ny * L * L
         else:
             psf = 4.0 * ((spec.oversample * spec.ny + 2 * h) * spec.nx + spec.nx * spec.ny) * L
-        fwd = points_per_eval(spec) * (6.0 * wl.n_quad + 200.0) + psf + 40.0 * spec.nx * spec.ny
+        fwd = points_per_eval(spec) * (6.0 * TAIL_SPLIT[wl.n_quad] + 16.0 + 200.0) + psf + 40.0 * spec.nx * spec.ny
         if grad:
             fwd += points_per_eval(spec) * (13.0 * wl.n_quad + 400.0) + psf
         return fwd
@@ -275,17 +289,28 @@ def rank_batch_seed(workload_id: int, rank: int) -> int:
 
 def roofline_block(wl: synth.Workload, step_s: float, gal_idx=None, rows: int | None = None, grad: bool = False,
                    mhz: float = SM_MAX_MHZ_NOMINAL, sms: int = SM_COUNT_NOMINAL) -> dict:
-    """The SFU roofline of one timed step: achieved = algorithmic SFU operations / step time;
-    peak = the same operations over the time the SFU needs for them at the measured per-SM
-    issue rates of their classes (sms x clock); frac = that time / the measured time.  The FP32
-    count against the measured FFMA rate is reported beside it."""
+    """The roofline of one timed step over its two arithmetic pipes: achieved = algorithmic SFU
+    operations / step time; peak = the same operations over the time the SFU needs for them
+    at the measured per-SM issue rates of their classes (sms x clock); sfu_frac = that time /
+    the measured time, fp32.frac the same for the FP32 count against the measured FFMA rate,
+    frac = the larger of the two (the pipe that bounds the step).  node_by_node_sfu_frac is
+    the SFU time the same step would need with every radial node evaluated one by one, over
+    the measured time (above 1 when the series beats that SFU bound)."""
     ops, cyc = sfu_work(wl, gal_idx, rows, grad)
     t_sfu = cyc / (sms * mhz * 1e6)
     fp32 = algorithmic_fp32_ops(wl, gal_idx, rows, grad)
     fp32_peak = sms * mhz * 1e6 * FP32_PER_CLK_SM
     t_fp32 = fp32 / fp32_peak
+    pts = _batch_points(wl, gal_idx, rows)
+    nbn = sfu_ops_per_point_node_by_node(wl.n_quad, wl.n_discs)
+    t_nbn = pts * (nbn["half"] / MUFU_LG2_PER_CLK_SM + nbn["full"] / MUFU_EX2_PER_CLK_SM) / (sms * mhz * 1e6)
+    if grad:
+        c = sfu_ops_per_point(wl.n_quad, wl.n_discs, True)
+        t_nbn += pts * (c["half"] / MUFU_LG2_PER_CLK_SM + c["full"] / MUFU_EX2_PER_CLK_SM) / (sms * mhz * 1e6)
     return {"bound": "alu", "achieved": ops / step_s / 1e9, "peak": ops / t_sfu / 1e9, "unit": "G SFU op/s",
-            "frac": t_sfu / step_s,
+            "frac": max(t_sfu, t_fp32) / step_s,
+            "sfu_frac": t_sfu / step_s,
+            "node_by_node_sfu_frac": t_nbn / step_s,
             "fp32": {"achieved": fp32 / step_s / 1e9, "peak": fp32_peak / 1e9, "unit": "G FP32 lane-op/s",
                      "frac": t_fp32 / step_s},
             "t_roof_over_t_meas": max(t_sfu, t_fp32) / step_s,

@@ -79,9 +79,57 @@ struct BulgeDer {
   float Sb, Qb, dSb_dR, dQb_dR, dSb_da, dQb_da, dSb_dg, dQb_dg;
 };
 
-template <int NQ>
-__device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, float R, const float4* nw = nullptr) {
+// Nodes [K0, K1) of the six sums (paired weights, packed two-lane instructions): even and
+// odd nodes accumulate in the two lanes.
+template <int NQ, int K0, int K1>
+__device__ __forceinline__ void adj_node_pairs(const ModelConst& m, const float4* __restrict__ nw, float w,
+                                               float2& S2, float2& Su2, float2& Sl2, float2& Q2, float2& Qu2,
+                                               float2& Ql2) {
   constexpr int base = NodeBase<NQ>::value;
+  const float2 w2 = make_float2(w, w), g2 = make_float2(m.g4, m.g4), one2 = make_float2(1.0f, 1.0f);
+  const float2 neg2 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+  for (int k = K0; k < K1; k += 2) {
+    const float2 q = __ffma2_rn(w2, make_float2(kNodeCm1[base + k], kNodeCm1[base + k + 1]), one2);
+    const float2 d = make_float2(lg2_approx(q.x), lg2_approx(q.y));
+    float4 wk;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(wk.x), "=f"(wk.y), "=f"(wk.z), "=f"(wk.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(nw + k / 2)));
+    const float2 t = __fmul2_rn(g2, d);
+    const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));   // q^(g-4); q^(2g-7) = e^2 q
+    const float2 t1 = __fmul2_rn(make_float2(wk.x, wk.y), e);
+    const float2 t2 = __fmul2_rn(__fmul2_rn(make_float2(wk.z, wk.w), e), __fmul2_rn(e, q));
+    const float2 mk = __ffma2_rn(d, neg2, make_float2(kNodeLc[base + k], kNodeLc[base + k + 1]));   // log2(u / w)
+    const float2 uw = make_float2(ex2_approx(mk.x), ex2_approx(mk.y));                             // u / w
+    S2 = __fadd2_rn(S2, t1);
+    Su2 = __ffma2_rn(t1, uw, Su2);
+    Sl2 = __ffma2_rn(t1, mk, Sl2);
+    Q2 = __fadd2_rn(Q2, t2);
+    Qu2 = __ffma2_rn(t2, uw, Qu2);
+    Ql2 = __ffma2_rn(t2, mk, Ql2);
+  }
+}
+
+// Horner of one packed coefficient set (kTailTerms pairs in shared memory) at u.
+__device__ __forceinline__ float2 tail_poly(const float2* __restrict__ c, float2 u2) {
+  float2 P;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(P.x), "=f"(P.y)
+               : "r"((unsigned)__cvta_generic_to_shared(c + kTailTerms - 1)));
+#pragma unroll
+  for (int j = kTailTerms - 2; j >= 0; --j) {
+    float2 cj;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(cj.x), "=f"(cj.y)
+                 : "r"((unsigned)__cvta_generic_to_shared(c + j)));
+    P = __ffma2_rn(P, u2, cj);
+  }
+  return P;
+}
+
+template <int NQ>
+__device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, float R, const float4* nw = nullptr,
+                                                         const float2* tail = nullptr) {
+  constexpr int base = NodeBase<NQ>::value, K = TailRule<NQ>::K;
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
   const float ix1 = rcp_approx(xp1);
@@ -94,34 +142,15 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
   // u_k = r_k / (r_k + a) = w 2^(lc_k - d_k): the per-point factors w and log2 w are taken
   // out of the sums, which carry t u / w and t (log2 u - log2 w)
   float S = 0.f, Su = 0.f, Sl = 0.f, Q = 0.f, Qu = 0.f, Ql = 0.f;
+  bool series = false;
   if (nw) {
     // per-model node factors folded into shared-memory weights, two nodes at a time in
-    // packed two-lane FP32 instructions (see bulge_projected_w); even and odd nodes
-    // accumulate in the two lanes
-    const float2 w2 = make_float2(w, w), g2 = make_float2(m.g4, m.g4), one2 = make_float2(1.0f, 1.0f);
-    const float2 neg2 = make_float2(-1.0f, -1.0f);
+    // packed two-lane FP32 instructions (see bulge_projected_w); with the series
+    // coefficients, the upper nodes of points away from the centre come from the series
     float2 S2 = make_float2(0.f, 0.f), Su2 = S2, Sl2 = S2, Q2 = S2, Qu2 = S2, Ql2 = S2;
-#pragma unroll
-    for (int k = 0; k < NQ; k += 2) {
-      const float2 q = __ffma2_rn(w2, make_float2(kNodeCm1[base + k], kNodeCm1[base + k + 1]), one2);
-      const float2 d = make_float2(lg2_approx(q.x), lg2_approx(q.y));
-      float4 wk;
-      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                   : "=f"(wk.x), "=f"(wk.y), "=f"(wk.z), "=f"(wk.w)
-                   : "r"((unsigned)__cvta_generic_to_shared(nw + k / 2)));
-      const float2 t = __fmul2_rn(g2, d);
-      const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));   // q^(g-4); q^(2g-7) = e^2 q
-      const float2 t1 = __fmul2_rn(make_float2(wk.x, wk.y), e);
-      const float2 t2 = __fmul2_rn(__fmul2_rn(make_float2(wk.z, wk.w), e), __fmul2_rn(e, q));
-      const float2 mk = __ffma2_rn(d, neg2, make_float2(kNodeLc[base + k], kNodeLc[base + k + 1]));   // log2(u / w)
-      const float2 uw = make_float2(ex2_approx(mk.x), ex2_approx(mk.y));                             // u / w
-      S2 = __fadd2_rn(S2, t1);
-      Su2 = __ffma2_rn(t1, uw, Su2);
-      Sl2 = __ffma2_rn(t1, mk, Sl2);
-      Q2 = __fadd2_rn(Q2, t2);
-      Qu2 = __ffma2_rn(t2, uw, Qu2);
-      Ql2 = __ffma2_rn(t2, mk, Ql2);
-    }
+    series = tail && w * kNodeCm1[base + K] >= kTailZ;
+    if (series) adj_node_pairs<NQ, 0, K>(m, nw, w, S2, Su2, Sl2, Q2, Qu2, Ql2);
+    else adj_node_pairs<NQ, 0, NQ>(m, nw, w, S2, Su2, Sl2, Q2, Qu2, Ql2);
     S = S2.x + S2.y;
     Su = Su2.x + Su2.y;
     Sl = Sl2.x + Sl2.y;
@@ -152,6 +181,18 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
   Qu *= w;
   Sl = fmaf(lw, S, Sl);
   Ql = fmaf(lw, Q, Ql);
+  if (series) {   // the upper nodes: w^n times the three polynomials in 1 / w (fill_tail_coeffs_adj)
+    const float2 u2 = make_float2(xp1 * rcp_approx(x), xp1 * rcp_approx(x));
+    const float2 P0 = tail_poly(tail, u2), P1 = tail_poly(tail + kTailTerms, u2),
+                 P2 = tail_poly(tail + 2 * kTailTerms, u2);
+    const float pwS = ex2_approx(m.g4 * lw), pwQ = ex2_approx(fmaf(2.0f, m.g4, 1.0f) * lw);   // w^(g-4), w^(2g-7)
+    S = fmaf(pwS, P0.x, S);
+    Q = fmaf(pwQ, P0.y, Q);
+    Su = fmaf(pwS, P1.x, Su);
+    Qu = fmaf(pwQ, P1.y, Qu);
+    Sl = fmaf(pwS, P2.x, Sl);
+    Ql = fmaf(pwQ, P2.y, Ql);
+  }
   const float fS = m.cS * x * pS, fQ = m.cQ * pQ;
   const float g = -m.ngam;
   const float inv3g = rcp_approx(m.three_mg);
@@ -209,7 +250,7 @@ __device__ __forceinline__ BulgeDer bulge_closed_vjp(const ModelConst& m, float 
 // Vector-Jacobian product of one fine point: adds sum_c a_c d f_c / d(constants) to acc.
 template <int NQ, int ND>
 __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y, float4 a, float* acc,
-                                          const float* tab, int T, const float4* nodew) {
+                                          const float* tab, int T, const float4* nodew, const float2* tail) {
   // ---- forward (Sec. 2.1-2.4), keeping what the reverse sweep needs
   const float xr = fmaf(X, m.cpa, Y * m.spa);
   const float yr = fmaf(Y, m.cpa, -X * m.spa);
@@ -224,7 +265,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
   const float cphi = xr * inv_r;
 
   const BulgeDer bd = tab ? bulge_table_vjp(m, tab, T, R)
-                           : (m.bulge_fit ? bulge_closed_vjp(m, R) : bulge_projected_vjp<NQ>(m, R, nodew));
+                           : (m.bulge_fit ? bulge_closed_vjp(m, R) : bulge_projected_vjp<NQ>(m, R, nodew, tail));
 
   const float xa = r * m.inv_a;
   const float ub = xa * rcp_approx(xa + 1.0f);
@@ -404,6 +445,7 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int next_item;
   __shared__ float4 nodew[NQ / 2];
+  __shared__ float2 tailc[3 * kTailTerms];
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
   for (int it = blockIdx.x; it < a.n_items;) {
@@ -474,8 +516,9 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
       const float* src = a.tables + (size_t)w.b * a.table_stride;
       const int nt = kTabHdr + 8 * a.table_T;
       for (int t = tid; t < nt; t += kAdjThreads) tab[t] = __ldg(src + t);
-    } else {
-      if (!mc.bulge_fit) fill_node_pairs<NQ>(mc, nodew, tid, kAdjThreads);
+    } else if (!mc.bulge_fit) {
+      fill_node_pairs<NQ>(mc, nodew, tid, kAdjThreads);
+      if (tid < 32) fill_tail_coeffs_adj<NQ>(mc, tailc, tid);
     }
 
     float acc[NACC];
@@ -552,7 +595,7 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
         }
         const float X = fmaf((float)qx, pk, mc.X0);
         const float Y = fmaf((float)y, pk, mc.Y0);
-        point_vjp<NQ, ND>(mc, X, Y, make_float4(sxy.x, sxy.y, szw.x, szw.y), acc, tab, a.table_T, nodew);
+        point_vjp<NQ, ND>(mc, X, Y, make_float4(sxy.x, sxy.y, szw.x, szw.y), acc, tab, a.table_T, nodew, tailc);
       }
     }
     // float64 block reduction of the adjoints, then theta-space gradient (one thread)
@@ -754,7 +797,15 @@ cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kin
 }
 
 cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq) {
+  float lm[192], lcm[192];   // the series' log tables, from the float32 m_k
+  for (int k = 0; k < 192; ++k) {
+    const double mk = (double)cm1[k];
+    lm[k] = (float)std::log2(mk);
+    lcm[k] = (float)std::log2(1.0 + 1.0 / mk);
+  }
   cudaError_t e = cudaMemcpyToSymbol(kNodeCm1, cm1, 192 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeLm, lm, sizeof lm);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeLcm, lcm, sizeof lcm);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeLc, lc, 192 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeWs, ws, 192 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeWq, wq, 192 * sizeof(float));

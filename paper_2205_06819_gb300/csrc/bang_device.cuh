@@ -34,6 +34,19 @@ static __constant__ float kNodeWq[192];
 
 template <int NQ> struct NodeBase { static constexpr int value = NQ == 64 ? 0 : 64; };
 
+// For the series coefficients (rows as above): log2 m_k and log2(cosh t_k / m_k), with m_k
+// the float32 cosh t_k - 1 of kNodeCm1 (computed in float64 on the host, then rounded).
+static __constant__ float kNodeLm[192];
+static __constant__ float kNodeLcm[192];
+
+// Split of the radial rule for the upper-node series (see fill_tail_coeffs): nodes k >= K
+// of points with w (cosh t_K - 1) >= kTailZ are summed by a kTailTerms-term series.
+template <int NQ> struct TailRule;
+template <> struct TailRule<64> { static constexpr int K = 24; };
+template <> struct TailRule<128> { static constexpr int K = 48; };
+constexpr int kTailTerms = 8;     // j = 0 .. 7
+constexpr float kTailZ = 16.0f;   // the series serves points with w (cosh t_K - 1) >= 16
+
 // One galaxy on the device.
 struct GalDev {
   int nx, ny, os, h;
@@ -453,23 +466,14 @@ __device__ __forceinline__ float table_plain(const float* __restrict__ tab, int 
 // instructions (one issue slot for both nodes, each lane rounded like fmaf), and one
 // 128-bit shared load brings the pair's four weights.  Even and odd nodes accumulate in
 // the two lanes, added at the end.
-template <int NQ>
-__device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const float4* __restrict__ nw, float R,
-                                                  float& Sigma, float& SigS2) {
+// Nodes [K0, K1) of the paired-weight sums (K0, K1 even).
+template <int NQ, int K0, int K1>
+__device__ __forceinline__ void node_pairs(const ModelConst& m, const float4* __restrict__ nw, float w, float2& S,
+                                           float2& Q) {
   constexpr int base = NodeBase<NQ>::value;
-  const float x = R * m.inv_a;
-  const float xp1 = x + 1.0f;
-  const float ix1 = rcp_approx(xp1);
-  const float w = x * ix1;
-  const float lw = lg2_approx(w);
-  const float i2 = ix1 * ix1;
-  const float ip4 = i2 * i2;
-  const float pS = ex2_approx(m.ngam * lw) * ip4;
-  const float pQ = ex2_approx(m.g3 * lw) * ip4;
   const float2 w2 = make_float2(w, w), g2 = make_float2(m.g4, m.g4), one2 = make_float2(1.0f, 1.0f);
-  float2 S = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int k = 0; k < NQ; k += 2) {
+  for (int k = K0; k < K1; k += 2) {
     const float2 q = __ffma2_rn(w2, make_float2(kNodeCm1[base + k], kNodeCm1[base + k + 1]), one2);
     const float2 d = make_float2(lg2_approx(q.x), lg2_approx(q.y));
     float4 wk;   // kept in the loop: hoisting 2 NQ invariant weights would exhaust the registers
@@ -481,8 +485,173 @@ __device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const flo
     S = __ffma2_rn(make_float2(wk.x, wk.y), e, S);
     Q = __ffma2_rn(__fmul2_rn(make_float2(wk.z, wk.w), e), __fmul2_rn(e, q), Q);
   }
+}
+
+// With `tail` (the series coefficients of fill_tail_coeffs), the upper nodes k >= K of
+// points with w (cosh t_K - 1) >= kTailZ come from the series; without it, or for points
+// nearer the bulge centre, every node is summed.
+template <int NQ>
+__device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const float4* __restrict__ nw, float R,
+                                                  float& Sigma, float& SigS2, const float2* __restrict__ tail = nullptr) {
+  constexpr int base = NodeBase<NQ>::value, K = TailRule<NQ>::K;
+  const float x = R * m.inv_a;
+  const float xp1 = x + 1.0f;
+  const float ix1 = rcp_approx(xp1);
+  const float w = x * ix1;
+  const float lw = lg2_approx(w);
+  const float i2 = ix1 * ix1;
+  const float ip4 = i2 * i2;
+  const float pS = ex2_approx(m.ngam * lw) * ip4;
+  const float pQ = ex2_approx(m.g3 * lw) * ip4;
+  float2 S = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
+  if (tail && w * kNodeCm1[base + K] >= kTailZ) {
+    node_pairs<NQ, 0, K>(m, nw, w, S, Q);
+    // upper nodes: w^n P(1 / w) for both sums, P by Horner in packed pairs
+    const float u = xp1 * rcp_approx(x);   // 1 / w
+    const float2 u2 = make_float2(u, u);
+    float2 P;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(P.x), "=f"(P.y)
+                 : "r"((unsigned)__cvta_generic_to_shared(tail + kTailTerms - 1)));
+#pragma unroll
+    for (int j = kTailTerms - 2; j >= 0; --j) {
+      float2 c;
+      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(c.x), "=f"(c.y)
+                   : "r"((unsigned)__cvta_generic_to_shared(tail + j)));
+      P = __ffma2_rn(P, u2, c);
+    }
+    S.x = fmaf(ex2_approx(m.g4 * lw), P.x, S.x);                    // w^(g-4)
+    Q.x = fmaf(ex2_approx(fmaf(2.0f, m.g4, 1.0f) * lw), P.y, Q.x);  // w^(2g-7)
+  } else {
+    node_pairs<NQ, 0, NQ>(m, nw, w, S, Q);
+  }
   Sigma = m.cS * x * pS * (S.x + S.y);
   SigS2 = m.cQ * pQ * (Q.x + Q.y);
+}
+
+// ---------------------------------------------------------------- upper nodes as a series
+// For the upper nodes k >= K of the radial rule (cosh t_k - 1 = m_k large), a point's
+// q_k = 1 + w m_k = w m_k (1 + z_k) with z_k = 1 / (w m_k) small, so that
+//   q_k^n = (w m_k)^n sum_j binom(n, j) z_k^j     (binomial series, |z_k| < 1)
+// and the upper part of each projected sum collapses into a polynomial in 1 / w:
+//   sum_{k>=K} W_k q_k^n = w^n sum_j binom(n, j) A_j w^-j,   A_j = sum_{k>=K} W_k m_k^(n-j),
+// with n = g - 4, W_k = ws_k c_k^-g for Sigma and n = 2g - 7, W_k = wq_k c_k^(3-2g) for
+// Sigma sigma^2 (the same terms as the per-node sums).  A_j depends on the model only.  It is
+// the same discrete sum: where w m_K >= kTailZ (z_k <= 1/16 for every upper node) the eight
+// terms leave a truncation error below 1e-9 of the whole sum for every gamma in [0, 3) (a
+// float64 check over the parameter range is a CPU test); a point closer to the bulge centre
+// (w < kTailZ / m_K: R below ~0.2 bulge scales) takes the upper nodes one by one instead.
+// K splits the rule where the series' range of validity still covers all but the centre
+// (t_K ~ 5.1 for both rules).
+
+// The series' per-model coefficients (binom(n, j) A_j for Sigma, for Sigma sigma^2), as
+// pairs, by the 32 lanes of one warp: lane l takes the upper nodes K + l, K + l + 32, ...,
+// and the lanes' partial sums are combined by a fixed shuffle tree (the same bits on every
+// call).  Float32 suffices: the upper nodes carry at most ~2e-4 of either sum (their terms
+// fall like cosh^-3 t), so the coefficients' float32 rounding moves a sum by < 1e-9 (a CPU
+// test emulates it).
+template <int NQ>
+__device__ __noinline__ void fill_tail_coeffs(const ModelConst& m, float2* tail, int lane) {
+  constexpr int base = NodeBase<NQ>::value, K = TailRule<NQ>::K;
+  const float nS = m.g4, nQ = fmaf(2.0f, m.g4, 1.0f);   // g - 4 and 2g - 7
+  float aS[kTailTerms], aQ[kTailTerms];
+#pragma unroll
+  for (int j = 0; j < kTailTerms; ++j) aS[j] = aQ[j] = 0.f;
+  for (int k = K + lane; k < NQ; k += 32) {
+    const float lm = kNodeLm[base + k], lc = kNodeLc[base + k];
+    const float r = 1.0f / kNodeCm1[base + k];
+    float eS = kNodeWs[base + k] * exp2f(fmaf(m.ngam, lc, nS * lm));   // W_k m_k^n for Sigma
+    float eQ = kNodeWq[base + k] * exp2f(fmaf(m.g3, lc, nQ * lm));     // and for Sigma sigma^2
+#pragma unroll
+    for (int j = 0; j < kTailTerms; ++j) {
+      aS[j] += eS;
+      aQ[j] += eQ;
+      eS *= r;
+      eQ *= r;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int j = 0; j < kTailTerms; ++j) {
+      aS[j] += __shfl_xor_sync(0xffffffffu, aS[j], o);
+      aQ[j] += __shfl_xor_sync(0xffffffffu, aQ[j], o);
+    }
+  }
+  if (lane < kTailTerms) {   // lane j: binom(n, j) by the product formula
+    float bS = 1.0f, bQ = 1.0f, vS = aS[0], vQ = aQ[0];
+#pragma unroll
+    for (int j = 1; j < kTailTerms; ++j) {
+      bS *= (nS - (j - 1)) / j;
+      bQ *= (nQ - (j - 1)) / j;
+      if (j == lane) {
+        vS = bS * aS[j];
+        vQ = bQ * aQ[j];
+      }
+    }
+    tail[lane] = make_float2(vS, vQ);
+  }
+}
+
+// The adjoint's series (three packed coefficient sets of kTailTerms pairs, Sigma in .x and
+// Sigma sigma^2 in .y).  Besides each sum sum W q^n, the adjoint carries the sums weighted by
+// u / w = c / q and by log2(u / w) = log2 c - log2 q (see bang_adjoint.cu).  With
+// A_j = sum_{k>=K} W_k m_k^(n-j), A'_j = sum_{k>=K} W_k log2(c_k / m_k) m_k^(n-j) and
+// log2 q = log2 w + log2 m + log2(1 + z):
+//   sum W q^n c / q          = w^(n-1) sum_j binom(n-1, j) (A_j + A_{j+1}) w^-j   (c = m + 1)
+//   sum W q^n log2(c / q) + log2 w sum W q^n
+//                            = w^n sum_j [binom(n, j) A'_j - f_j(n) A_j] w^-j,
+// f_j(n) = (d/dn binom(n, j)) / ln 2 = binom(n, j) sum_{i<j} 1 / (n - i) / ln 2, the
+// coefficients of (1 + z)^n log2(1 + z).  tail[0..T) hold binom(n, j) A_j (the sums),
+// tail[T..2T) binom(n-1, j) (A_j + A_{j+1}), tail[2T..3T) the log-weighted coefficients.
+template <int NQ>
+__device__ __noinline__ void fill_tail_coeffs_adj(const ModelConst& m, float2* tail, int lane) {
+  constexpr int base = NodeBase<NQ>::value, K = TailRule<NQ>::K, T = kTailTerms;
+  constexpr float kInvLn2 = 1.44269504088896341f;
+  for (int fam = 0; fam < 2; ++fam) {   // 0: Sigma (n = g - 4), 1: Sigma sigma^2 (n = 2g - 7)
+    const float n = fam == 0 ? m.g4 : fmaf(2.0f, m.g4, 1.0f);
+    const float pc = fam == 0 ? m.ngam : m.g3;   // power of c in W
+    float A[T + 1], Ap[T];
+#pragma unroll
+    for (int j = 0; j <= T; ++j) A[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < T; ++j) Ap[j] = 0.f;
+    for (int k = K + lane; k < NQ; k += 32) {
+      const float lcm = kNodeLcm[base + k], r = 1.0f / kNodeCm1[base + k];
+      const float W = fam == 0 ? kNodeWs[base + k] : kNodeWq[base + k];
+      float e = W * exp2f(fmaf(pc, kNodeLc[base + k], n * kNodeLm[base + k]));   // W_k m_k^n
+#pragma unroll
+      for (int j = 0; j <= T; ++j) {
+        A[j] += e;
+        if (j < T) Ap[j] = fmaf(e, lcm, Ap[j]);
+        e *= r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int j = 0; j <= T; ++j) A[j] += __shfl_xor_sync(0xffffffffu, A[j], o);
+#pragma unroll
+      for (int j = 0; j < T; ++j) Ap[j] += __shfl_xor_sync(0xffffffffu, Ap[j], o);
+    }
+    if (lane < T) {   // lane j: the three coefficient sets of pair j
+      float b = 1.0f, b1 = 1.0f, hs = 0.f;   // binom(n, j), binom(n - 1, j), sum_{i<j} 1 / (n - i)
+      float v0 = A[0], v1 = A[0] + A[1], v2 = Ap[0];
+#pragma unroll
+      for (int j = 1; j < T; ++j) {
+        b *= (n - (j - 1)) / j;
+        b1 *= (n - 1.0f - (j - 1)) / j;
+        hs += 1.0f / (n - (j - 1));
+        if (j == lane) {
+          v0 = b * A[j];
+          v1 = b1 * (A[j] + A[j + 1]);
+          v2 = b * (Ap[j] - hs * kInvLn2 * A[j]);
+        }
+      }
+      reinterpret_cast<float*>(tail + lane)[fam] = v0;
+      reinterpret_cast<float*>(tail + T + lane)[fam] = v1;
+      reinterpret_cast<float*>(tail + 2 * T + lane)[fam] = v2;
+    }
+  }
 }
 
 // Per-model node weights for bulge_projected_w, paired as (ws_k, ws_k+1, wq_k, wq_k+1)
@@ -503,7 +672,8 @@ __device__ __forceinline__ void fill_node_pairs(const ModelConst& m, float4* nw,
 // sigma^2 = C2 / C0 - v^2 and M/L = C3 / C0.
 template <int NQ, int ND>
 __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float Y, const float* tab = nullptr,
-                                             int T = 0, const float4* nodew = nullptr) {
+                                             int T = 0, const float4* nodew = nullptr,
+                                             const float2* tail = nullptr) {
   // Sec. 2.1: rotate the major axis onto x; deproject the razor-thin discs by 1 / cos i
   const float xr = fmaf(X, m.cpa, Y * m.spa);
   const float yr = fmaf(Y, m.cpa, -X * m.spa);
@@ -524,7 +694,7 @@ __device__ __forceinline__ float4 eval_point(const ModelConst& m, float X, float
   } else if (m.bulge_fit) {
     bulge_closed(m, R, Sb, SbS2);
   } else if (nodew) {
-    bulge_projected_w<NQ>(m, nodew, R, Sb, SbS2);
+    bulge_projected_w<NQ>(m, nodew, R, Sb, SbS2, tail);
   } else {
     bulge_projected<NQ>(m, R, Sb, SbS2);
   }

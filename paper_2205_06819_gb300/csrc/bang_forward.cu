@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
   __shared__ int next_item;
   __shared__ int chunk_ctr[2];
   __shared__ float4 nodew[NQ / 2];
+  __shared__ float2 tailc[kTailTerms];
   const int lane = threadIdx.x & 31;
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
@@ -216,7 +217,10 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       for (int t = tid; t < nt; t += kThreads) tab[t] = __ldg(src + t);
     }
     if (tid < 2) chunk_ctr[tid] = 0;
-    if (!tab && !mc.bulge_fit) fill_node_pairs<NQ>(mc, nodew, tid, kThreads);
+    if (!tab && !mc.bulge_fit) {
+      fill_node_pairs<NQ>(mc, nodew, tid, kThreads);
+      if (tid < 32) fill_tail_coeffs<NQ>(mc, tailc, tid);
+    }
     __syncthreads();
 
     double chi_thread = 0.0, vsys_thread = 0.0;
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           const int qx = p - gr * W;
           const float X = fmaf((float)qx, pk, mc.X0);
           const float Y = fmaf((float)(y0 + gr), pk, mc.Y0);
-          st[p] = eval_point<NQ, ND>(mc, X, Y, tab, a.table_T, nodew);
+          st[p] = eval_point<NQ, ND>(mc, X, Y, tab, a.table_T, nodew, tailc);
         }
       }
     };
@@ -589,7 +593,15 @@ cudaError_t launch_check_selftest(long long i, long long n, cudaStream_t st) {
 }
 
 cudaError_t upload_nodes_forward(const float* cm1, const float* lc, const float* ws, const float* wq) {
+  float lm[192], lcm[192];   // the series' log tables, from the float32 m_k
+  for (int k = 0; k < 192; ++k) {
+    const double mk = (double)cm1[k];
+    lm[k] = (float)std::log2(mk);
+    lcm[k] = (float)std::log2(1.0 + 1.0 / mk);
+  }
   cudaError_t e = cudaMemcpyToSymbol(kNodeCm1, cm1, 192 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeLm, lm, sizeof lm);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeLcm, lcm, sizeof lcm);
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeLc, lc, 192 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeWs, ws, 192 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(kNodeWq, wq, 192 * sizeof(float));
