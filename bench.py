@@ -48,12 +48,12 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 122.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "5f321c2e9dfcac65", "bytes_per_launch": 582400}
+NCU_TRAFFIC = {"stamp": "e33c55f6ceea5eb7", "bytes_per_launch": 491264}
 # Pipe activity of the forward kernel from the same kind of capture (ncu --set full on 456
 # rows of the benchmark batch): SFU (xu) and FMA pipes, issue active, thread instructions
 # per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "5f321c2e9dfcac65", "pipe_xu_pct": 48.9, "pipe_fma_pct": 27.1, "pipe_fma_cycles_pct": 44.3,
-             "issue_active_pct": 58.6, "thread_instr_per_point": 737}
+NCU_PIPES = {"stamp": "e33c55f6ceea5eb7", "pipe_xu_pct": 37.4, "pipe_fma_pct": 29.7, "pipe_fma_cycles_pct": 43.2,
+             "issue_active_pct": 66.0, "thread_instr_per_point": 518}
 
 
 def kernel_stamp() -> str:
@@ -198,23 +198,26 @@ def points_per_eval(spec: synth.GalaxySpec) -> int:
 #    1/Sigma) and 3 + n_discs ex2 (the bulge's two per-point powers, the bulge velocity power,
 #    each disc's exponential).  The few points within ~0.2 bulge scales of the centre that
 #    take every node one by one are counted as the others;
-#  adjoint (point_vjp): per radial node one lg2 and two ex2 (q^(g-4) and u/w); per point the
-#    forward recomputation's operations plus 1/(3-g), 1/R (twice), 1/(1+x) of the halo
-#    derivative, the two divisions of the reverse sweep: 18 + (n_discs - 1) / 2 half-rate and
-#    3 + n_discs ex2.
+#  adjoint (point_vjp): per radial node below the split one lg2 and two ex2 (q^(g-4) and
+#    u/w), the upper nodes as three series (one reciprocal, two ex2); per point the forward
+#    recomputation's operations plus 1/(3-g), 1/R (twice), 1/(1+x) of the halo derivative,
+#    the two divisions of the reverse sweep: 18 + (n_discs - 1) / 2 half-rate and 3 + n_discs
+#    ex2.
 TAIL_SPLIT = {64: 24, 128: 48}   # first radial node of the forward kernel's series (TailRule)
 
 
 def sfu_ops_per_point(n_quad: int, n_discs: int, adjoint: bool = False) -> dict:
-    if adjoint:
-        return {"half": n_quad + 18.0 + 0.5 * (n_discs - 1), "full": 2.0 * n_quad + 3.0 + n_discs}
     k = TAIL_SPLIT[n_quad]
+    if adjoint:
+        return {"half": k + 19.0 + 0.5 * (n_discs - 1), "full": 2.0 * k + 5.0 + n_discs}
     return {"half": k + 14.0 + 0.5 * (n_discs - 1), "full": k + 5.0 + n_discs}
 
 
-def sfu_ops_per_point_node_by_node(n_quad: int, n_discs: int) -> dict:
-    """The forward pass's SFU operations with every radial node evaluated one by one (the
-    plain form of the same sum)."""
+def sfu_ops_per_point_node_by_node(n_quad: int, n_discs: int, adjoint: bool = False) -> dict:
+    """The SFU operations of a pass with every radial node evaluated one by one (the plain
+    form of the same sum)."""
+    if adjoint:
+        return {"half": n_quad + 18.0 + 0.5 * (n_discs - 1), "full": 2.0 * n_quad + 3.0 + n_discs}
     return {"half": n_quad + 13.0 + 0.5 * (n_discs - 1), "full": n_quad + 3.0 + n_discs}
 
 
@@ -250,9 +253,9 @@ def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = No
     steps) and ~200 for geometry, velocities, discs and light weighting; per galaxy the
     PSF stencil (separable: 4 channels x (fine rows x nx + nx x ny) x (os + 2h); two-
     dimensional: 4 x nx x ny x (os + 2h)^2) and ~40 per spaxel for the chi-square.  A
-    gradient step adds the adjoint pass: per point 13 per radial node (the six sums) and ~400
-    for the forward recomputation and the reverse sweep, and the transposed stencil (the
-    forward's count)."""
+    gradient step adds the adjoint pass: per point 13 per radial node below the split (the six
+    sums), 48 lane operations for the three series and ~400 for the forward recomputation
+    and the reverse sweep, and the transposed stencil (the forward's count)."""
     def per_row(spec):
         sig = spec.psf_fwhm_arcsec / (2.0 * math.sqrt(2.0 * math.log(2.0)))
         h = int(math.floor(3.0 * sig / (spec.spaxel_arcsec / spec.oversample))) if spec.psf_fwhm_arcsec > 0 else 0
@@ -263,7 +266,7 @@ def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = No
             psf = 4.0 * ((spec.oversample * spec.ny + 2 * h) * spec.nx + spec.nx * spec.ny) * L
         fwd = points_per_eval(spec) * (6.0 * TAIL_SPLIT[wl.n_quad] + 16.0 + 200.0) + psf + 40.0 * spec.nx * spec.ny
         if grad:
-            fwd += points_per_eval(spec) * (13.0 * wl.n_quad + 400.0) + psf
+            fwd += points_per_eval(spec) * (13.0 * TAIL_SPLIT[wl.n_quad] + 48.0 + 400.0) + psf
         return fwd
     per = [per_row(g) for g in wl.galaxies]
     if rows is None:
@@ -305,7 +308,7 @@ def roofline_block(wl: synth.Workload, step_s: float, gal_idx=None, rows: int | 
     nbn = sfu_ops_per_point_node_by_node(wl.n_quad, wl.n_discs)
     t_nbn = pts * (nbn["half"] / MUFU_LG2_PER_CLK_SM + nbn["full"] / MUFU_EX2_PER_CLK_SM) / (sms * mhz * 1e6)
     if grad:
-        c = sfu_ops_per_point(wl.n_quad, wl.n_discs, True)
+        c = sfu_ops_per_point_node_by_node(wl.n_quad, wl.n_discs, True)
         t_nbn += pts * (c["half"] / MUFU_LG2_PER_CLK_SM + c["full"] / MUFU_EX2_PER_CLK_SM) / (sms * mhz * 1e6)
     return {"bound": "alu", "achieved": ops / step_s / 1e9, "peak": ops / t_sfu / 1e9, "unit": "G SFU op/s",
             "frac": max(t_sfu, t_fp32) / step_s,

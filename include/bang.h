@@ -246,8 +246,9 @@ bang_status bang_loglike_batch_noalloc(bang_model *m, const float *theta, const 
 bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t *gal_idx, int B, double *logL,
                               void *stream);
 
-/* Chooses launch parameters (fine rows per block step, spaxel-row bands per row) for
- * batches of B rows by timing candidates on the device; the choice is cached in the model.
+/* Chooses launch parameters (fine rows per block step and spaxel-row bands per row of the
+ * forward kernel; fine rows per work item of the adjoint) for batches of B rows by timing
+ * candidates on the device; the choice is cached in the model.
  * With a host gal_idx (or NULL: galaxy 0 for every row) it applies to later calls with that
  * same gal_idx and B; with a device gal_idx (read here, this call being synchronous) it
  * applies to every later call of B rows with a device gal_idx. */

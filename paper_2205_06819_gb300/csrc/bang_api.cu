@@ -375,6 +375,7 @@ struct bang_model {
   struct Tuning {
     int G = 4;       // fine rows per block step of the forward kernel
     int bands = 0;   // spaxel-row bands per batch row (0: default policy)
+    int adj_G = 0;   // fine rows per band of the adjoint (0: default policy)
   };
   std::map<uint64_t, Tuning> tuned;         // batch-shape key -> launch parameters
   std::mutex mu;
@@ -552,7 +553,8 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     const long long total_rows = (long long)B * H_model;
     // one staging step per band: rows per band = rows per block step (at most 16)
     const long long target = 16LL * m->num_sms;
-    const int rows = (int)std::max<long long>(1, std::min<long long>(16, (total_rows + target - 1) / target));
+    const int rows = tune.adj_G > 0 ? tune.adj_G
+                                    : (int)std::max<long long>(1, std::min<long long>(16, (total_rows + target - 1) / target));
     p->adj_G = rows;
     std::vector<bang::WorkItem> ai;
     std::vector<double> acost;
@@ -702,7 +704,8 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
   }
   if (mode == bang::kModeSeed) {
     const long long target = 16LL * m->num_sms;
-    const int rows = (int)std::max<long long>(1, std::min<long long>(16, ((long long)B * H_max + target - 1) / target));
+    const int rows = tune.adj_G > 0 ? tune.adj_G
+                                    : (int)std::max<long long>(1, std::min<long long>(16, ((long long)B * H_max + target - 1) / target));
     p->adj_G = rows;
     p->adj_nb = (H_max + rows - 1) / rows;
     p->adj_items = B * p->adj_nb;
@@ -1418,7 +1421,8 @@ bang_status bang_loglike_fp64(bang_model* m, const double* theta, const int32_t*
 }
 
 // Autotuner: times the forward launch for every (fine rows per block step G, spaxel-row
-// bands per row) candidate on this batch shape and keeps the fastest for later calls.
+// bands per row) candidate on this batch shape, then the logL + gradient call for every
+// adjoint band height with that forward choice, and keeps the fastest for later calls.
 bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   bang::NvtxRange nvtx("bang_model_tune");
   g_last_error.clear();
@@ -1494,13 +1498,52 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  m->plans.clear();
   if (!any) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->plans.clear();
     m->tuned.erase(skey);
     return fail(BANG_E_UNSUPPORTED, "no launch configuration fits this batch");
   }
+  // the gradient path's band height (fine rows per adjoint work item), timed on whole
+  // logL + gradient calls with the forward's choice fixed
+  {
+    float best_g = 1e30f;
+    int best_rows = 0;
+    for (int rows : {0, 4, 8, 16, 24, 32}) {
+      m->tuned[skey] = bang_model::Tuning{best_t.G, best_t.bands, rows};
+      m->plans.clear();
+      Plan* p = nullptr;
+      if ((dgal ? get_dplan(m, B, bang::kModeSeed, &p) : get_plan(m, hgal, B, bang::kModeSeed, &p)) != BANG_OK)
+        continue;
+      if (p->G != best_t.G) continue;
+      if (m->scratch_seed.reserve(sizeof(float) * (size_t)std::max<int64_t>(p->out_total, 4)) != cudaSuccess ||
+          m->scratch_grad.reserve(grad_scratch_bytes(p)) != cudaSuccess ||
+          m->stage_out2.reserve(sizeof(float) * (size_t)B * m->P) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        BANG_CUDA(cudaEventRecord(e0, st));
+        BANG_CUDA(enqueue_grad(m, p, m->stage_theta.as<float>(), m->stage_out.as<double>(), m->scratch_seed.as<float>(),
+                               m->scratch_grad.as<double>(), m->stage_out2.as<float>(), st, dgal));
+        BANG_CUDA(cudaEventRecord(e1, st));
+        BANG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BANG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) t_min = std::min(t_min, ms);
+      }
+      if (t_min < best_g) {
+        best_g = t_min;
+        best_rows = rows;
+      }
+    }
+    best_t.adj_G = best_rows;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->plans.clear();
   m->tuned[skey] = best_t;
   return bang::check_faults(st);
 }

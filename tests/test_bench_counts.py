@@ -33,16 +33,18 @@ def test_series_split_matches_the_kernel_header():
 
 
 def test_sfu_count_of_the_gradient_step():
-    """logL + gradient = the forward seed pass plus the adjoint: per node one lg2 and two ex2
-    (q^(g-4) and u/w), per point 18 half-rate and 4 ex2 (one disc); two discs add half a
-    half-rate and one ex2 per point to each pass."""
+    """logL + gradient = the forward seed pass plus the adjoint: per node below the split one
+    lg2 and two ex2 (q^(g-4) and u/w), the series one reciprocal and two ex2, per point 18
+    half-rate and 4 ex2 (one disc); two discs add half a half-rate and one ex2 per point to
+    each pass."""
     wl = synth.workload("adjoint")
     ops, cyc = bench.sfu_work(wl, grad=True)
     fwd = 430 * 430 * ((24 + 14) / 16 + (24 + 6) / 32)
-    adj = 430 * 430 * ((64 + 18) / 16 + (128 + 4) / 32)
+    adj = 430 * 430 * ((24 + 19) / 16 + (48 + 6) / 32)
     assert cyc / wl.batch == pytest.approx(fwd + adj, rel=1e-12)
-    assert ops / wl.batch == 430 * 430 * (24 + 14 + 24 + 6 + 64 + 18 + 128 + 4)
-    assert bench.sfu_ops_per_point(128, 2, True) == {"half": 128 + 18.5, "full": 256 + 5}
+    assert ops / wl.batch == 430 * 430 * (24 + 14 + 24 + 6 + 24 + 19 + 48 + 6)
+    assert bench.sfu_ops_per_point(128, 2, True) == {"half": 48 + 19.5, "full": 96 + 7}
+    assert bench.sfu_ops_per_point_node_by_node(128, 2, True) == {"half": 128 + 18.5, "full": 256 + 5}
     assert bench.sfu_ops_per_point(128, 2, False) == {"half": 48 + 14.5, "full": 48 + 7}
 
 

@@ -156,8 +156,19 @@ def test_full_size_adjoint_workload_sampled_rows(Model):
     ds = Dataset(wl.galaxies[0], tt, seed=synth.dataset_seed(wid))
     theta = synth.draw_theta_batch(box, tt, wl.batch, synth.batch_seed(wid)).astype(np.float32)
     m = Model(ds.model_galaxy())
-    _, grad = m.loglike_grad(torch.from_numpy(theta).cuda())
+    m.tune(wl.batch)                               # the launch shape bench.py times
+    logL, grad = m.loglike_grad(torch.from_numpy(theta).cuda())
     grad = grad.cpu().numpy()
     pick = np.array([0, 255])
-    _, ref = oracle_grad(ds, theta[pick])
+    ref_l, ref = oracle_grad(ds, theta[pick])
+    import json
+    import oracle
+    from bang_testdata import grad_errors
+    chi = -2.0 * (logL.cpu().numpy()[pick] + oracle.norm_const(ds.og))
+    chi_ref = -2.0 * (ref_l + oracle.norm_const(ds.og))
+    ge = grad_errors(grad[pick], ref)
+    print(json.dumps({"workload": "adjoint", "rows": int(wl.batch), "rows_checked": pick.tolist(),
+                      "max_rel_chi2": float((np.abs(chi - chi_ref) / chi_ref).max()),
+                      "grad_err_over_norm": max(e[0] for e in ge), "grad_err_component_relative": max(e[1] for e in ge)}))
+    assert (np.abs(chi - chi_ref) / chi_ref).max() < CHI2_RTOL
     assert_grad_close(grad[pick], ref, "full")
