@@ -476,10 +476,12 @@ def _event_time(torch, fn, steps, flush=None):
 
 
 def time_workload(name, torch, grad=False, rows=None, steps=5, warmup=2, mhz=SM_MAX_MHZ_NOMINAL,
-                  sms=SM_COUNT_NOMINAL, flush=None, forward_too=False):
+                  sms=SM_COUNT_NOMINAL, flush=None, forward_too=False, plain_rows=0):
     """One workload (or its first `rows` rows) in one launch after the autotuner has chosen
     its shape: device-timed logL (or logL + gradient) evaluations per second and the SFU
-    roofline of the timed step."""
+    roofline of the timed step.  With plain_rows, also the paper's one-kernel-per-task form
+    (bang_loglike_plain) on the first plain_rows rows, and its largest relative logL
+    difference from the fused launch."""
     wl = synth.workload(name)
     model, _, theta_np, gal_idx = make_model(wl, 0, torch)
     if rows:
@@ -501,12 +503,25 @@ def time_workload(name, torch, grad=False, rows=None, steps=5, warmup=2, mhz=SM_
     ms = _event_time(torch, call, steps, flush)
     metric = "logL+gradient evals/s" if grad else "logL evals/s"
     res = {"value": B / ms * 1e3, "unit": metric, "ms_per_step": ms, "rows": B, "steps": steps,
-           "workload": f"{wl.name}: {wl.description}",
+           "workload": f"{wl.name}: {wl.description}", "launch": model.launch_info(B, gal_idx, grad),
            "roofline": roofline_block(wl, ms / 1e3, gal_idx, B, grad, mhz, sms)}
     if forward_too:
         fms = _event_time(torch, lambda: model.loglike(theta, gal_idx, out=out), steps, flush)
         res["forward_only_ms"] = fms
         res["grad_over_forward"] = ms / fms
+    if plain_rows:
+        n = min(plain_rows, B)
+        tp = theta[:n]
+        gp = None if gal_idx is None else np.ascontiguousarray(gal_idx[:n])
+        model.loglike_plain(tp[:1], None if gp is None else gp[:1])
+        torch.cuda.synchronize()
+        pms = _event_time(torch, lambda: model.loglike_plain(tp, gp), 1)
+        ref = model.loglike(tp, gp)
+        got = model.loglike_plain(tp, gp)
+        fin = torch.isfinite(ref)
+        res["plain_gpu"] = {"value": n / pms * 1e3, "unit": "logL evals/s", "rows": n, "ms": pms,
+                            "max_rel_logL_vs_fused": ((got[fin] - ref[fin]).abs() / ref[fin].abs()).max().item(),
+                            "form": "one kernel per task per parameter vector (bang_loglike_plain)"}
     model.close()
     return res
 
@@ -700,7 +715,8 @@ def run_ours(args):
                    + (f", psf_mode {args.psf_mode}" if args.psf_mode else ""),
                    "padded_fine_points_per_row": points_per_eval(wl.galaxies[0]) if len(wl.galaxies) == 1 else
                    "per galaxy", "n_quad": wl.n_quad, "galaxies": len(wl.galaxies),
-                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "launch": model.launch_info(B, gal_idx, args.grad)},
         "e2e": {"value": e2e_value, "unit": metric, "h2d_bytes_per_step": int(B * P * 4),
                 "d2h_bytes_per_step": int(B * 8 + (B * P * 4 if args.grad else 0))},
         "gpu_launches": launches_per_step * args.steps,
@@ -723,8 +739,8 @@ def run_ours(args):
         # uneven batch (64 galaxies x 64 rows), the largest (4096 rows; its gradient on the
         # first 1024), and the single row's latency in three forms
         line["fwd_adjoint"] = time_workload("adjoint", grad=True, steps=10, forward_too=True, **side)
-        line["uneven"] = time_workload("uneven", steps=5, **side)
-        line["largest"] = time_workload("largest", steps=3, **side)
+        line["uneven"] = time_workload("uneven", steps=5, plain_rows=4096, **side)
+        line["largest"] = time_workload("largest", steps=3, plain_rows=32, **side)
         line["largest_grad"] = time_workload("largest", grad=True, rows=1024, steps=3, **side)
         line["single"] = time_single(torch)
         line["radial_table"] = time_table(wl, torch)

@@ -254,6 +254,17 @@ bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t 
  * applies to every later call of B rows with a device gal_idx. */
 bang_status bang_model_tune(bang_model *m, const int32_t *gal_idx, int B);
 
+/* The launch shape bang_loglike_batch (grad = 0) or bang_loglike_grad_batch (grad = 1)
+ * would use for (gal_idx, B), after any bang_model_tune: info[10] (host) receives
+ *   0 fine rows per block step of the forward kernel, 1 spaxel-row bands per batch row,
+ *   2 forward blocks per SM, 3 forward grid, 4 forward work items, 5 forward dynamic shared
+ *   memory per block (bytes), 6 fine rows per adjoint work item, 7 adjoint grid,
+ *   8 adjoint work items (6-8 zero when grad = 0), 9 1 when the work items are derived on
+ *   the device (device gal_idx), else 0.
+ * Builds (and caches) the batch's plan like a call; launches nothing.  Synchronous.  For
+ * diagnostics (the paper has no counterpart). */
+bang_status bang_model_launch_info(bang_model *m, const int32_t *gal_idx, int B, int grad, int32_t *info);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *bang_last_error(void);
 

@@ -998,6 +998,20 @@ bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang
     if ((st = upload(m.get(), iv, &G.iv)) != BANG_OK) return st;
     const std::vector<float> taps =
         make_taps(d.psf_kind, d.psf_fwhm_arcsec, d.moffat_beta, G.os, G.h, pitch, opts->psf_mode);
+    if (G.psf_kind == 1) {
+      // the forward kernel keeps one quadrant of the two-dimensional taps: every window here
+      // is even in dx and dy, so the mirrored taps agree (to float64 summation order)
+      const int L = G.L;
+      float tmax = 0.f;
+      for (float t : taps) tmax = std::max(tmax, std::fabs(t));
+      for (int cy = 0; cy < L; ++cy)
+        for (int cx = 0; cx < L; ++cx) {
+          const float t = taps[(size_t)cy * L + cx];
+          if (std::fabs(t - taps[(size_t)(L - 1 - cy) * L + cx]) > 1e-6f * tmax ||
+              std::fabs(t - taps[(size_t)cy * L + (L - 1 - cx)]) > 1e-6f * tmax)
+            return fail(BANG_E_UNSUPPORTED, "galaxy %d: two-dimensional PSF taps are not mirror-symmetric", g);
+        }
+    }
     if ((st = upload(m.get(), taps, &G.taps)) != BANG_OK) return st;
     m->gals.push_back(G);
     m->desc.push_back(d);
@@ -1418,6 +1432,26 @@ bang_status bang_loglike_fp64(bang_model* m, const double* theta, const int32_t*
     std::memcpy(logL, out.data(), sizeof(double) * B);
   }
   return bang::check_faults(st);
+}
+
+// The launch shape a call would use (plans are built, nothing is launched).
+bang_status bang_model_launch_info(bang_model* m, const int32_t* gal_idx, int B, int grad, int32_t* info) {
+  g_last_error.clear();
+  if (!m || !info) return fail(BANG_E_INVALID_ARG, "null model or info");
+  if (B < 1) return fail(BANG_E_INVALID_ARG, "B < 1");
+  std::lock_guard<std::mutex> lock(m->mu);
+  ScratchScope scope(&m->budget);
+  BANG_CUDA(cudaSetDevice(m->device));
+  const int gplace = gal_idx_place(gal_idx, m->device);
+  if (gplace < 0) return fail(BANG_E_INVALID_ARG, "gal_idx is device memory of another device");
+  const int mode = grad ? bang::kModeSeed : bang::kModeLogL;
+  Plan* p = nullptr;
+  bang_status s = gplace > 0 ? get_dplan(m, B, mode, &p) : get_plan(m, gal_idx, B, mode, &p);
+  if (s != BANG_OK) return s;
+  const int32_t v[10] = {p->G, p->bands, p->blocks_per_sm, p->grid, p->n_items, (int32_t)p->smem,
+                         grad ? p->adj_G : 0, grad ? p->adj_grid : 0, grad ? p->adj_items : 0, p->implicit ? 1 : 0};
+  std::memcpy(info, v, sizeof v);
+  return BANG_OK;
 }
 
 // Autotuner: times the forward launch for every (fine rows per block step G, spaxel-row

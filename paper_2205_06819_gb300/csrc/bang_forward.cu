@@ -159,10 +159,14 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx;
     const int NA = (L + os - 1) / os;                       // open spaxel rows
     // separable taps stored twice, (t, t): a 64-bit load gives the pair the packed
-    // two-lane FMAs need; the L x L two-dimensional taps once (shared memory)
+    // two-lane FMAs need; of the L x L two-dimensional taps only the Lq x Lq quadrant
+    // (Lq = (L + 1) / 2): every two-dimensional window here is even in dx and dy about the
+    // window's centre, and so is the os x os mean, so tap (cy, cx) equals tap (L-1-cy, cx)
+    // and (cy, L-1-cx)
     float2* taps = reinterpret_cast<float2*>(smem_raw);
     float* taps2d = reinterpret_cast<float*>(smem_raw);
-    const int ntaps = PSF == 0 ? L : L * L;
+    const int Lq = (L + 1) / 2;
+    const int ntaps = PSF == 0 ? L : Lq * Lq;
     float4* acc = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * (PSF == 0 ? 8 : 4) + 15) / 16) * 16);
     float4* stage = acc + (size_t)NA * nx;
     float* tab = a.tables ? reinterpret_cast<float*>(stage + 2 * (size_t)a.G * W) : nullptr;
@@ -206,9 +210,13 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
     }
 
     for (int t = tid; t < ntaps; t += kThreads) {
-      const float tv = __ldg(gs.taps + t);
-      if (PSF == 0) taps[t] = make_float2(tv, tv);
-      else taps2d[t] = tv;
+      if (PSF == 0) {
+        const float tv = __ldg(gs.taps + t);
+        taps[t] = make_float2(tv, tv);
+      } else {
+        const int ty = t / Lq, tx = t - ty * Lq;
+        taps2d[t] = __ldg(gs.taps + ty * L + tx);
+      }
     }
     for (int t = tid; t < NA * nx; t += kThreads) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tab) {   // this row's radial table: header, values and log-ratios of Sigma and Q
@@ -313,13 +321,21 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
           const int ga = max(0, j * os - y0);
           const int gb = min(G - 1, j * os + L - 1 - y0);
           for (int gr = ga; gr <= gb; ++gr) {
-            if (!BANG_IN(y0 + gr - j * os, L, kSiteFwdTap)) continue;
-            const float* wrow = taps2d + (y0 + gr - j * os) * L;
+            const int cy = y0 + gr - j * os;
+            if (!BANG_IN(cy, L, kSiteFwdTap)) continue;
+            const float* wrow = taps2d + min(cy, L - 1 - cy) * Lq;
             const float4* srow = stage_c + gr * W + i * os;
             float2 axy = make_float2(A.x, A.y), azw = make_float2(A.z, A.w);
-            for (int k = 0; k < L; ++k) {
+            // columns k and L-1-k share a tap: their points are summed first
+            for (int k = 0; k < L / 2; ++k) {
               const float2 tw = make_float2(wrow[k], wrow[k]);
-              const float4 v = srow[k];
+              const float4 v = srow[k], u = srow[L - 1 - k];
+              axy = __ffma2_rn(tw, __fadd2_rn(make_float2(v.x, v.y), make_float2(u.x, u.y)), axy);
+              azw = __ffma2_rn(tw, __fadd2_rn(make_float2(v.z, v.w), make_float2(u.z, u.w)), azw);
+            }
+            if (L & 1) {
+              const float2 tw = make_float2(wrow[L / 2], wrow[L / 2]);
+              const float4 v = srow[L / 2];
               axy = __ffma2_rn(tw, make_float2(v.x, v.y), axy);
               azw = __ffma2_rn(tw, make_float2(v.z, v.w), azw);
             }
@@ -488,7 +504,7 @@ cudaError_t launch_psf(const FwdArgs& a, int psf2d, int mode, int grid, size_t s
 int forward_threads() { return kThreads; }
 
 size_t forward_smem_bytes(int L, int os, int nx, int W, int G, int psf2d, int table_T) {
-  const int ntaps = psf2d ? L * L : L;
+  const int ntaps = psf2d ? ((L + 1) / 2) * ((L + 1) / 2) : L;   // two-dimensional: the quadrant
   const int NA = (L + os - 1) / os;
   return (((size_t)ntaps * (psf2d ? 4 : 8) + 15) / 16) * 16 + (size_t)NA * nx * 16 + 2 * (size_t)G * W * 16 +
          (table_T > 0 ? sizeof(float) * (size_t)(kTabHdr + 4 * table_T) : 0);

@@ -196,6 +196,15 @@ class Model:
         gi, gptr = self._gal_idx(gal_idx, B)
         _lib.check(_lib.lib().bang_model_tune(self._h, gptr, B))
 
+    def launch_info(self, B: int, gal_idx=None, grad: bool = False) -> dict:
+        """The launch shape a call on (gal_idx, B) would use (bang_model_launch_info)."""
+        gi, gptr = self._gal_idx(gal_idx, B)
+        info = (ctypes.c_int32 * 10)()
+        _lib.check(_lib.lib().bang_model_launch_info(self._h, gptr, B, int(grad), info))
+        keys = ["rows_per_step", "bands", "blocks_per_sm", "grid", "items", "smem_bytes", "adj_rows_per_item",
+                "adj_grid", "adj_items", "device_items"]
+        return dict(zip(keys, list(info)))
+
 
 class LogLike(torch.autograd.Function):
     """logL = LogLike.apply(theta, model, gal_idx): batched log-likelihood whose backward is

@@ -120,3 +120,19 @@ def test_maps_refuse_a_device_gal_idx(setup):
     st = L.bang_model_maps(m.handle, ctypes.c_void_p(theta.data_ptr()), ctypes.c_void_p(gal_dev.data_ptr()), 4,
                            ctypes.c_void_p(out.data_ptr()), None)
     assert st == 4                                  # BANG_E_UNSUPPORTED
+
+
+def test_launch_info_reports_the_plan(setup):
+    """bang_model_launch_info: the launch shape of a host-index and a device-index batch of the
+    same rows (the same bands; the device plan's items derived on the device), and of the
+    gradient call (its adjoint band height and work items)."""
+    m, dss = setup
+    theta_np, gal = batch(24, 87)
+    h = m.launch_info(24, gal)
+    d = m.launch_info(24, torch.from_numpy(gal).cuda())
+    g = m.launch_info(24, gal, grad=True)
+    assert h["device_items"] == 0 and d["device_items"] == 1
+    assert h["bands"] == d["bands"] >= 1 and d["items"] == 24 * d["bands"]
+    assert 1 <= h["grid"] <= h["items"] and h["blocks_per_sm"] >= 1 and h["rows_per_step"] >= 1
+    assert h["adj_rows_per_item"] == 0 and g["adj_rows_per_item"] >= 1 and g["adj_items"] >= 24
+    assert 1 <= g["adj_grid"] <= g["adj_items"]
