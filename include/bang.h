@@ -246,21 +246,23 @@ bang_status bang_loglike_batch_noalloc(bang_model *m, const float *theta, const 
 bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t *gal_idx, int B, double *logL,
                               void *stream);
 
-/* Chooses launch parameters (fine rows per block step and spaxel-row bands per row of the
- * forward kernel; fine rows per work item of the adjoint) for batches of B rows by timing
- * candidates on the device; the choice is cached in the model.
+/* Chooses launch parameters (kernel form, fine rows per block step and spaxel-row bands per
+ * row of the forward kernel; the gradient call's forward rows per step and the adjoint's
+ * fine rows per work item) for batches of B rows by timing candidates on the device; the
+ * choice is cached in the model.
  * With a host gal_idx (or NULL: galaxy 0 for every row) it applies to later calls with that
  * same gal_idx and B; with a device gal_idx (read here, this call being synchronous) it
  * applies to every later call of B rows with a device gal_idx. */
 bang_status bang_model_tune(bang_model *m, const int32_t *gal_idx, int B);
 
 /* The launch shape bang_loglike_batch (grad = 0) or bang_loglike_grad_batch (grad = 1)
- * would use for (gal_idx, B), after any bang_model_tune: info[10] (host) receives
+ * would use for (gal_idx, B), after any bang_model_tune: info[11] (host) receives
  *   0 fine rows per block step of the forward kernel, 1 spaxel-row bands per batch row,
  *   2 forward blocks per SM, 3 forward grid, 4 forward work items, 5 forward dynamic shared
  *   memory per block (bytes), 6 fine rows per adjoint work item, 7 adjoint grid,
  *   8 adjoint work items (6-8 zero when grad = 0), 9 1 when the work items are derived on
- *   the device (device gal_idx), else 0.
+ *   the device (device gal_idx), else 0, 10 fine points per thread of the forward kernel
+ *   (2: the two-point form the autotuner may choose for logL batches, 3 blocks per SM).
  * Builds (and caches) the batch's plan like a call; launches nothing.  Synchronous.  For
  * diagnostics (the paper has no counterpart). */
 bang_status bang_model_launch_info(bang_model *m, const int32_t *gal_idx, int B, int grad, int32_t *info);

@@ -282,6 +282,7 @@ struct Plan {
   int B = 0, n_items = 0, G = 4, grid = 0, blocks_per_sm = 0;
   size_t smem = 0;
   int mode = 0;
+  int kmode = 0;   // the forward kernel form launched (kModeLogL2 for a tuned logL batch)
   std::vector<bang::WorkItem> items;
   std::vector<int> order, row_first, row_g;
   std::vector<int64_t> out_off;
@@ -376,6 +377,8 @@ struct bang_model {
     int G = 4;       // fine rows per block step of the forward kernel
     int bands = 0;   // spaxel-row bands per batch row (0: default policy)
     int adj_G = 0;   // fine rows per band of the adjoint (0: default policy)
+    int pair = 0;    // logL batches: 1 = the two-points-per-thread kernel form (kModeLogL2)
+    int seed_G = 0;  // fine rows per block step of the gradient call's forward pass (0: G)
   };
   std::map<uint64_t, Tuning> tuned;         // batch-shape key -> launch parameters
   std::mutex mu;
@@ -516,7 +519,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   for (int b = 0; b < B; ++b)
     if (m->gals[p->row_g[b]].psf_kind != psf2d)
       return fail(BANG_E_UNSUPPORTED, "a batch mixes Gaussian and Moffat PSF galaxies");
-  p->G = tune.G;
+  p->G = (mode == bang::kModeSeed && tune.seed_G > 0) ? tune.seed_G : tune.G;
   // shared memory: the NA bound uses the smallest os among rows with the largest L, so
   // take it per galaxy
   size_t smem = 0;
@@ -534,7 +537,8 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     if (smem > (size_t)m->smem_optin - 4096) return fail(BANG_E_UNSUPPORTED, "galaxy too large for one block's shared memory");
   }
   p->smem = smem;
-  const void* kp = bang::forward_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, mode);
+  p->kmode = (mode == bang::kModeLogL && tune.pair) ? bang::kModeLogL2 : mode;
+  const void* kp = bang::forward_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, p->kmode);
   cudaFuncAttributes fa;
   BANG_CUDA(cudaFuncGetAttributes(&fa, kp));
   if (smem + fa.sharedSizeBytes > (size_t)m->smem_optin)
@@ -667,7 +671,7 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
   p->n_items = B * p->nb;
   p->out_stride = n4_max;
   p->out_total = (int64_t)B * n4_max;
-  p->G = tune.G;
+  p->G = (mode == bang::kModeSeed && tune.seed_G > 0) ? tune.seed_G : tune.G;
   size_t smem = 0;
   for (const bang::GalDev& G : m->gals)
     smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, p->G, psf2d, m->opts.bulge_table));
@@ -679,7 +683,8 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
     if (smem > (size_t)m->smem_optin - 4096) return fail(BANG_E_UNSUPPORTED, "galaxy too large for one block's shared memory");
   }
   p->smem = smem;
-  const void* kp = bang::forward_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, mode);
+  p->kmode = (mode == bang::kModeLogL && tune.pair) ? bang::kModeLogL2 : mode;
+  const void* kp = bang::forward_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, p->kmode);
   cudaFuncAttributes fa;
   BANG_CUDA(cudaFuncGetAttributes(&fa, kp));
   if (smem + fa.sharedSizeBytes > (size_t)m->smem_optin)
@@ -791,7 +796,8 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   }
   e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode, p->grid, p->smem, st);
+  e = bang::launch_forward(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), mode == bang::kModeLogL ? p->kmode : mode,
+                           p->grid, p->smem, st);
   if (e != cudaSuccess || !logL) return e;
   if (p->implicit)
     return bang::launch_finalize(a.partial, nullptr, dgal, a.gals, p->B, p->n_items, a.n_gal, logL, st, p->nb, 1);
@@ -1448,15 +1454,17 @@ bang_status bang_model_launch_info(bang_model* m, const int32_t* gal_idx, int B,
   Plan* p = nullptr;
   bang_status s = gplace > 0 ? get_dplan(m, B, mode, &p) : get_plan(m, gal_idx, B, mode, &p);
   if (s != BANG_OK) return s;
-  const int32_t v[10] = {p->G, p->bands, p->blocks_per_sm, p->grid, p->n_items, (int32_t)p->smem,
-                         grad ? p->adj_G : 0, grad ? p->adj_grid : 0, grad ? p->adj_items : 0, p->implicit ? 1 : 0};
+  const int32_t v[11] = {p->G, p->bands, p->blocks_per_sm, p->grid, p->n_items, (int32_t)p->smem,
+                         grad ? p->adj_G : 0, grad ? p->adj_grid : 0, grad ? p->adj_items : 0, p->implicit ? 1 : 0,
+                         p->kmode == bang::kModeLogL2 ? 2 : 1};
   std::memcpy(info, v, sizeof v);
   return BANG_OK;
 }
 
-// Autotuner: times the forward launch for every (fine rows per block step G, spaxel-row
-// bands per row) candidate on this batch shape, then the logL + gradient call for every
-// adjoint band height with that forward choice, and keeps the fastest for later calls.
+// Autotuner: times the forward launch for every (kernel form, fine rows per block step G,
+// spaxel-row bands per row) candidate on this batch shape, then logL + gradient calls for
+// the seed pass's rows per step and the adjoint's band height, and keeps the fastest for
+// later calls.
 bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   bang::NvtxRange nvtx("bang_model_tune");
   g_last_error.clear();
@@ -1506,9 +1514,10 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   float best = 1e30f;
   bang_model::Tuning best_t;
   bool any = false;
+  for (int pair : {0, 1}) {
   for (int G : {1, 2, 4, 8}) {
     for (int nb : bands) {
-      m->tuned[skey] = bang_model::Tuning{G, nb};
+      m->tuned[skey] = bang_model::Tuning{G, nb, 0, pair};
       m->plans.clear();
       Plan* p = nullptr;
       if ((dgal ? get_dplan(m, B, bang::kModeLogL, &p) : get_plan(m, hgal, B, bang::kModeLogL, &p)) != BANG_OK)
@@ -1527,10 +1536,11 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
       }
       if (t_min < best) {
         best = t_min;
-        best_t = bang_model::Tuning{G, nb};
+        best_t = bang_model::Tuning{G, nb, 0, pair};
         any = true;
       }
     }
+  }
   }
   if (!any) {
     cudaEventDestroy(e0);
@@ -1539,18 +1549,29 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
     m->tuned.erase(skey);
     return fail(BANG_E_UNSUPPORTED, "no launch configuration fits this batch");
   }
-  // the gradient path's band height (fine rows per adjoint work item), timed on whole
-  // logL + gradient calls with the forward's choice fixed
+  // the gradient path: the forward seed pass's rows per step, then the adjoint's band height
+  // (fine rows per work item), each timed on whole logL + gradient calls
   {
     float best_g = 1e30f;
-    int best_rows = 0;
-    for (int rows : {0, 4, 8, 16, 24, 32}) {
-      m->tuned[skey] = bang_model::Tuning{best_t.G, best_t.bands, rows};
+    int best_rows = 0, best_sg = best_t.G;
+    struct Cand {
+      int sg, rows;
+    };
+    std::vector<Cand> cands;
+    for (int sg : {1, 2, 4}) cands.push_back({sg, 0});
+    for (int rows : {4, 8, 16, 24, 32}) cands.push_back({-1, rows});   // -1: the best rows per step so far
+    for (const Cand& c : cands) {
+      const int sg = c.sg < 0 ? best_sg : c.sg;
+      const int rows = c.sg < 0 ? c.rows : best_rows;
+      bang_model::Tuning tg = best_t;
+      tg.seed_G = sg;
+      tg.adj_G = rows;
+      m->tuned[skey] = tg;
       m->plans.clear();
       Plan* p = nullptr;
       if ((dgal ? get_dplan(m, B, bang::kModeSeed, &p) : get_plan(m, hgal, B, bang::kModeSeed, &p)) != BANG_OK)
         continue;
-      if (p->G != best_t.G) continue;
+      if (p->G != sg) continue;
       if (m->scratch_seed.reserve(sizeof(float) * (size_t)std::max<int64_t>(p->out_total, 4)) != cudaSuccess ||
           m->scratch_grad.reserve(grad_scratch_bytes(p)) != cudaSuccess ||
           m->stage_out2.reserve(sizeof(float) * (size_t)B * m->P) != cudaSuccess) {
@@ -1571,9 +1592,11 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
       if (t_min < best_g) {
         best_g = t_min;
         best_rows = rows;
+        best_sg = sg;
       }
     }
     best_t.adj_G = best_rows;
+    best_t.seed_G = best_sg;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -107,7 +107,7 @@ __device__ __forceinline__ float finish_spaxel(const GalDev& g, const ModelConst
 }
 
 template <int NQ, int ND, int PSF, int MODE>
-__global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_kernel(FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ModelConst mc;
   __shared__ GalDev gs;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
                  dynamic_smem_bytes(), kSiteFwdSmem) ||
         !BANG_IN((nx - 1) * os + L - 1, W, kSiteFwdStencil) || !BANG_IN(w.j0, w.j1, kSiteFwdSpaxel) ||
         !BANG_IN(w.j1 - 1, gs.ny, kSiteFwdSpaxel) ||
-        (MODE != kModeLogL && !BANG_IN(ooff + 4ll * nx * gs.ny - 1, a.out_total, kSiteFwdOut)) ||
+        ((MODE == kModeMaps || MODE == kModeSeed) && !BANG_IN(ooff + 4ll * nx * gs.ny - 1, a.out_total, kSiteFwdOut)) ||
         (tab && !BANG_IN((long long)w.b * a.table_stride + kTabHdr + 4 * a.table_T - 1,
                          (long long)a.B * a.table_stride, kSiteFwdTable))) {
       BANG_NEXT_ITEM(it);
@@ -246,6 +246,27 @@ __global__ void __launch_bounds__(kThreads, 4) forward_kernel(FwdArgs a) {
       const int npts = min(a.G, y_end - y0) * W;
       float4* st = stage + (size_t)(c & 1) * a.G * W;
       if (!BANG_IN(npts, a.G * W + 1, kSiteFwdStage)) return;
+      if (MODE == kModeLogL2) {   // two points per thread: their independent chains interleave
+        for (;;) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&chunk_ctr[c & 1], 64);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (base >= npts) break;
+          const int pA = base + lane;
+          if (pA < npts) {
+            const int pB = min(base + 32 + lane, npts - 1);   // a lane past the end repeats the last point
+            const int grA = __float2int_rz(((float)pA + 0.5f) * inv_W);
+            const int grB = __float2int_rz(((float)pB + 0.5f) * inv_W);
+            const float XA = fmaf((float)(pA - grA * W), pk, mc.X0), YA = fmaf((float)(y0 + grA), pk, mc.Y0);
+            const float XB = fmaf((float)(pB - grB * W), pk, mc.X0), YB = fmaf((float)(y0 + grB), pk, mc.Y0);
+            const float4 oA = eval_point<NQ, ND>(mc, XA, YA, tab, a.table_T, nodew, tailc);
+            const float4 oB = eval_point<NQ, ND>(mc, XB, YB, tab, a.table_T, nodew, tailc);
+            st[pA] = oA;
+            if (base + 32 + lane < npts) st[pB] = oB;
+          }
+        }
+        return;
+      }
       for (;;) {
         int base = 0;
         if (lane == 0) base = atomicAdd(&chunk_ctr[c & 1], 32);
@@ -489,6 +510,7 @@ template <int NQ, int ND, int PSF>
 cudaError_t launch_mode(const FwdArgs& a, int mode, int grid, size_t smem, cudaStream_t st) {
   switch (mode) {
     case kModeLogL: return launch_t<NQ, ND, PSF, kModeLogL>(a, grid, smem, st);
+    case kModeLogL2: return launch_t<NQ, ND, PSF, kModeLogL2>(a, grid, smem, st);
     case kModeMaps: return launch_t<NQ, ND, PSF, kModeMaps>(a, grid, smem, st);
     default: return launch_t<NQ, ND, PSF, kModeSeed>(a, grid, smem, st);
   }
@@ -514,6 +536,7 @@ const void* forward_kernel_ptr(int n_quad, int n_discs, int psf2d, int mode) {
 #define BANG_PICK(NQ, ND, PSF)                                                    \
   if (n_quad == NQ && n_discs == ND && psf2d == PSF) {                            \
     if (mode == kModeLogL) return (const void*)forward_kernel<NQ, ND, PSF, kModeLogL>; \
+    if (mode == kModeLogL2) return (const void*)forward_kernel<NQ, ND, PSF, kModeLogL2>; \
     if (mode == kModeMaps) return (const void*)forward_kernel<NQ, ND, PSF, kModeMaps>; \
     return (const void*)forward_kernel<NQ, ND, PSF, kModeSeed>;                   \
   }

@@ -36,7 +36,10 @@ struct NvtxRange {
 constexpr int kAdjSlots = 24;   // constant adjoints per adjoint work item (the adjoint kernel's accumulators)
 constexpr int kVsysSlot = 24;   // index of d logL / d v_sys among a row's summed adjoints (from the forward seed pass)
 
-enum { kModeLogL = 0, kModeMaps = 1, kModeSeed = 2 };
+// Forward kernel modes: logL only, model maps, adjoint seeds; kModeLogL2 is logL with two
+// fine points per thread at 3 blocks per SM (80 registers), an alternative launch form the
+// autotuner may choose for logL batches.
+enum { kModeLogL = 0, kModeMaps = 1, kModeSeed = 2, kModeLogL2 = 3 };
 
 // Arguments of the fused forward kernel.
 struct FwdArgs {
