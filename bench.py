@@ -48,12 +48,12 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 122.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "e33c55f6ceea5eb7", "bytes_per_launch": 491264}
-# Pipe activity of the forward kernel from the same kind of capture (ncu --set full on 456
-# rows of the benchmark batch): SFU (xu) and FMA pipes, issue active, thread instructions
-# per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "e33c55f6ceea5eb7", "pipe_xu_pct": 37.4, "pipe_fma_pct": 29.7, "pipe_fma_cycles_pct": 43.2,
-             "issue_active_pct": 66.0, "thread_instr_per_point": 518}
+NCU_TRAFFIC = {"stamp": "af1250c70a7d1ebf", "bytes_per_launch": 513280}
+# Pipe activity of the forward kernel from the same kind of capture (ncu --set full on one
+# timed launch of the tuned benchmark batch): SFU (xu) and FMA pipes, issue active, thread
+# instructions per fine point; stamp-checked like the traffic.
+NCU_PIPES = {"stamp": "af1250c70a7d1ebf", "pipe_xu_pct": 39.2, "pipe_fma_pct": 30.3, "pipe_fma_cycles_pct": 44.4,
+             "issue_active_pct": 66.4, "thread_instr_per_point": 494}
 
 
 def kernel_stamp() -> str:
@@ -488,7 +488,7 @@ def time_workload(name, torch, grad=False, rows=None, steps=5, warmup=2, mhz=SM_
         theta_np = np.ascontiguousarray(theta_np[:rows])
         gal_idx = None if gal_idx is None else np.ascontiguousarray(gal_idx[:rows])
     B = theta_np.shape[0]
-    model.tune(B, gal_idx)
+    model.tune(B, gal_idx, grad=grad)
     theta = torch.from_numpy(theta_np).cuda()
     out = torch.empty(B, dtype=torch.float64, device="cuda")
     if grad:
@@ -624,7 +624,7 @@ def run_ours(args):
         theta_np = np.ascontiguousarray(theta_np[:args.rows])
         gal_idx = None if gal_idx is None else np.ascontiguousarray(gal_idx[:args.rows])
     if not args.no_tune:
-        model.tune(theta_np.shape[0], gal_idx)
+        model.tune(theta_np.shape[0], gal_idx, grad=args.grad)
     B, P = theta_np.shape
     if args.grad:
         def call(th, out):

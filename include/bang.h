@@ -246,14 +246,19 @@ bang_status bang_loglike_batch_noalloc(bang_model *m, const float *theta, const 
 bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t *gal_idx, int B, double *logL,
                               void *stream);
 
-/* Chooses launch parameters (kernel form, fine rows per block step and spaxel-row bands per
- * row of the forward kernel; the gradient call's forward rows per step and the adjoint's
- * fine rows per work item) for batches of B rows by timing candidates on the device; the
- * choice is cached in the model.
+/* Chooses the launch parameters of bang_loglike_batch (kernel form, fine rows per block
+ * step, spaxel-row bands per row) for batches of B rows by timing candidates on the device;
+ * the choice is cached in the model.
  * With a host gal_idx (or NULL: galaxy 0 for every row) it applies to later calls with that
  * same gal_idx and B; with a device gal_idx (read here, this call being synchronous) it
  * applies to every later call of B rows with a device gal_idx. */
 bang_status bang_model_tune(bang_model *m, const int32_t *gal_idx, int B);
+
+/* As bang_model_tune, and then the launch parameters of bang_loglike_grad_batch for the same
+ * batches (the forward seed pass's fine rows per block step, the adjoint's fine rows per
+ * work item), timed on whole logL + gradient calls.  Synchronous; a gradient call costs a
+ * few times a logL call, so this takes correspondingly longer. */
+bang_status bang_model_tune_grad(bang_model *m, const int32_t *gal_idx, int B);
 
 /* The launch shape bang_loglike_batch (grad = 0) or bang_loglike_grad_batch (grad = 1)
  * would use for (gal_idx, B), after any bang_model_tune: info[11] (host) receives

@@ -61,6 +61,7 @@ _SIGNATURES = {
     "bang_loglike_batch_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "bang_loglike_fp64": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP]),
     "bang_model_tune": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "bang_model_tune_grad": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "bang_model_launch_info": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     "bang_last_error": (ctypes.c_char_p, []),
     "bang_checked_build": (ctypes.c_int, []),

@@ -1465,8 +1465,25 @@ bang_status bang_model_launch_info(bang_model* m, const int32_t* gal_idx, int B,
 // spaxel-row bands per row) candidate on this batch shape, then logL + gradient calls for
 // the seed pass's rows per step and the adjoint's band height, and keeps the fastest for
 // later calls.
+namespace {
+bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad);
+}  // namespace
+
 bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   bang::NvtxRange nvtx("bang_model_tune");
+  return tune_paths(m, gal_idx, B, false);
+}
+
+bang_status bang_model_tune_grad(bang_model* m, const int32_t* gal_idx, int B) {
+  bang::NvtxRange nvtx("bang_model_tune_grad");
+  return tune_paths(m, gal_idx, B, true);
+}
+
+}  // extern "C"
+
+namespace {
+
+bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) {
   g_last_error.clear();
   if (!m) return fail(BANG_E_INVALID_ARG, "null model");
   if (B < 1) return fail(BANG_E_INVALID_ARG, "B < 1");
@@ -1502,6 +1519,11 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   BANG_CUDA(cudaMemcpy(m->stage_theta.p, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice));
   BANG_CUDA(m->stage_out.reserve(sizeof(double) * B));
   const uint64_t skey = dgal ? device_key(B) : shape_key(hgal, B);
+  bang_model::Tuning prior;   // an earlier gradient choice survives a forward-only tuning
+  {
+    auto t = m->tuned.find(skey);
+    if (t != m->tuned.end()) prior = t->second;
+  }
   std::vector<int> bands = {0};
   if (B < 4 * m->num_sms)
     for (int nb : {1, 2, 4, 8, 16})
@@ -1551,7 +1573,7 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   }
   // the gradient path: the forward seed pass's rows per step, then the adjoint's band height
   // (fine rows per work item), each timed on whole logL + gradient calls
-  {
+  if (grad) {
     float best_g = 1e30f;
     int best_rows = 0, best_sg = best_t.G;
     struct Cand {
@@ -1597,6 +1619,9 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
     }
     best_t.adj_G = best_rows;
     best_t.seed_G = best_sg;
+  } else {
+    best_t.adj_G = prior.adj_G;
+    best_t.seed_G = prior.seed_G;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1605,4 +1630,4 @@ bang_status bang_model_tune(bang_model* m, const int32_t* gal_idx, int B) {
   return bang::check_faults(st);
 }
 
-}  // extern "C"
+}  // namespace

@@ -192,9 +192,12 @@ class Model:
             off += k
         return out
 
-    def tune(self, B: int, gal_idx=None):
+    def tune(self, B: int, gal_idx=None, grad: bool = False):
+        """Autotune the launch shape for batches of B rows (with grad, the logL + gradient
+        call's shape as well: bang_model_tune_grad)."""
         gi, gptr = self._gal_idx(gal_idx, B)
-        _lib.check(_lib.lib().bang_model_tune(self._h, gptr, B))
+        fn = _lib.lib().bang_model_tune_grad if grad else _lib.lib().bang_model_tune
+        _lib.check(fn(self._h, gptr, B))
 
     def launch_info(self, B: int, gal_idx=None, grad: bool = False) -> dict:
         """The launch shape a call on (gal_idx, B) would use (bang_model_launch_info)."""

@@ -156,7 +156,7 @@ def test_full_size_adjoint_workload_sampled_rows(Model):
     ds = Dataset(wl.galaxies[0], tt, seed=synth.dataset_seed(wid))
     theta = synth.draw_theta_batch(box, tt, wl.batch, synth.batch_seed(wid)).astype(np.float32)
     m = Model(ds.model_galaxy())
-    m.tune(wl.batch)                               # the launch shape bench.py times
+    m.tune(wl.batch, grad=True)                    # the launch shape bench.py times
     logL, grad = m.loglike_grad(torch.from_numpy(theta).cuda())
     grad = grad.cpu().numpy()
     pick = np.array([0, 255])

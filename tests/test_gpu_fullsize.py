@@ -139,7 +139,7 @@ def test_largest_workload_full_size(Model):
     import oracle
     Bg = 1024
     tg = torch.from_numpy(theta[:Bg]).cuda()
-    m.tune(Bg)
+    m.tune(Bg, grad=True)
     lg, g = m.loglike_grad(tg)
     g = g.cpu().numpy()
     ds = dss[0]
