@@ -4,14 +4,21 @@
 Default workload: 1024 parameter vectors against one 80x80-spaxel galaxy with 5x5
 oversampling and a Gaussian PSF of FWHM 2.5" (Dehnen bulge with gamma in [0, 2], one
 exponential disc, NFW halo, 64 radial quadrature nodes), float32 compute with float64
-chi-square accumulation.  One step = logL of the whole batch (one persistent launch).
+chi-square accumulation.  One step = logL of the whole batch (one persistent launch, in the
+shape bang_model_tune chose for it).
 
 Prints one JSON line: device-timed evals/s (`value`), end-to-end evals/s through the C
-ABI with host buffers (`e2e`), the roofline of the dominant kernel, SM clocks sampled
-during the timed region, the GPU, its SM count and the host's cores (`device`), and the
-FP64 CPU oracle timed on a bounded sample (`cpu_baseline`, whose `parity` compares the
-oracle's chi^2 of the rows it evaluated with the timed batch's logL).  ``--impl
-reference`` times the oracle alone in the same format.
+ABI with host buffers (`e2e`), the roofline of the dominant kernel (the SFU and FP32 work
+of the step's own algorithm against the measured per-SM issue rates), the launch shape,
+SM clocks sampled during the timed region, the GPU, its SM count and the host's cores
+(`device`), and the FP64 CPU oracle timed on a bounded sample (`cpu_baseline`, whose
+`parity` compares the oracle's chi^2 of the rows it evaluated with the timed batch's logL).
+Side lines, each in one tuned launch with its own roofline and launch shape: the paper's
+one-kernel-per-task form on the same batch (`plain_gpu`), logL + gradient for 256 rows
+(`fwd_adjoint`), the 64-galaxy uneven batch (`uneven`, with the plain form), the 128x128
+Moffat two-disc workload (`largest`, with the plain form on 32 rows; `largest_grad`, 1024
+rows), the single row's latency in three forms (`single`) and the radial-table option
+(`radial_table`).  ``--impl reference`` times the oracle alone in the same format.
 
 Multi-GPU: launched by torchrun, every rank evaluates its own batch (weak scaling, no
 collective on the data path); the timing is the maximum over ranks.
