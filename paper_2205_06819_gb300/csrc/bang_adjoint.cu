@@ -21,8 +21,8 @@
 // with Su, Qu the u-weighted and Sl, Ql the (ln u)-weighted sums.  Nothing is stored
 // between the forward and the backward evaluation: the quadrature is recomputed.
 // Work items are bands of fine rows (no halo is needed: the seeds live in global memory).
-// Per-thread float32 partials are reduced per block in float64 into the work item's own
-// slots; grad_out_kernel sums a row's items in item order (no atomics) and maps the
+// Per-thread float32 partials are reduced per block (sums of four lanes in float32, the
+// rest in float64) into the work item's own slots; grad_out_kernel sums a row's items in item order (no atomics) and maps the
 // per-model constants to theta in float64.
 #include <cuda_runtime.h>
 
@@ -69,10 +69,39 @@ enum {
 constexpr int kPerDisc = 7;
 enum { D_SDC = 0, D_VDC, D_IRD, D_HIRD, D_LD, D_KS, D_OMK };
 
-__device__ __forceinline__ double warp_sum(double v) {
+// One level of a warp reduce-scatter: a lane holds the partial sums of 2h slots and keeps
+// the half its lane bit o selects (upper if set), adding the partner lane's copy of it.
+template <int H, typename T>
+__device__ __forceinline__ void scatter_level(const T* v, T* out, int lane, int o) {
+  const bool up = (lane & o) != 0;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
+  for (int j = 0; j < H; ++j) {
+    const T keep = up ? v[j + H] : v[j], send = up ? v[j] : v[j + H];
+    out[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+}
+
+// Warp sum of each of N <= 32 per-lane float32 accumulators, as a reduce-scatter: lane k
+// returns the sum over the warp's 32 lanes of acc[k] (lanes k >= N return 0).  The first
+// two levels (sums of 2 and 4 lanes) add in float32, the last three in float64, in a fixed
+// order.  A float64 add issues at 1/64 the float32 rate here, and a full-width float64
+// shuffle sum of every accumulator (5 adds each) took a fifth of the FP64 pipe's time;
+// this form needs 8 conversions and 7 float64 adds per lane whatever N is.
+template <int N>
+__device__ __forceinline__ double warp_sum_scatter(const float* acc, int lane) {
+  static_assert(N > 16 && N <= 32, "the reduce-scatter expects 17 to 32 accumulators");
+  float v32[32], v16[16], v8[8];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v32[j] = j < N ? acc[j] : 0.f;
+  scatter_level<16>(v32, v16, lane, 16);
+  scatter_level<8>(v16, v8, lane, 8);
+  double d8[8], d4[4], d2[2], d1[1];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) d8[j] = (double)v8[j];
+  scatter_level<4>(d8, d4, lane, 4);
+  scatter_level<2>(d4, d2, lane, 2);
+  scatter_level<1>(d2, d1, lane, 1);
+  return lane < N ? d1[0] : 0.0;
 }
 
 struct BulgeDer {
@@ -391,7 +420,7 @@ __device__ __forceinline__ void point_vjp(const ModelConst& m, float X, float Y,
 
 // d logL / d theta from the reduced constant adjoints and the row's decode terms T
 // (float64, one thread).
-__device__ void constants_to_theta(const float* __restrict__ th, const double* T, int nd, int halo_kind,
+__device__ void constants_to_theta(const float* __restrict__ th, const float* T, int nd, int halo_kind,
                                    int bulge_kind, const double* s, double* g) {
   const double ln10 = 2.302585092994045684;
   const double ci = T[0], si = T[1];
@@ -598,11 +627,11 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
         point_vjp<NQ, ND>(mc, X, Y, make_float4(sxy.x, sxy.y, szw.x, szw.y), acc, tab, a.table_T, nodew, tailc);
       }
     }
-    // float64 block reduction of the adjoints, then theta-space gradient (one thread)
-#pragma unroll
-    for (int k = 0; k < NACC; ++k) {
-      const double v = warp_sum((double)acc[k]);
-      if (lane == 0) red[warp][k] = v;
+    // block reduction of the adjoints: lane k of each warp ends with the warp's sum of
+    // accumulator k, then one thread per accumulator sums the warps in float64
+    {
+      const double v = warp_sum_scatter<NACC>(acc, lane);
+      if (lane < NACC) red[warp][lane] = v;
     }
     __syncthreads();
     if (tid < NACC) {   // one thread per accumulator: sum over warps into the item's slots
@@ -633,8 +662,8 @@ __global__ void grad_out_kernel(const float* __restrict__ theta, int P, int nd, 
   const float* th = theta + (size_t)b * P;
   const bool ok = theta_in_domain(th, nd, halo_kind, bulge_kind) &&
                   (!gal_idx || (unsigned)gal_idx[b] < (unsigned)n_gal);
-  const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
-  double T[kDecodeTerms];
+  const float v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.f;
+  float T[kDecodeTerms];
 #pragma unroll
   for (int i = 0; i < kDecodeTerms; ++i) T[i] = __shfl_sync(0xffffffffu, v, i);
   double sum = 0.0;

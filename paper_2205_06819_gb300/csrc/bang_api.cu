@@ -773,15 +773,21 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.out_off = p->implicit ? nullptr : p->d_out_off.as<int64_t>();
   a.out_stride = p->out_stride;
   a.queue = p->d_queue.as<int>();
-  a.consts = p->d_consts.as<bang::ModelConst>();
   a.halo_kind = m->opts.halo_kind;
+  a.l10k = bang::decode_l10k_host();
   a.B = p->B;
   a.n_gal = (int)m->gals.size();
   a.out_total = p->out_total;
   const int* row_g = p->implicit ? dgal : p->d_row_g.as<int>();
-  cudaError_t e = bang::launch_decode(theta, m->P, m->opts.n_discs, m->opts.halo_kind, a.gals, row_g, a.n_gal, p->B,
-                                      p->d_consts.as<bang::ModelConst>(), st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (m->opts.bulge_table > 0) {   // the radial tables are built from the decoded rows
+    a.consts = p->d_consts.as<bang::ModelConst>();
+    e = bang::launch_decode(theta, m->P, m->opts.n_discs, m->opts.halo_kind, a.gals, row_g, a.n_gal, p->B,
+                            p->d_consts.as<bang::ModelConst>(), st);
+    if (e != cudaSuccess) return e;
+  } else {                         // each item decodes its row; the adjoint reads what the seed pass stores
+    a.consts_out = mode == bang::kModeSeed ? p->d_consts.as<bang::ModelConst>() : nullptr;
+  }
   if (p->implicit && p->n_rank > 0) {
     e = bang::launch_order(dgal, p->d_rank.as<int>(), a.n_gal, p->n_rank, p->B, p->nb, p->d_order.as<int>(), st);
     if (e != cudaSuccess) return e;

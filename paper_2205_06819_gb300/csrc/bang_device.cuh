@@ -4,8 +4,8 @@
 // isotropic dispersion by a fixed radial quadrature (Sec. 2.2, Eqs. 4 and 6 definitions),
 // circular velocities of bulge (Eq. 2 generalised), NFW halo and exponential discs (Eq. 9,
 // Binney & Tremaine form), Satoh decomposition (Eqs. 10-12) and the light-weighted
-// observables (Eqs. 13-15, 19).  Bulk arithmetic is float32; per-model constants are decoded
-// in float64 once per work item.
+// observables (Eqs. 13-15, 19).  Arithmetic is float32, per-model constants decoded once
+// per row.
 #pragma once
 
 #include <cstdint>
@@ -69,7 +69,7 @@ struct WorkItem {
   int b, g, j0, j1;
 };
 
-// Per-model constants, decoded in float64 and stored as float32 in shared memory.
+// Per-model constants (float32), decoded once per row and held in shared memory.
 struct ModelConst {
   float X0, Y0;            // kpc offset of fine column/row 0 relative to the model centre
   float cpa, spa;          // cos, sin of the position angle
@@ -145,25 +145,28 @@ __device__ inline bool theta_in_domain(const float* __restrict__ th, int nd, int
 //   0 cos i, 1 sin i, 2 cos PA, 3 sin PA, 4 M_b, 5 a, 6 M_200 (or M_h),
 //   7 r_200 = (3 M_200 / (4 pi 200 rho_c))^(1/3) (or R_h), 8 m(c) = ln(1 + c) - c / (1 + c)
 //   (NFW only), 9 M_d1, 10 R_d1, 11 M_d2, 12 R_d2.
-// They reduce to three functions so that the lanes of a warp diverge into three paths, not
-// thirteen: sin (cos x = sin(x + pi/2)), 10^x (r_200 = 10^((log10 M_200 + l10k) / 3) with
-// l10k = log10(3 / (4 pi 200 rho_c))) and ln(1 + c).
+// r_200 is 10^((log10 M_200 + l10k) / 3) with l10k = log10(3 / (4 pi 200 rho_c)).
+// The decode runs in float32 (CUDA's sinf, cosf, exp10f and log1pf, within 2 ulp): the
+// constants are float32 in the model anyway, a float64 operation issues at 1/64 of the
+// float32 rate here, and the float64 form (each constant rounded once) made the decode of
+// one row a 16 us chain of dependent float64 operations (7 us in float32) at no gain in
+// logL against the float64 oracle.
 constexpr int kDecodeTerms = 13;
 
 __device__ inline double decode_l10k() { return log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit)); }
 
-__device__ inline double decode_term(int i, const float* __restrict__ th, int nd, int halo_kind, double l10k) {
-  int kind = 1;   // 0 sin, 1 10^x, 2 ln(1 + x) - x / (1 + x), 3 unused
-  double x = 0.0;
+__device__ inline float decode_term(int i, const float* __restrict__ th, int nd, int halo_kind, double l10k) {
+  int kind = 1;   // 0 sin, 1 10^x, 2 ln(1 + x) - x / (1 + x), 3 unused, 4 cos
+  float x = 0.f;
   switch (i) {
-    case 0: kind = 0; x = (double)th[3] + 0.5 * kPi; break;
+    case 0: kind = 4; x = th[3]; break;
     case 1: kind = 0; x = th[3]; break;
-    case 2: kind = 0; x = (double)th[2] + 0.5 * kPi; break;
+    case 2: kind = 4; x = th[2]; break;
     case 3: kind = 0; x = th[2]; break;
     case 4: x = th[4]; break;
     case 5: x = th[5]; break;
     case 6: x = th[12]; break;
-    case 7: x = halo_kind == 0 ? ((double)th[12] + l10k) / 3.0 : (double)th[13]; break;
+    case 7: x = halo_kind == 0 ? (float)(((double)th[12] + l10k) / 3.0) : th[13]; break;
     case 8: kind = halo_kind == 0 ? 2 : 3; x = th[13]; break;
     case 9: x = th[7]; break;
     case 10: x = th[8]; break;
@@ -171,50 +174,53 @@ __device__ inline double decode_term(int i, const float* __restrict__ th, int nd
     case 12: kind = nd == 2 ? 1 : 3; x = th[16]; break;
     default: kind = 3;
   }
-  if (kind == 0) return sin(x);
-  if (kind == 1) return exp10(x);
-  if (kind == 2) return log1p(x) - x / (1.0 + x);
-  return 0.0;
+  if (kind == 0) return sinf(x);
+  if (kind == 4) return cosf(x);
+  if (kind == 1) return exp10f(x);
+  if (kind == 2) return log1pf(x) - x / (1.0f + x);
+  return 0.f;
 }
 
-// The per-model constants from theta and its decode terms T[kDecodeTerms] (float64
-// arithmetic, rounded to float32 once).
-__device__ inline void decode_finish(const float* __restrict__ th, const double* T, int nd, int halo_kind,
+// The per-model constants from theta and its decode terms T[kDecodeTerms] (float32; the
+// centre offsets X0, Y0 are one float64 subtraction, rounded once).
+__device__ inline void decode_finish(const float* __restrict__ th, const float* T, int nd, int halo_kind,
                                      const GalDev& g, ModelConst& m) {
-  const double ci = T[0], si = T[1];
+  const float two_pi = (float)(2.0 * kPi), G = (float)kG;
+  const float ci = T[0], si = T[1];
   m.X0 = (float)(g.xoff_kpa - (double)th[0]);
   m.Y0 = (float)(g.yoff_kpa - (double)th[1]);
-  m.cpa = (float)T[2];
-  m.spa = (float)T[3];
-  m.inv_ci = (float)(1.0 / ci);
-  m.si = (float)si;
+  m.cpa = T[2];
+  m.spa = T[3];
+  m.inv_ci = 1.0f / ci;
+  m.si = si;
   // bulge
-  const double Mb = T[4], a = T[5], gam = g.bulge_kind == 0 ? (double)th[6] : (double)g.bulge_kind;
-  m.inv_a = (float)(1.0 / a);
-  m.ngam = (float)(-gam);
-  m.g4 = (float)(gam - 4.0);
-  m.g3 = (float)(3.0 - 2.0 * gam);
-  m.three_mg = (float)(3.0 - gam);
-  m.cS = (float)((3.0 - gam) * Mb / (2.0 * kPi * a * a));
-  m.cQ = (float)(kG * (3.0 - gam) * Mb * Mb / (2.0 * kPi * a * a * a));
-  m.vb_c = (float)(kG * Mb / a);
-  m.vb_r = (float)(kG * Mb);
+  const float Mb = T[4], a = T[5], gam = g.bulge_kind == 0 ? th[6] : (float)g.bulge_kind;
+  const float ia = 1.0f / a;
+  m.inv_a = ia;
+  m.ngam = -gam;
+  m.g4 = gam - 4.0f;
+  m.g3 = 3.0f - 2.0f * gam;
+  m.three_mg = 3.0f - gam;
+  m.cS = (3.0f - gam) * Mb * (ia * ia) / two_pi;
+  m.cQ = G * (3.0f - gam) * (Mb * Mb) * (ia * ia * ia) / two_pi;
+  m.vb_c = G * Mb * ia;
+  m.vb_r = G * Mb;
   m.bulge_fit = g.bulge_kind;
   if (g.bulge_kind != 0) {   // closed-form fits: Sigma = (M / a^2) F_S, Sigma sigma^2 = (G M^2 / a^3) F_Q
-    m.cS = (float)(Mb / (a * a));
-    m.cQ = (float)(kG * Mb * Mb / (a * a * a));
+    m.cS = Mb * (ia * ia);
+    m.cQ = G * (Mb * Mb) * (ia * ia * ia);
   }
-  m.Lb = (float)(1e-6 / (double)th[10]);
+  m.Lb = 1e-6f / th[10];
   // halo
   m.hern = halo_kind;
   if (halo_kind == 0) {   // NFW: vh^2 = vh_c m(r/rs) / r
-    const double M200 = T[6], c = th[13], r200 = T[7], mc = T[8];
-    m.inv_rs = (float)(c / r200);
-    m.vh_c = (float)(kG * M200 / mc);
+    const float M200 = T[6], c = th[13], r200 = T[7], mc = T[8];
+    m.inv_rs = c / r200;
+    m.vh_c = G * M200 / mc;
   } else {                // Hernquist (Eq. 2 with M_h, R_h): vh^2 = vh_c x / (1 + x)^2, x = r / R_h
-    const double Mh = T[6], Rh = T[7];
-    m.inv_rs = (float)(1.0 / Rh);
-    m.vh_c = (float)(kG * Mh / Rh);
+    const float Mh = T[6], Rh = T[7];
+    m.inv_rs = 1.0f / Rh;
+    m.vh_c = G * Mh / Rh;
   }
   // discs
   for (int j = 0; j < 2; ++j) {
@@ -223,26 +229,46 @@ __device__ inline void decode_finish(const float* __restrict__ th, const double*
       continue;
     }
     const int o = j == 0 ? 7 : 15;
-    const double Md = T[9 + 2 * j], Rd = T[10 + 2 * j], k = th[o + 2];
-    const double ml = j == 0 ? th[11] : th[18];
-    m.inv_Rd[j] = (float)(1.0 / Rd);
-    m.half_inv_Rd[j] = (float)(0.5 / Rd);
-    m.two_Rd[j] = (float)(2.0 * Rd);
-    m.vd_c[j] = (float)(2.0 * kG * Md / Rd);
-    m.Sd_c[j] = (float)(Md / (2.0 * kPi * Rd * Rd * ci));
-    m.Ld[j] = (float)(1e-6 / ml);
-    m.ks[j] = (float)(-k * si);
-    m.omk[j] = (float)((1.0 - k * k) / 3.0);
+    const float Md = T[9 + 2 * j], Rd = T[10 + 2 * j], k = th[o + 2];
+    const float ml = j == 0 ? th[11] : th[18];
+    const float iR = 1.0f / Rd;
+    m.inv_Rd[j] = iR;
+    m.half_inv_Rd[j] = 0.5f * iR;
+    m.two_Rd[j] = 2.0f * Rd;
+    m.vd_c[j] = 2.0f * G * Md * iR;
+    m.Sd_c[j] = Md * (iR * iR) / (two_pi * ci);
+    m.Ld[j] = 1e-6f / ml;
+    m.ks[j] = -k * si;
+    m.omk[j] = (1.0f - k * k) / 3.0f;
   }
   m.vsys = th[14];
   m.flux = g.flux;
+}
+
+// theta -> per-model constants by one warp (all 32 lanes call it): lane i < kDecodeTerms
+// evaluates decode term i (the terms are independent, so a row costs the latency of one
+// transcendental, not thirteen in a chain), lane 0 gathers them and writes m.  A row outside
+// the parameter domain, or with ok_gal false, gets m.valid = 0 and no other field.
+__device__ inline void decode_row_warp(const float* __restrict__ th, int nd, int halo_kind, const GalDev& g,
+                                       bool ok_gal, double l10k, int lane, ModelConst& m) {
+  const bool ok = ok_gal && theta_in_domain(th, nd, halo_kind, g.bulge_kind);
+  const float v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.f;
+  float T[kDecodeTerms];
+#pragma unroll
+  for (int i = 0; i < kDecodeTerms; ++i) T[i] = __shfl_sync(0xffffffffu, v, i);
+  if (lane != 0) return;
+  m.valid = 0;
+  if (ok) {
+    decode_finish(th, T, nd, halo_kind, g, m);
+    m.valid = 1;
+  }
 }
 
 // theta -> per-model constants by one thread; 0 for a row outside the domain.
 __device__ inline int decode_model(const float* __restrict__ th, int nd, int halo_kind, const GalDev& g,
                                    ModelConst& m) {
   if (!theta_in_domain(th, nd, halo_kind, g.bulge_kind)) return 0;
-  double T[kDecodeTerms];
+  float T[kDecodeTerms];
   const double l10k = decode_l10k();
   for (int i = 0; i < kDecodeTerms; ++i) T[i] = decode_term(i, th, nd, halo_kind, l10k);
   decode_finish(th, T, nd, halo_kind, g, m);

@@ -150,12 +150,18 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
       BANG_NEXT_ITEM(it);
       continue;
     }
-    if (tid == 0) {
-      gs = a.gals[w.g];
-      if (a.consts) mc = a.consts[w.b];
-      else mc.valid = decode_model(a.theta + (size_t)w.b * a.P, ND, a.halo_kind, gs, mc);
+    if (a.consts) {
+      if (tid == 0) {
+        gs = a.gals[w.g];
+        mc = a.consts[w.b];
+      }
+    } else if (tid < 32) {   // warp 0 decodes the row (a few microseconds, once per item)
+      if (tid == 0) gs = a.gals[w.g];
+      decode_row_warp(a.theta + (size_t)w.b * a.P, ND, a.halo_kind, a.gals[w.g], true, a.l10k, tid, mc);
     }
     __syncthreads();
+    // the gradient's forward pass leaves each row's constants for the adjoint (first band)
+    if (a.consts_out && tid == 0 && w.j0 == 0) a.consts_out[w.b] = mc;
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx;
     const int NA = (L + os - 1) / os;                       // open spaxel rows
     // separable taps stored twice, (t, t): a 64-bit load gives the pair the packed
@@ -400,9 +406,8 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
   }
 }
 
-// One warp per row: lane i < kDecodeTerms evaluates decode term i (the float64
-// transcendentals are independent), lane 0 gathers them and finishes the row, so a row
-// costs the latency of one transcendental instead of thirteen in a chain.
+// One warp per row (decode_row_warp): the rows' constants ahead of the radial tables, which
+// are built from them.
 __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, int halo_kind,
                               const GalDev* __restrict__ gals, const int* __restrict__ row_g, int n_gal, int B,
                               double l10k, ModelConst* __restrict__ out) {
@@ -413,19 +418,9 @@ __global__ void decode_kernel(const float* __restrict__ theta, int P, int nd, in
   const int g = row_g ? row_g[b] : 0;
   const bool gal_ok = (unsigned)g < (unsigned)n_gal && BANG_IN(g, n_gal, kSiteDecodeGal);
   const GalDev& gal = gals[gal_ok ? g : 0];
-  const bool ok = gal_ok && theta_in_domain(th, nd, halo_kind, gal.bulge_kind);
-  const double v = (ok && lane < kDecodeTerms) ? decode_term(lane, th, nd, halo_kind, l10k) : 0.0;
-  double T[kDecodeTerms];
-#pragma unroll
-  for (int i = 0; i < kDecodeTerms; ++i) T[i] = __shfl_sync(0xffffffffu, v, i);
-  if (lane != 0) return;
   ModelConst m;
-  m.valid = 0;
-  if (ok) {
-    decode_finish(th, T, nd, halo_kind, gal, m);
-    m.valid = 1;
-  }
-  out[b] = m;
+  decode_row_warp(th, nd, halo_kind, gal, gal_ok, l10k, lane, m);
+  if (lane == 0) out[b] = m;
 }
 
 // logL[b] = -chi^2/2 - const from the per-item partial sums (items of row b are contiguous).
@@ -558,10 +553,12 @@ cudaError_t launch_forward(const FwdArgs& a, int n_quad, int n_discs, int psf2d,
 
 size_t model_const_bytes() { return sizeof(ModelConst); }
 
+double decode_l10k_host() { return std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit)); }
+
 cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
                           int n_gal, int B, ModelConst* out, cudaStream_t st) {
   constexpr int kRowsPerBlock = 4;   // 4 warps of 32 lanes, one row each
-  const double l10k = std::log10(3.0 / (4.0 * kPi * 200.0 * kRhoCrit));
+  const double l10k = decode_l10k_host();
   decode_kernel<<<(B + kRowsPerBlock - 1) / kRowsPerBlock, 32 * kRowsPerBlock, 0, st>>>(
       theta, P, n_discs, halo_kind, gals, row_g, n_gal, B, l10k, out);
   return cudaGetLastError();
@@ -796,6 +793,7 @@ extern "C" bang_status bang_loglike_batch_noalloc(bang_model* m, const float* th
   a.G = rows_per_step;
   a.partial = partial;
   a.out_off = nullptr;
+  a.l10k = decode_l10k_host();
   a.B = B;
   a.n_gal = v.n_gal;
   const int grid = std::min(B, per_sm * v.num_sms);

@@ -47,7 +47,9 @@ struct FwdArgs {
   int P;
   int halo_kind;            // 0 NFW, 1 Hernquist (used when consts is NULL)
   const GalDev* gals;
-  const ModelConst* consts; // [B] decoded rows (NULL: each block decodes its row itself)
+  const ModelConst* consts; // [B] decoded rows (NULL: warp 0 of the block decodes the item's row)
+  ModelConst* consts_out;   // with consts NULL (may be NULL): each row's constants, stored by its first band
+  double l10k;              // log10(3 / (4 pi 200 rho_c)), for the decode when consts is NULL
   const WorkItem* items;    // [n_items], items of one row contiguous, rows in order; NULL: implicit items,
                             // item i is band i % nb of row i / nb against galaxy gal_idx[i / nb]
   const int* gal_idx;       // implicit items: device [B] galaxy of each row (NULL = galaxy 0)
@@ -145,6 +147,7 @@ cudaError_t launch_grad_out(const float* theta, int P, int n_discs, int halo_kin
                             int adj_nb = 1, int nb = 1, const int* gal_idx = nullptr, int n_gal = 0);
 size_t model_const_bytes();
 // row_g NULL: galaxy 0 for every row; a galaxy index outside [0, n_gal) makes the row invalid.
+double decode_l10k_host();   // log10(3 / (4 pi 200 rho_c)), the r_200 decode term's offset
 cudaError_t launch_decode(const float* theta, int P, int n_discs, int halo_kind, const GalDev* gals, const int* row_g,
                           int n_gal, int B, ModelConst* out, cudaStream_t st);
 cudaError_t upload_nodes_adjoint(const float* cm1, const float* lc, const float* ws, const float* wq);
