@@ -280,6 +280,7 @@ struct DevBuf {
 struct Plan {
   uint64_t key = 0;
   int B = 0, n_items = 0, G = 4, grid = 0, blocks_per_sm = 0;
+  int max_W = 0;   // widest fine grid among the plan's galaxies (chunk_pts = G max_W)
   size_t smem = 0;
   int mode = 0;
   int kmode = 0;   // the forward kernel form launched (kModeLogL2 for a tuned logL batch)
@@ -519,6 +520,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   for (int b = 0; b < B; ++b)
     if (m->gals[p->row_g[b]].psf_kind != psf2d)
       return fail(BANG_E_UNSUPPORTED, "a batch mixes Gaussian and Moffat PSF galaxies");
+  p->max_W = max_W;
   p->G = (mode == bang::kModeSeed && tune.seed_G > 0) ? tune.seed_G : tune.G;
   // shared memory: the NA bound uses the smallest os among rows with the largest L, so
   // take it per galaxy
@@ -672,6 +674,7 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
   p->out_stride = n4_max;
   p->out_total = (int64_t)B * n4_max;
   p->G = (mode == bang::kModeSeed && tune.seed_G > 0) ? tune.seed_G : tune.G;
+  for (const bang::GalDev& G : m->gals) p->max_W = std::max(p->max_W, G.W);
   size_t smem = 0;
   for (const bang::GalDev& G : m->gals)
     smem = std::max(smem, bang::forward_smem_bytes(G.L, G.os, G.nx, G.W, p->G, psf2d, m->opts.bulge_table));
@@ -766,6 +769,7 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.order = p->d_order.as<int>();
   a.n_items = p->n_items;
   a.G = p->G;
+  a.chunk_pts = p->G * p->max_W;
   a.partial = p->d_partial.as<double>();
   a.maps = mode == bang::kModeMaps ? out : nullptr;
   a.seed = mode == bang::kModeSeed ? out : nullptr;

@@ -175,7 +175,18 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
     const int ntaps = PSF == 0 ? L : Lq * Lq;
     float4* acc = reinterpret_cast<float4*>(smem_raw + (((size_t)ntaps * (PSF == 0 ? 8 : 4) + 15) / 16) * 16);
     float4* stage = acc + (size_t)NA * nx;
-    float* tab = a.tables ? reinterpret_cast<float*>(stage + 2 * (size_t)a.G * W) : nullptr;
+    // fine rows per chunk: a.G, or for a narrower galaxy of a mixed batch the rows that
+    // hold the widest galaxy's a.chunk_pts points, as far as the launch's shared memory
+    // goes (fewer barriers, and whole 64-point grabs for every warp between them)
+    int Gc = a.G;
+    if (a.chunk_pts > 0) {
+      const size_t used = (size_t)(reinterpret_cast<unsigned char*>(stage) - smem_raw) +
+                          (a.tables ? sizeof(float) * (size_t)(kTabHdr + 4 * a.table_T) : 0);
+      const size_t dyn = dynamic_smem_bytes();
+      const int cap = dyn > used ? (int)((dyn - used) / (2 * sizeof(float4) * (size_t)W)) : 0;
+      Gc = max(a.G, min(a.chunk_pts / W, cap));
+    }
+    float* tab = a.tables ? reinterpret_cast<float*>(stage + 2 * (size_t)Gc * W) : nullptr;
     float* out = nullptr;
     const int64_t ooff = a.out_off ? a.out_off[w.b] : (int64_t)w.b * a.out_stride;
     if (MODE == kModeMaps) out = a.maps + ooff;
@@ -183,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
     // checked build: the layout fits the launch's shared memory, a fine row holds every
     // stencil read, the item's spaxel rows, output block and radial table are in range
     if (!BANG_IN((tab ? reinterpret_cast<const unsigned char*>(tab + kTabHdr + 4 * a.table_T)
-                      : reinterpret_cast<const unsigned char*>(stage + 2 * (size_t)a.G * W)) - smem_raw - 1,
+                      : reinterpret_cast<const unsigned char*>(stage + 2 * (size_t)Gc * W)) - smem_raw - 1,
                  dynamic_smem_bytes(), kSiteFwdSmem) ||
         !BANG_IN((nx - 1) * os + L - 1, W, kSiteFwdStencil) || !BANG_IN(w.j0, w.j1, kSiteFwdSpaxel) ||
         !BANG_IN(w.j1 - 1, gs.ny, kSiteFwdSpaxel) ||
@@ -240,18 +251,18 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
     double chi_thread = 0.0, vsys_thread = 0.0;
     const int y_begin = w.j0 * os;
     const int y_end = (w.j1 - 1) * os + L;                   // exclusive
-    const int nchunks = (y_end - y_begin + a.G - 1) / a.G;
+    const int nchunks = (y_end - y_begin + Gc - 1) / Gc;
     const float pk = gs.pitch_kpa;
     const float inv_W = 1.0f / (float)W;
 
-    // Evaluation of chunk c (a.G fine rows) into stage buffer c & 1.  Warps take 32 points
+    // Evaluation of chunk c (Gc fine rows) into stage buffer c & 1.  Warps take 32 points
     // at a time from the chunk's shared counter, so warps that are busy with the stencil
     // of the previous chunk simply take fewer points.
     auto eval_chunk = [&](int c) {
-      const int y0 = y_begin + c * a.G;
-      const int npts = min(a.G, y_end - y0) * W;
-      float4* st = stage + (size_t)(c & 1) * a.G * W;
-      if (!BANG_IN(npts, a.G * W + 1, kSiteFwdStage)) return;
+      const int y0 = y_begin + c * Gc;
+      const int npts = min(Gc, y_end - y0) * W;
+      float4* st = stage + (size_t)(c & 1) * Gc * W;
+      if (!BANG_IN(npts, Gc * W + 1, kSiteFwdStage)) return;
       if (MODE == kModeLogL2) {   // two points per thread: their independent chains interleave
         for (;;) {
           int base = 0;
@@ -294,9 +305,9 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
     for (int c = 0; c < nchunks; ++c) {
       // stage c & 1 holds chunk c; its counter is free again (next used by chunk c + 2)
       if (tid == 0) chunk_ctr[c & 1] = 0;
-      const int y0 = y_begin + c * a.G;
-      const int G = min(a.G, y_end - y0);
-      const float4* stage_c = stage + (size_t)(c & 1) * a.G * W;
+      const int y0 = y_begin + c * Gc;
+      const int G = min(Gc, y_end - y0);
+      const float4* stage_c = stage + (size_t)(c & 1) * Gc * W;
       // filter chunk c into the open spaxel rows; finish the rows that complete
       if (PSF == 0) {
         for (int i = tid; i < nx; i += kThreads) {
