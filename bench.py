@@ -55,11 +55,11 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 122.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "590593baf49d4c1a", "bytes_per_launch": 405248}
+NCU_TRAFFIC = {"stamp": "e43937c975946e35", "bytes_per_launch": 399872}
 # Pipe activity of the forward kernel from the same kind of capture (ncu --set full on one
 # timed launch of the tuned benchmark batch): SFU (xu) and FMA pipes, issue active, thread
 # instructions per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "590593baf49d4c1a", "pipe_xu_pct": 39.7, "pipe_fma_pct": 30.5, "pipe_fma_cycles_pct": 45.0,
+NCU_PIPES = {"stamp": "e43937c975946e35", "pipe_xu_pct": 39.7, "pipe_fma_pct": 30.6, "pipe_fma_cycles_pct": 45.0,
              "issue_active_pct": 66.6, "thread_instr_per_point": 490}
 
 

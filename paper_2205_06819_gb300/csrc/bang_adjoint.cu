@@ -22,8 +22,8 @@
 // between the forward and the backward evaluation: the quadrature is recomputed.
 // Work items are bands of fine rows (no halo is needed: the seeds live in global memory).
 // Per-thread float32 partials are reduced per block (sums of four lanes in float32, the
-// rest in float64) into the work item's own slots; grad_out_kernel sums a row's items in item order (no atomics) and maps the
-// per-model constants to theta in float64.
+// rest in float64) into the work item's own slots; grad_out_kernel sums a row's items in
+// item order (no atomics) and maps the per-model constants to theta in float64.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -761,10 +761,12 @@ __global__ void table_kernel(const ModelConst* __restrict__ consts, const GalDev
 
 constexpr int adj_min_blocks(int nd, bool table) { return nd == 1 && !table ? 4 : 3; }
 
+// minb 3 runs the one-disc quadrature form at 3 blocks per SM (80 registers, the table
+// form's instance, which handles tables == NULL by the per-point quadrature)
 template <int NQ, int ND>
-cudaError_t launch_nd(const AdjArgs& a, int psf2d, int grid, size_t smem, cudaStream_t st) {
+cudaError_t launch_nd(const AdjArgs& a, int psf2d, int minb, int grid, size_t smem, cudaStream_t st) {
   constexpr int kQuad = adj_min_blocks(ND, false), kTab = adj_min_blocks(ND, true);
-  if (a.tables) {
+  if (a.tables || minb == kTab) {
     if (psf2d) adjoint_kernel<NQ, ND, 1, kTab><<<grid, kAdjThreads, smem, st>>>(a);
     else adjoint_kernel<NQ, ND, 0, kTab><<<grid, kAdjThreads, smem, st>>>(a);
   } else {
@@ -787,21 +789,28 @@ size_t adjoint_smem_bytes(int L, int os, int nx, int G, int psf2d, int table_T) 
 
 int64_t table_row_floats(int T, int derivs) { return kTabHdr + (int64_t)(derivs ? 8 : 4) * T; }
 
-const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d, int table) {
+int adjoint_minb(int n_discs, int table, int want) {
+  if (n_discs == 1 && !table && (want == 3 || want == 4)) return want;
+  return adj_min_blocks(n_discs, table != 0);
+}
+
+const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d, int table, int minb) {
 #define BANG_PICK(NQ, ND, PSF)                                                                        \
   if (n_quad == NQ && n_discs == ND && psf2d == PSF)                                                  \
-    return table ? (const void*)adjoint_kernel<NQ, ND, PSF, adj_min_blocks(ND, true)>                 \
-                 : (const void*)adjoint_kernel<NQ, ND, PSF, adj_min_blocks(ND, false)>;
+    return (table || minb == adj_min_blocks(ND, true))                                                \
+               ? (const void*)adjoint_kernel<NQ, ND, PSF, adj_min_blocks(ND, true)>                   \
+               : (const void*)adjoint_kernel<NQ, ND, PSF, adj_min_blocks(ND, false)>;
   BANG_PICK(64, 1, 0) BANG_PICK(64, 1, 1) BANG_PICK(64, 2, 0) BANG_PICK(64, 2, 1)
   BANG_PICK(128, 1, 0) BANG_PICK(128, 1, 1) BANG_PICK(128, 2, 0) BANG_PICK(128, 2, 1)
 #undef BANG_PICK
   return nullptr;
 }
 
-cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
+cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int minb, int grid, size_t smem,
                            cudaStream_t st) {
-  if (n_quad == 64) return n_discs == 2 ? launch_nd<64, 2>(a, psf2d, grid, smem, st) : launch_nd<64, 1>(a, psf2d, grid, smem, st);
-  return n_discs == 2 ? launch_nd<128, 2>(a, psf2d, grid, smem, st) : launch_nd<128, 1>(a, psf2d, grid, smem, st);
+  if (n_quad == 64)
+    return n_discs == 2 ? launch_nd<64, 2>(a, psf2d, minb, grid, smem, st) : launch_nd<64, 1>(a, psf2d, minb, grid, smem, st);
+  return n_discs == 2 ? launch_nd<128, 2>(a, psf2d, minb, grid, smem, st) : launch_nd<128, 1>(a, psf2d, minb, grid, smem, st);
 }
 
 cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int n_gal, int B, int n_quad,

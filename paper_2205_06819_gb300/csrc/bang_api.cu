@@ -292,7 +292,7 @@ struct Plan {
   int64_t table_stride = 0;   // floats per row of the radial tables (bulge_table option)
   int bands = 1;
   // adjoint sweep (kModeSeed plans only): bands of fine rows
-  int adj_items = 0, adj_G = 4, adj_grid = 0;
+  int adj_items = 0, adj_G = 4, adj_grid = 0, adj_minb = 0, adj_blocks_per_sm = 0;
   size_t adj_smem = 0;
   DevBuf d_adj_items, d_adj_order, d_adj_row_first;
   // device-index plan (gal_idx in device memory): implicit work items, nb per row and
@@ -380,6 +380,7 @@ struct bang_model {
     int adj_G = 0;   // fine rows per band of the adjoint (0: default policy)
     int pair = 0;    // logL batches: 1 = the two-points-per-thread kernel form (kModeLogL2)
     int seed_G = 0;  // fine rows per block step of the gradient call's forward pass (0: G)
+    int adj_minb = 0;  // blocks per SM of the one-disc quadrature adjoint, 3 or 4 (0: 4)
   };
   std::map<uint64_t, Tuning> tuned;         // batch-shape key -> launch parameters
   std::mutex mu;
@@ -584,7 +585,9 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
       asmem = std::max(asmem, bang::adjoint_smem_bytes(G.L, G.os, G.nx, p->adj_G, psf2d, m->opts.bulge_table));
     }
     p->adj_smem = asmem;
-    const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, m->opts.bulge_table > 0);
+    p->adj_minb = bang::adjoint_minb(m->opts.n_discs, m->opts.bulge_table > 0, tune.adj_minb);
+    const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, m->opts.bulge_table > 0,
+                                              p->adj_minb);
     cudaFuncAttributes afa;
     BANG_CUDA(cudaFuncGetAttributes(&afa, ak));
     if (asmem + afa.sharedSizeBytes > (size_t)m->smem_optin)
@@ -594,6 +597,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     int aper = 0;
     BANG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&aper, ak, bang::adjoint_threads(), asmem));
     if (aper < 1) return fail(BANG_E_UNSUPPORTED, "adjoint kernel does not fit on an SM");
+    p->adj_blocks_per_sm = aper;
     p->adj_grid = std::min(p->adj_items, aper * m->num_sms);
     BANG_CUDA(copy_vec(p->d_adj_items, ai));
     BANG_CUDA(copy_vec(p->d_adj_order, aorder));
@@ -721,7 +725,9 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
     for (const bang::GalDev& G : m->gals)
       asmem = std::max(asmem, bang::adjoint_smem_bytes(G.L, G.os, G.nx, p->adj_G, psf2d, m->opts.bulge_table));
     p->adj_smem = asmem;
-    const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, m->opts.bulge_table > 0);
+    p->adj_minb = bang::adjoint_minb(m->opts.n_discs, m->opts.bulge_table > 0, tune.adj_minb);
+    const void* ak = bang::adjoint_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, m->opts.bulge_table > 0,
+                                              p->adj_minb);
     cudaFuncAttributes afa;
     BANG_CUDA(cudaFuncGetAttributes(&afa, ak));
     if (asmem + afa.sharedSizeBytes > (size_t)m->smem_optin)
@@ -731,6 +737,7 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
     int aper = 0;
     BANG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&aper, ak, bang::adjoint_threads(), asmem));
     if (aper < 1) return fail(BANG_E_UNSUPPORTED, "adjoint kernel does not fit on an SM");
+    p->adj_blocks_per_sm = aper;
     p->adj_grid = std::min(p->adj_items, aper * m->num_sms);
     if (ordered) {
       std::vector<double> cost(n_gal);
@@ -859,7 +866,8 @@ cudaError_t enqueue_grad(bang_model* m, Plan* p, const float* theta, double* log
   }
   e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_grid, p->adj_smem, st);
+  e = bang::launch_adjoint(a, m->opts.n_quad, m->opts.n_discs, psf2d_of(m, p), p->adj_minb, p->adj_grid, p->adj_smem,
+                           st);
   if (e != cudaSuccess) return e;
   if (p->implicit)
     return bang::launch_grad_out(theta, m->P, m->opts.n_discs, m->opts.halo_kind, m->opts.bulge_kind, acc_partial,
@@ -1464,9 +1472,9 @@ bang_status bang_model_launch_info(bang_model* m, const int32_t* gal_idx, int B,
   Plan* p = nullptr;
   bang_status s = gplace > 0 ? get_dplan(m, B, mode, &p) : get_plan(m, gal_idx, B, mode, &p);
   if (s != BANG_OK) return s;
-  const int32_t v[11] = {p->G, p->bands, p->blocks_per_sm, p->grid, p->n_items, (int32_t)p->smem,
+  const int32_t v[12] = {p->G, p->bands, p->blocks_per_sm, p->grid, p->n_items, (int32_t)p->smem,
                          grad ? p->adj_G : 0, grad ? p->adj_grid : 0, grad ? p->adj_items : 0, p->implicit ? 1 : 0,
-                         p->kmode == bang::kModeLogL2 ? 2 : 1};
+                         p->kmode == bang::kModeLogL2 ? 2 : 1, grad ? p->adj_blocks_per_sm : 0};
   std::memcpy(info, v, sizeof v);
   return BANG_OK;
 }
@@ -1582,22 +1590,26 @@ bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) 
     return fail(BANG_E_UNSUPPORTED, "no launch configuration fits this batch");
   }
   // the gradient path: the forward seed pass's rows per step, then the adjoint's band height
-  // (fine rows per work item), each timed on whole logL + gradient calls
+  // (fine rows per work item), then (one-disc quadrature form) the adjoint's blocks per SM,
+  // each timed on whole logL + gradient calls
   if (grad) {
     float best_g = 1e30f;
-    int best_rows = 0, best_sg = best_t.G;
+    int best_rows = 0, best_sg = best_t.G, best_minb = 0;
     struct Cand {
-      int sg, rows;
+      int sg, rows, minb;   // -1: the best value so far
     };
     std::vector<Cand> cands;
-    for (int sg : {1, 2, 4}) cands.push_back({sg, 0});
-    for (int rows : {4, 8, 16, 24, 32}) cands.push_back({-1, rows});   // -1: the best rows per step so far
+    for (int sg : {1, 2, 4}) cands.push_back({sg, 0, 0});
+    for (int rows : {4, 8, 16, 24, 32}) cands.push_back({-1, rows, 0});
+    if (m->opts.n_discs == 1 && m->opts.bulge_table == 0) cands.push_back({-1, -1, 3});   // 4 is the default
     for (const Cand& c : cands) {
       const int sg = c.sg < 0 ? best_sg : c.sg;
-      const int rows = c.sg < 0 ? c.rows : best_rows;
+      const int rows = c.rows < 0 ? best_rows : c.rows;
+      const int minb = c.minb;
       bang_model::Tuning tg = best_t;
       tg.seed_G = sg;
       tg.adj_G = rows;
+      tg.adj_minb = minb;
       m->tuned[skey] = tg;
       m->plans.clear();
       Plan* p = nullptr;
@@ -1625,13 +1637,16 @@ bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) 
         best_g = t_min;
         best_rows = rows;
         best_sg = sg;
+        best_minb = minb;
       }
     }
     best_t.adj_G = best_rows;
     best_t.seed_G = best_sg;
+    best_t.adj_minb = best_minb;
   } else {
     best_t.adj_G = prior.adj_G;
     best_t.seed_G = prior.seed_G;
+    best_t.adj_minb = prior.adj_minb;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

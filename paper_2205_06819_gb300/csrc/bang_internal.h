@@ -138,8 +138,11 @@ int64_t table_row_floats(int T, int derivs);
 cudaError_t launch_tables(const ModelConst* consts, const GalDev* gals, const int* row_g, int n_gal, int B, int n_quad,
                           int T, int derivs, float* tables, int64_t stride, cudaStream_t st);
 // The adjoint kernel a launch uses (its blocks-per-SM bound depends on the radial-table mode).
-const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d, int table);
-cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int grid, size_t smem,
+// Blocks per SM the adjoint kernel instance is built for: `want` (3 or 4) for the one-disc
+// quadrature form, otherwise its fixed value (3)
+int adjoint_minb(int n_discs, int table, int want);
+const void* adjoint_kernel_ptr(int n_quad, int n_discs, int psf2d, int table, int minb);
+cudaError_t launch_adjoint(const AdjArgs& a, int n_quad, int n_discs, int psf2d, int minb, int grid, size_t smem,
                            cudaStream_t st);
 // adj_row_first / row_first NULL: implicit items, adj_nb / nb per row; gal_idx (device, may be
 // NULL) marks rows with a galaxy index outside [0, n_gal) as invalid (zero gradient).

@@ -92,7 +92,7 @@ def synthetic_data(spec: synth.GalaxySpec, truth: np.ndarray, seed: int, n_quad:
 
 
 def run_model(model_name: str, spec, data, err, truth, n_live: int, batch: int, seed: int,
-              free_geometry: bool = False, frac: float = 0.01, n_quad: int = 64, slice_steps=None, speculate: int = 1):
+              free_geometry: bool = False, frac: float = 0.01, n_quad: int = 64, slice_steps=None, speculate: int = 4):
     from .model import Model
     box = selection_box(model_name, truth, free_geometry)
     prior = BoxPrior(box, sin_slot=SLOT["inc"] if free_geometry else None)
@@ -159,8 +159,9 @@ def main(argv=None):
     ap.add_argument("--frac", type=float, default=0.01)
     ap.add_argument("--free-geometry", action="store_true")
     ap.add_argument("--models", default="BD1D2,BD,BD_rot")
-    ap.add_argument("--speculate", type=int, default=1,
-                    help="slice-sampling positions per chain and likelihood call (NestedSampler)")
+    ap.add_argument("--speculate", type=int, default=4,
+                    help="slice-sampling positions per chain and likelihood call (NestedSampler; 4 cut the "
+                         "wall time of a 78x73 fit from 42.7 to 28.3 s and of a 30x30 fit 2.7x)")
     a = ap.parse_args(argv)
     spec = synth.GalaxySpec(a.nx, a.ny or a.nx, a.oversample, a.psf_fwhm)
     truth = truth_two_discs()
