@@ -255,9 +255,9 @@ bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t 
 bang_status bang_model_tune(bang_model *m, const int32_t *gal_idx, int B);
 
 /* As bang_model_tune, and then the launch parameters of bang_loglike_grad_batch for the same
- * batches (the forward seed pass's fine rows per block step, the adjoint's fine rows per
- * work item and, for the one-disc model without the radial table, the adjoint's blocks per
- * SM, 3 or 4), timed on whole logL + gradient calls.  Synchronous; a gradient call costs a
+ * batches (the forward seed pass's spaxel-row bands and fine rows per block step, the
+ * adjoint's fine rows per work item and, for the one-disc model without the radial table,
+ * the adjoint's blocks per SM, 3 or 4), timed on whole logL + gradient calls.  Synchronous; a gradient call costs a
  * few times a logL call, so this takes correspondingly longer. */
 bang_status bang_model_tune_grad(bang_model *m, const int32_t *gal_idx, int B);
 

@@ -381,6 +381,7 @@ struct bang_model {
     int pair = 0;    // logL batches: 1 = the two-points-per-thread kernel form (kModeLogL2)
     int seed_G = 0;  // fine rows per block step of the gradient call's forward pass (0: G)
     int adj_minb = 0;  // blocks per SM of the one-disc quadrature adjoint, 3 or 4 (0: 4)
+    int seed_bands = 0;  // spaxel-row bands per row of the gradient call's forward pass (0: bands)
   };
   std::map<uint64_t, Tuning> tuned;         // batch-shape key -> launch parameters
   std::mutex mu;
@@ -484,7 +485,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     ny_model = std::max(ny_model, G.ny);
     H_model = std::max(H_model, G.H);
   }
-  const int nb = bands_for(m, B, ny_model, tune.bands);
+  const int nb = bands_for(m, B, ny_model, mode == bang::kModeSeed && tune.seed_bands > 0 ? tune.seed_bands : tune.bands);
   for (int b = 0; b < B; ++b) {
     const int g = gal_idx ? gal_idx[b] : 0;
     if (g < 0 || g >= (int)m->gals.size()) return fail(BANG_E_INVALID_ARG, "gal_idx[%d] = %d out of range", b, g);
@@ -672,7 +673,7 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
   p->B = B;
   p->mode = mode;
   p->implicit = true;
-  p->nb = bands_for(m, B, ny_max, tune.bands);
+  p->nb = bands_for(m, B, ny_max, mode == bang::kModeSeed && tune.seed_bands > 0 ? tune.seed_bands : tune.bands);
   p->bands = p->nb;
   p->n_items = B * p->nb;
   p->out_stride = n4_max;
@@ -1594,19 +1595,25 @@ bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) 
   // each timed on whole logL + gradient calls
   if (grad) {
     float best_g = 1e30f;
-    int best_rows = 0, best_sg = best_t.G, best_minb = 0;
+    int best_rows = 0, best_sg = best_t.G, best_minb = 0, best_sb = 0;
     struct Cand {
-      int sg, rows, minb;   // -1: the best value so far
+      int sb, sg, rows, minb;   // -1: the best value so far
     };
     std::vector<Cand> cands;
-    for (int sg : {1, 2, 4}) cands.push_back({sg, 0, 0});
-    for (int rows : {4, 8, 16, 24, 32}) cands.push_back({-1, rows, 0});
-    if (m->opts.n_discs == 1 && m->opts.bulge_table == 0) cands.push_back({-1, -1, 3});   // 4 is the default
+    // the seed pass's bands (0: the logL launch's), chosen for its own kernel form, whose
+    // blocks per SM can differ from the tuned logL form's
+    for (int sb : {0, 1, 2, 3, 4, 6, 8})
+      if (sb <= ny_max && (sb == 0 || B < 2 * m->num_sms)) cands.push_back({sb, best_t.G, 0, 0});
+    for (int sg : {1, 2, 4}) cands.push_back({-1, sg, 0, 0});
+    for (int rows : {4, 8, 16, 24, 32}) cands.push_back({-1, -1, rows, 0});
+    if (m->opts.n_discs == 1 && m->opts.bulge_table == 0) cands.push_back({-1, -1, -1, 3});   // 4 is the default
     for (const Cand& c : cands) {
+      const int sb = c.sb < 0 ? best_sb : c.sb;
       const int sg = c.sg < 0 ? best_sg : c.sg;
       const int rows = c.rows < 0 ? best_rows : c.rows;
       const int minb = c.minb;
       bang_model::Tuning tg = best_t;
+      tg.seed_bands = sb;
       tg.seed_G = sg;
       tg.adj_G = rows;
       tg.adj_minb = minb;
@@ -1635,15 +1642,18 @@ bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) 
       }
       if (t_min < best_g) {
         best_g = t_min;
+        best_sb = sb;
         best_rows = rows;
         best_sg = sg;
         best_minb = minb;
       }
     }
+    best_t.seed_bands = best_sb;
     best_t.adj_G = best_rows;
     best_t.seed_G = best_sg;
     best_t.adj_minb = best_minb;
   } else {
+    best_t.seed_bands = prior.seed_bands;
     best_t.adj_G = prior.adj_G;
     best_t.seed_G = prior.seed_G;
     best_t.adj_minb = prior.adj_minb;
