@@ -276,6 +276,11 @@ struct DevBuf {
   template <class T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Batch shapes whose plans (and captured graphs) a model keeps, least recently used
+// evicted: a sampler's calls come in a few dozen sizes, and an evicted plan frees device
+// buffers (which synchronises) and is rebuilt and re-captured on its next use.
+constexpr size_t kMaxPlans = 32;
+
 // A batch shape: the work items of (gal_idx, B) and their device copies.
 struct Plan {
   uint64_t key = 0;
@@ -617,7 +622,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
     BANG_CUDA(p->d_tables.reserve(sizeof(float) * (size_t)p->table_stride * B));
   }
   m->plans.push_front(std::move(p));
-  while (m->plans.size() > 8) m->plans.pop_back();
+  while (m->plans.size() > kMaxPlans) m->plans.pop_back();
   *out = m->plans.front().get();
   return BANG_OK;
 }
@@ -757,7 +762,7 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
   }
   p->row_g.assign(1, 0);   // psf2d_of: every galaxy of the model has the same PSF kind here
   m->plans.push_front(std::move(p));
-  while (m->plans.size() > 8) m->plans.pop_back();
+  while (m->plans.size() > kMaxPlans) m->plans.pop_back();
   *out = m->plans.front().get();
   return BANG_OK;
 }

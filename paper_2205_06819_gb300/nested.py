@@ -108,16 +108,41 @@ class BoxPrior:
 
 
 def gpu_loglike(model, gal_idx: int | None = None):
-    """theta [B, P] float64 (host) -> logL [B] float64 through bang_loglike_batch.  theta is
-    passed as a host buffer; the library stages it to the device and copies logL back."""
-    import torch
+    """theta [B, P] float64 (host) -> logL [B] float64 through bang_loglike_batch (see
+    _GpuLogLike)."""
+    return _GpuLogLike(model, gal_idx)
 
-    def f(theta: np.ndarray) -> np.ndarray:
-        th = torch.from_numpy(np.ascontiguousarray(theta, dtype=np.float32))
-        gi = None if gal_idx is None else np.full(th.shape[0], gal_idx, dtype=np.int32)
-        return model.loglike(th, gal_idx=gi).numpy()
 
-    return f
+def _bucket(n: int) -> int:
+    """Call size for n rows: the next of 16, 20, 28, 36, 48, 60, 76, 96, ... (each 5/4 of
+    the one before, rounded up to a multiple of 4), so that a sampler's calls come in a few
+    dozen sizes whose plans and captured graphs the library keeps."""
+    b = 16
+    while b < n:
+        b = (b * 5 // 4 + 3) // 4 * 4
+    return b
+
+
+class _GpuLogLike:
+    """theta [B, P] float64 (host) -> logL [B] float64 through bang_loglike_batch (host
+    buffers: the library stages them).  Every call is padded to a bucket size (_bucket) with
+    copies of its first row, whose values are dropped: the sampler's calls vary in size from
+    one step to the next, and the library keeps a plan and a captured graph per size."""
+
+    def __init__(self, model, gal_idx: int | None = None):
+        import torch
+        self._torch, self.model, self.gal_idx = torch, model, gal_idx
+
+    def __call__(self, theta: np.ndarray) -> np.ndarray:
+        n = len(theta)
+        if n == 0:
+            return np.empty(0)
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        nb = _bucket(n)
+        if nb > n:
+            th = np.concatenate([th, np.repeat(th[:1], nb - n, axis=0)])
+        gi = None if self.gal_idx is None else np.full(nb, self.gal_idx, dtype=np.int32)
+        return self.model.loglike(self._torch.from_numpy(th), gal_idx=gi).numpy()[:n]
 
 
 def _logaddexp(a: float, b: float) -> float:
@@ -184,9 +209,7 @@ class NestedSampler:
     def _above(self, pts: np.ndarray, lstar: float):
         """(inside, logL): points outside the cube are outside the prior support and are not
         evaluated."""
-        inc = np.all((pts >= 0.0) & (pts <= 1.0), axis=1)
-        lp = np.full(len(pts), -np.inf)
-        lp[inc] = self._logl(pts[inc])
+        lp = self._eval(pts)
         return lp > lstar, lp
 
     # -- evidence bookkeeping ----------------------------------------------------------
@@ -245,6 +268,24 @@ class NestedSampler:
 
     def _chains_speculative(self, u: np.ndarray, lu: np.ndarray, lstar: float, chol: np.ndarray):
         """_chains with ``speculate`` positions per chain and call (see the class notes)."""
+        gen = self._chain_gen(u, lu, lstar, chol)
+        try:
+            pts = next(gen)
+            while True:
+                pts = gen.send(self._eval(pts))
+        except StopIteration as stop:
+            return stop.value
+
+    def _eval(self, pts: np.ndarray) -> np.ndarray:
+        """logL of pts, -inf outside the unit cube (the prior's support; not evaluated)."""
+        inc = np.all((pts >= 0.0) & (pts <= 1.0), axis=1)
+        lp = np.full(len(pts), -np.inf)
+        lp[inc] = self._logl(pts[inc])
+        return lp
+
+    def _chain_gen(self, u: np.ndarray, lu: np.ndarray, lstar: float, chol: np.ndarray):
+        """The speculative chains as a generator: yields the points of each likelihood call,
+        receives their logL (-inf outside the cube) and returns (u, lu) at the end."""
         K, D = u.shape
         m = self.speculate
         width = 0.5 * math.sqrt(D + 2.0)
@@ -266,7 +307,7 @@ class NestedSampler:
                 ph = hi[ih, None] + offs[None, :]
                 pts = np.concatenate([(u[il, None, :] + pl[..., None] * d[il, None, :]).reshape(-1, D),
                                       (u[ih, None, :] + ph[..., None] * d[ih, None, :]).reshape(-1, D)])
-                ok, _ = self._above(pts, lstar)
+                ok = (yield pts) > lstar
                 okl = ok[:len(il) * mm].reshape(len(il), mm)
                 okh = ok[len(il) * mm:].reshape(len(ih), mm)
                 fl = np.where(okl.all(axis=1), mm, np.argmin(okl, axis=1))
@@ -296,8 +337,8 @@ class NestedSampler:
                     lo_c = np.where(neg, t, lo_c)
                     hi_c = np.where(neg, hi_c, t)
                 cand = u[idx, None, :] + ts[..., None] * d[idx, None, :]
-                ok, lp = self._above(cand.reshape(-1, D), lstar)
-                ok, lp = ok.reshape(n, mm), lp.reshape(n, mm)
+                lp = (yield cand.reshape(-1, D)).reshape(n, mm)
+                ok = lp > lstar
                 hit = ok.any(axis=1)
                 first = np.argmax(ok, axis=1)
                 acc = idx[hit]
@@ -372,6 +413,7 @@ class NestedSampler:
     # -- checkpoint / resume -----------------------------------------------------------
     _STATE = ("n_live", "batch", "slice_steps", "frac", "max_steps_out", "max_shrink", "speculate", "n_like",
               "it", "plateau", "logz", "h", "logx", "dead_u", "dead_l", "dead_lw", "u", "lv")
+    _DEFAULTS = {"speculate": 1}   # states saved before this option: one position at a time
 
     def state_dict(self) -> dict:
         s = {k: getattr(self, k) for k in self._STATE}
@@ -380,7 +422,7 @@ class NestedSampler:
 
     def load_state_dict(self, s: dict):
         for k in self._STATE:
-            setattr(self, k, s.get(k, 1) if k == "speculate" else s[k])   # older states: one at a time
+            setattr(self, k, s.get(k, self._DEFAULTS[k]) if k in self._DEFAULTS else s[k])
         self.ndim = self.u.shape[1]
         self.rng.bit_generator.state = s["rng"]
 

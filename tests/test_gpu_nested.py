@@ -50,3 +50,27 @@ def test_best_sample_matches_oracle(selection):
     chi2_gpu = -2.0 * (r2.log_l.max() + norm)
     chi2_or = -2.0 * (ds.oracle_loglike(best)[0] + norm)
     assert abs(chi2_gpu - chi2_or) <= 1e-5 * chi2_or, (chi2_gpu, chi2_or)
+
+
+def test_padded_calls_return_the_rows_own_values():
+    """gpu_loglike pads each call to a bucket size with copies of its first row: the values
+    returned are the call's own rows, equal to an unpadded call of the bucket's size."""
+    from paper_2205_06819_gb300.model import Model
+    from paper_2205_06819_gb300.nested import _bucket, gpu_loglike
+    import torch
+    spec = synth.GalaxySpec(16, 14, 3, 2.5)
+    truth = fit.truth_two_discs()
+    ds = Dataset(spec, truth, n_discs=2, seed=21)
+    m = Model([ds.model_galaxy()], n_discs=2)
+    try:
+        box = fit.selection_box("BD1D2", truth)
+        rng = np.random.default_rng(4)
+        th = box[:, 0] + rng.random((37, box.shape[0])) * (box[:, 1] - box[:, 0])
+        got = gpu_loglike(m)(th)
+        nb = _bucket(37)
+        assert got.shape == (37,) and nb == 48
+        full = np.concatenate([th, np.repeat(th[:1], nb - 37, axis=0)]).astype(np.float32)
+        ref = m.loglike(torch.from_numpy(full)).numpy()
+        assert np.array_equal(got, ref[:37]) and np.isfinite(got).all()
+    finally:
+        m.close()

@@ -274,3 +274,15 @@ def test_speculative_limits_and_edges():
     lstar = float(ll(start[:1])[0]) - 1e-12
     u, lu = s._chains(start.copy(), ll(start), lstar, np.eye(D) * 0.5)
     assert np.all(lu > lstar)
+
+
+def test_call_size_buckets():
+    """gpu_loglike pads a call to a bucket size: never smaller than the call, a multiple of
+    4, at most 1/3 (1/4 from 60 on) larger than the bucket below, and few sizes in all (the
+    library keeps 32 plans)."""
+    from paper_2205_06819_gb300.nested import _bucket
+    sizes = sorted({_bucket(n) for n in range(1, 3001)})
+    assert all(_bucket(n) >= n for n in range(1, 5000))
+    assert all(b % 4 == 0 for b in sizes) and sizes[0] == 16
+    assert all(b1 <= b0 * 4 // 3 + 4 for b0, b1 in zip(sizes, sizes[1:]))
+    assert len(sizes) <= 24
