@@ -55,12 +55,12 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 122.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "e43937c975946e35", "bytes_per_launch": 399872}
+NCU_TRAFFIC = {"stamp": "e9f1438ab731d356", "bytes_per_launch": 408832}
 # Pipe activity of the forward kernel from the same kind of capture (ncu --set full on one
 # timed launch of the tuned benchmark batch): SFU (xu) and FMA pipes, issue active, thread
 # instructions per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "e43937c975946e35", "pipe_xu_pct": 39.7, "pipe_fma_pct": 30.6, "pipe_fma_cycles_pct": 45.0,
-             "issue_active_pct": 66.6, "thread_instr_per_point": 490}
+NCU_PIPES = {"stamp": "e9f1438ab731d356", "pipe_xu_pct": 35.8, "pipe_fma_pct": 31.2, "pipe_fma_cycles_pct": 45.0,
+             "issue_active_pct": 67.8, "thread_instr_per_point": 469}
 
 
 def kernel_stamp() -> str:
@@ -196,27 +196,33 @@ def points_per_eval(spec: synth.GalaxySpec) -> int:
 
 # SFU (MUFU) operations per padded fine point, by issue class: "half" are the functions the
 # SFU issues at 16 per clock per SM (lg2, rcp, rsqrt, sqrt), "full" is ex2 (32 per clock).
-#  forward (eval_point): per radial node below the series split K (TAIL_SPLIT) one lg2 and
-#    one ex2 (q^(g-4); q^(2g-7) = (q^(g-4))^2 q by multiplications); the nodes from K on as a
-#    series in 1 / w (one reciprocal and the two powers w^(g-4), w^(2g-7)); per point 13 +
+#  forward (eval_point): per radial node below the far series split KF (TAIL_SPLIT) one lg2
+#    and one ex2 (q^(g-4); q^(2g-7) = (q^(g-4))^2 q by multiplications); the nodes from KF on
+#    as a series in 1 / w (one reciprocal and the two powers w^(g-4), w^(2g-7)); per point 13 +
 #    (n_discs - 1) / 2 half-rate (the bulge's 1/(x+1) and log2 w, sqrt R, rsqrt r2, the bulge
 #    velocity's 1/(x+1) and log2 u, the NFW m(x) (two reciprocals, or a log and a
 #    reciprocal), a disc fit's log for y <= 1 (half the points), sqrt v, 1/B, sqrt sigma^2,
 #    1/Sigma) and 3 + n_discs ex2 (the bulge's two per-point powers, the bulge velocity power,
-#    each disc's exponential).  The few points within ~0.2 bulge scales of the centre that
-#    take every node one by one are counted as the others;
-#  adjoint (point_vjp): per radial node below the split one lg2 and two ex2 (q^(g-4) and
-#    u/w), the upper nodes as three series (one reciprocal, two ex2); per point the forward
+#    each disc's exponential).  The points within ~2-3 bulge scales of the centre (a few
+#    per cent of a grid), which take the mid split's nodes or every node, are counted as the
+#    others: the count is a lower bound of the work;
+#  adjoint (point_vjp): per radial node below the mid split K (MID_SPLIT: the adjoint uses
+#    the mid level only) one lg2 and two ex2 (q^(g-4) and u/w), the upper nodes as three
+#    series (one reciprocal, two ex2); per point the forward
 #    recomputation's operations plus 1/(3-g), 1/R (twice), 1/(1+x) of the halo derivative,
 #    the two divisions of the reverse sweep: 18 + (n_discs - 1) / 2 half-rate and 3 + n_discs
 #    ex2.
-TAIL_SPLIT = {64: 24, 128: 48}   # first radial node of the forward kernel's series (TailRule)
+TAIL_SPLIT = {64: 18, 128: 36}   # first radial node of the far-level series (TailRule::KF)
+FAR_TERMS = 14                    # its terms (kFarTerms): two-lane Horner steps per point
+MID_SPLIT = {64: 24, 128: 48}    # the mid level's split (TailRule::K), the adjoint's series
+MID_TERMS = 8                     # its terms (kTailTerms)
 
 
 def sfu_ops_per_point(n_quad: int, n_discs: int, adjoint: bool = False) -> dict:
-    k = TAIL_SPLIT[n_quad]
     if adjoint:
+        k = MID_SPLIT[n_quad]
         return {"half": k + 19.0 + 0.5 * (n_discs - 1), "full": 2.0 * k + 5.0 + n_discs}
+    k = TAIL_SPLIT[n_quad]
     return {"half": k + 14.0 + 0.5 * (n_discs - 1), "full": k + 5.0 + n_discs}
 
 
@@ -255,14 +261,15 @@ def algorithmic_sfu_ops(wl: synth.Workload, gal_idx=None, rows: int | None = Non
 
 def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = None, grad: bool = False) -> float:
     """FP32 instructions of one batch: per padded fine point 6 per radial node below the
-    series split (the argument of the logarithm, the exponent, and the two weighted sums with
-    the (q^(g-4))^2 q product), 16 lane operations for the series (eight two-lane Horner
-    steps) and ~200 for geometry, velocities, discs and light weighting; per galaxy the
-    PSF stencil (separable: 4 channels x (fine rows x nx + nx x ny) x (os + 2h); two-
+    far series split (the argument of the logarithm, the exponent, and the two weighted sums
+    with the (q^(g-4))^2 q product), 2 FAR_TERMS lane operations for the series (two-lane
+    Horner steps) and ~200 for geometry, velocities, discs and light weighting; per galaxy
+    the PSF stencil (separable: 4 channels x (fine rows x nx + nx x ny) x (os + 2h); two-
     dimensional: 4 x nx x ny x (os + 2h)^2) and ~40 per spaxel for the chi-square.  A
-    gradient step adds the adjoint pass: per point 13 per radial node below the split (the six
-    sums), 48 lane operations for the three series and ~400 for the forward recomputation
-    and the reverse sweep, and the transposed stencil (the forward's count)."""
+    gradient step adds the adjoint pass: per point 13 per radial node below the mid split (the
+    six sums), 6 MID_TERMS lane operations for the three series and ~400 for the forward
+    recomputation and the reverse sweep, and the transposed stencil (the forward's count).
+    Forward points counted at the far level, as in sfu_ops_per_point."""
     def per_row(spec):
         sig = spec.psf_fwhm_arcsec / (2.0 * math.sqrt(2.0 * math.log(2.0)))
         h = int(math.floor(3.0 * sig / (spec.spaxel_arcsec / spec.oversample))) if spec.psf_fwhm_arcsec > 0 else 0
@@ -271,9 +278,10 @@ def algorithmic_fp32_ops(wl: synth.Workload, gal_idx=None, rows: int | None = No
             psf = 4.0 * spec.nx * spec.ny * L * L
         else:
             psf = 4.0 * ((spec.oversample * spec.ny + 2 * h) * spec.nx + spec.nx * spec.ny) * L
-        fwd = points_per_eval(spec) * (6.0 * TAIL_SPLIT[wl.n_quad] + 16.0 + 200.0) + psf + 40.0 * spec.nx * spec.ny
+        fwd = points_per_eval(spec) * (6.0 * TAIL_SPLIT[wl.n_quad] + 2.0 * FAR_TERMS + 200.0) + psf \
+            + 40.0 * spec.nx * spec.ny
         if grad:
-            fwd += points_per_eval(spec) * (13.0 * TAIL_SPLIT[wl.n_quad] + 48.0 + 400.0) + psf
+            fwd += points_per_eval(spec) * (13.0 * MID_SPLIT[wl.n_quad] + 6.0 * MID_TERMS + 400.0) + psf
         return fwd
     per = [per_row(g) for g in wl.galaxies]
     if rows is None:

@@ -175,7 +175,8 @@ __device__ __forceinline__ BulgeDer bulge_projected_vjp(const ModelConst& m, flo
   if (nw) {
     // per-model node factors folded into shared-memory weights, two nodes at a time in
     // packed two-lane FP32 instructions (see bulge_projected_w); with the series
-    // coefficients, the upper nodes of points away from the centre come from the series
+    // coefficients, the upper nodes k >= K of points away from the centre come from the
+    // mid-level series (the forward's far level is not used here: fill_tail_coeffs_adj)
     float2 S2 = make_float2(0.f, 0.f), Su2 = S2, Sl2 = S2, Q2 = S2, Qu2 = S2, Ql2 = S2;
     series = tail && w * kNodeCm1[base + K] >= kTailZ;
     if (series) adj_node_pairs<NQ, 0, K>(m, nw, w, S2, Su2, Sl2, Q2, Qu2, Ql2);
@@ -474,7 +475,7 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int next_item;
   __shared__ float4 nodew[NQ / 2];
-  __shared__ float2 tailc[3 * kTailTerms];
+  __shared__ float2 tailc[kTailSetAdj];
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
   for (int it = blockIdx.x; it < a.n_items;) {

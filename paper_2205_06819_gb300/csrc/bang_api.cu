@@ -915,7 +915,10 @@ bang_status set_error(bang_status s, const char* fmt, ...) {
 }
 
 bang_status check_faults(cudaStream_t st) {
-  if (!kChecked) return BANG_OK;
+  if constexpr (!kChecked) {
+    (void)st;
+    return BANG_OK;
+  } else {
   BANG_CUDA(cudaStreamSynchronize(st));
   struct {
     const char* unit;
@@ -929,6 +932,7 @@ bang_status check_faults(cudaStream_t st) {
                   check_site_name((int)f.site - 1), f.index, f.bound);
   }
   return BANG_OK;
+  }
 }
 
 }  // namespace bang
@@ -941,10 +945,14 @@ int bang_checked_build(void) { return bang::kChecked ? 1 : 0; }
 
 bang_status bang_check_selftest(int device, long long index, long long bound) {
   g_last_error.clear();
-  if (!bang::kChecked) return fail(BANG_E_UNSUPPORTED, "bang_check_selftest: not the checked build");
-  BANG_CUDA(cudaSetDevice(device));
-  BANG_CUDA(bang::launch_check_selftest(index, bound, nullptr));
-  return bang::check_faults(nullptr);
+  if constexpr (!bang::kChecked) {
+    (void)device, (void)index, (void)bound;
+    return fail(BANG_E_UNSUPPORTED, "bang_check_selftest: not the checked build");
+  } else {
+    BANG_CUDA(cudaSetDevice(device));
+    BANG_CUDA(bang::launch_check_selftest(index, bound, nullptr));
+    return bang::check_faults(nullptr);
+  }
 }
 
 bang_status bang_model_create(const bang_galaxy_desc* gal, int n_gal, const bang_model_opts* opts, int device,

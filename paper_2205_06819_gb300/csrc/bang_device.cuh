@@ -39,13 +39,21 @@ template <int NQ> struct NodeBase { static constexpr int value = NQ == 64 ? 0 : 
 static __constant__ float kNodeLm[192];
 static __constant__ float kNodeLcm[192];
 
-// Split of the radial rule for the upper-node series (see fill_tail_coeffs): nodes k >= K
-// of points with w (cosh t_K - 1) >= kTailZ are summed by a kTailTerms-term series.
+// Splits of the radial rule for the upper-node series (see fill_tail_coeffs), two levels:
+// nodes k >= KF of points with w (cosh t_KF - 1) >= kFarZ are summed by a kFarTerms-term
+// series (t_KF ~ 3: the far level, most of the grid); otherwise nodes k >= K of points with
+// w (cosh t_K - 1) >= kTailZ by a kTailTerms-term series (t_K ~ 5: the mid level); the
+// points nearest the bulge centre take every node one by one.
 template <int NQ> struct TailRule;
-template <> struct TailRule<64> { static constexpr int K = 24; };
-template <> struct TailRule<128> { static constexpr int K = 48; };
-constexpr int kTailTerms = 8;     // j = 0 .. 7
-constexpr float kTailZ = 16.0f;   // the series serves points with w (cosh t_K - 1) >= 16
+template <> struct TailRule<64> { static constexpr int K = 24, KF = 18; };
+template <> struct TailRule<128> { static constexpr int K = 48, KF = 36; };
+constexpr int kTailTerms = 8;     // mid level: j = 0 .. 7
+constexpr float kTailZ = 16.0f;   // mid level serves points with w (cosh t_K - 1) >= 16
+constexpr int kFarTerms = 14;     // far level: j = 0 .. 13
+constexpr float kFarZ = 7.0f;     // far level serves points with w (cosh t_KF - 1) >= 7
+// shared coefficient pairs of one set: the far level's kFarTerms, then the mid level's
+// kTailTerms padded with zeros to kFarTerms (one Horner length serves both)
+constexpr int kTailSet = 2 * kFarTerms;
 
 // One galaxy on the device.
 struct GalDev {
@@ -513,13 +521,14 @@ __device__ __forceinline__ void node_pairs(const ModelConst& m, const float4* __
   }
 }
 
-// With `tail` (the series coefficients of fill_tail_coeffs), the upper nodes k >= K of
-// points with w (cosh t_K - 1) >= kTailZ come from the series; without it, or for points
-// nearer the bulge centre, every node is summed.
+// With `tail` (kTailSet coefficient pairs: fill_tail_coeffs for both levels), the upper
+// nodes of points away from the bulge centre come from a series: k >= KF where
+// w (cosh t_KF - 1) >= kFarZ, else k >= K where w (cosh t_K - 1) >= kTailZ; without it, or
+// for points nearer the centre, every node is summed.
 template <int NQ>
 __device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const float4* __restrict__ nw, float R,
                                                   float& Sigma, float& SigS2, const float2* __restrict__ tail = nullptr) {
-  constexpr int base = NodeBase<NQ>::value, K = TailRule<NQ>::K;
+  constexpr int base = NodeBase<NQ>::value, K = TailRule<NQ>::K, KF = TailRule<NQ>::KF;
   const float x = R * m.inv_a;
   const float xp1 = x + 1.0f;
   const float ix1 = rcp_approx(xp1);
@@ -530,25 +539,29 @@ __device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const flo
   const float pS = ex2_approx(m.ngam * lw) * ip4;
   const float pQ = ex2_approx(m.g3 * lw) * ip4;
   float2 S = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
-  if (tail && w * kNodeCm1[base + K] >= kTailZ) {
-    node_pairs<NQ, 0, K>(m, nw, w, S, Q);
-    // upper nodes: w^n P(1 / w) for both sums, P by Horner in packed pairs
+  const bool far = tail && w * kNodeCm1[base + KF] >= kFarZ;
+  const bool mid = !far && tail && w * kNodeCm1[base + K] >= kTailZ;
+  node_pairs<NQ, 0, KF>(m, nw, w, S, Q);
+  if (!far) node_pairs<NQ, KF, K>(m, nw, w, S, Q);
+  if (!far && !mid) node_pairs<NQ, K, NQ>(m, nw, w, S, Q);
+  if (far || mid) {
+    // upper nodes: w^n P(1 / w) for both sums, P by Horner in packed pairs (the mid set's
+    // top coefficients are zero)
+    const float2* c = far ? tail : tail + kFarTerms;
     const float u = xp1 * rcp_approx(x);   // 1 / w
     const float2 u2 = make_float2(u, u);
     float2 P;
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(P.x), "=f"(P.y)
-                 : "r"((unsigned)__cvta_generic_to_shared(tail + kTailTerms - 1)));
+                 : "r"((unsigned)__cvta_generic_to_shared(c + kFarTerms - 1)));
 #pragma unroll
-    for (int j = kTailTerms - 2; j >= 0; --j) {
-      float2 c;
-      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(c.x), "=f"(c.y)
-                   : "r"((unsigned)__cvta_generic_to_shared(tail + j)));
-      P = __ffma2_rn(P, u2, c);
+    for (int j = kFarTerms - 2; j >= 0; --j) {
+      float2 cj;
+      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(cj.x), "=f"(cj.y)
+                   : "r"((unsigned)__cvta_generic_to_shared(c + j)));
+      P = __ffma2_rn(P, u2, cj);
     }
     S.x = fmaf(ex2_approx(m.g4 * lw), P.x, S.x);                    // w^(g-4)
     Q.x = fmaf(ex2_approx(fmaf(2.0f, m.g4, 1.0f) * lw), P.y, Q.x);  // w^(2g-7)
-  } else {
-    node_pairs<NQ, 0, NQ>(m, nw, w, S, Q);
   }
   Sigma = m.cS * x * pS * (S.x + S.y);
   SigS2 = m.cQ * pQ * (Q.x + Q.y);
@@ -562,33 +575,34 @@ __device__ __forceinline__ void bulge_projected_w(const ModelConst& m, const flo
 //   sum_{k>=K} W_k q_k^n = w^n sum_j binom(n, j) A_j w^-j,   A_j = sum_{k>=K} W_k m_k^(n-j),
 // with n = g - 4, W_k = ws_k c_k^-g for Sigma and n = 2g - 7, W_k = wq_k c_k^(3-2g) for
 // Sigma sigma^2 (the same terms as the per-node sums).  A_j depends on the model only.  It is
-// the same discrete sum: where w m_K >= kTailZ (z_k <= 1/16 for every upper node) the eight
-// terms leave a truncation error below 1e-9 of the whole sum for every gamma in [0, 3) (a
-// float64 check over the parameter range is a CPU test); a point closer to the bulge centre
-// (w < kTailZ / m_K: R below ~0.2 bulge scales) takes the upper nodes one by one instead.
-// K splits the rule where the series' range of validity still covers all but the centre
-// (t_K ~ 5.1 for both rules).
+// the same discrete sum up to the series' truncation, which stays below 1e-9 of the whole
+// sum for every gamma in [0, 3) at both levels (a float64 check over the parameter range is
+// a CPU test): the far level splits at t_KF ~ 3 and takes fourteen terms where
+// w m_KF >= kFarZ = 7 (R above ~2.2 bulge scales, most of a grid); the mid level splits at
+// t_K ~ 5.1 and takes eight terms where w m_K >= kTailZ = 16 (R above ~0.2 bulge scales);
+// a point closer to the bulge centre takes the upper nodes one by one.
 
-// The series' per-model coefficients (binom(n, j) A_j for Sigma, for Sigma sigma^2), as
-// pairs, by the 32 lanes of one warp: lane l takes the upper nodes K + l, K + l + 32, ...,
-// and the lanes' partial sums are combined by a fixed shuffle tree (the same bits on every
-// call).  Float32 suffices: the upper nodes carry at most ~2e-4 of either sum (their terms
-// fall like cosh^-3 t), so the coefficients' float32 rounding moves a sum by < 1e-9 (a CPU
-// test emulates it).
-template <int NQ>
-__device__ __noinline__ void fill_tail_coeffs(const ModelConst& m, float2* tail, int lane) {
-  constexpr int base = NodeBase<NQ>::value, K = TailRule<NQ>::K;
+// The series' per-model coefficients (binom(n, j) A_j for Sigma, for Sigma sigma^2) of the
+// split at node K, T terms, as pairs, by the 32 lanes of one warp: lane l takes the upper
+// nodes K + l, K + l + 32, ..., and the lanes' partial sums are combined by a fixed shuffle
+// tree (the same bits on every call).  Float32 suffices: the upper nodes' share of either
+// sum is small (their terms fall like cosh^-3 t: < 2.4e-4 above the mid split, < 1.5e-3
+// above the far one), so the coefficients' float32 rounding and the float32 Horner move a
+// sum by < 1e-9 (a CPU test emulates both).
+template <int NQ, int K, int T>
+__device__ __noinline__ void fill_tail_level(const ModelConst& m, float2* tail, int lane) {
+  constexpr int base = NodeBase<NQ>::value;
   const float nS = m.g4, nQ = fmaf(2.0f, m.g4, 1.0f);   // g - 4 and 2g - 7
-  float aS[kTailTerms], aQ[kTailTerms];
+  float aS[T], aQ[T];
 #pragma unroll
-  for (int j = 0; j < kTailTerms; ++j) aS[j] = aQ[j] = 0.f;
+  for (int j = 0; j < T; ++j) aS[j] = aQ[j] = 0.f;
   for (int k = K + lane; k < NQ; k += 32) {
     const float lm = kNodeLm[base + k], lc = kNodeLc[base + k];
     const float r = 1.0f / kNodeCm1[base + k];
     float eS = kNodeWs[base + k] * exp2f(fmaf(m.ngam, lc, nS * lm));   // W_k m_k^n for Sigma
     float eQ = kNodeWq[base + k] * exp2f(fmaf(m.g3, lc, nQ * lm));     // and for Sigma sigma^2
 #pragma unroll
-    for (int j = 0; j < kTailTerms; ++j) {
+    for (int j = 0; j < T; ++j) {
       aS[j] += eS;
       aQ[j] += eQ;
       eS *= r;
@@ -598,15 +612,15 @@ __device__ __noinline__ void fill_tail_coeffs(const ModelConst& m, float2* tail,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int j = 0; j < kTailTerms; ++j) {
+    for (int j = 0; j < T; ++j) {
       aS[j] += __shfl_xor_sync(0xffffffffu, aS[j], o);
       aQ[j] += __shfl_xor_sync(0xffffffffu, aQ[j], o);
     }
   }
-  if (lane < kTailTerms) {   // lane j: binom(n, j) by the product formula
+  if (lane < T) {   // lane j: binom(n, j) by the product formula
     float bS = 1.0f, bQ = 1.0f, vS = aS[0], vQ = aQ[0];
 #pragma unroll
-    for (int j = 1; j < kTailTerms; ++j) {
+    for (int j = 1; j < T; ++j) {
       bS *= (nS - (j - 1)) / j;
       bQ *= (nQ - (j - 1)) / j;
       if (j == lane) {
@@ -618,6 +632,15 @@ __device__ __noinline__ void fill_tail_coeffs(const ModelConst& m, float2* tail,
   }
 }
 
+// Both levels' coefficients into tail[kTailSet] (one warp): the far set, then the mid set
+// padded with zeros to kFarTerms.
+template <int NQ>
+__device__ __forceinline__ void fill_tail_coeffs(const ModelConst& m, float2* tail, int lane) {
+  fill_tail_level<NQ, TailRule<NQ>::KF, kFarTerms>(m, tail, lane);
+  fill_tail_level<NQ, TailRule<NQ>::K, kTailTerms>(m, tail + kFarTerms, lane);
+  if (lane >= kTailTerms && lane < kFarTerms) tail[kFarTerms + lane] = make_float2(0.f, 0.f);
+}
+
 // The adjoint's series (three packed coefficient sets of kTailTerms pairs, Sigma in .x and
 // Sigma sigma^2 in .y).  Besides each sum sum W q^n, the adjoint carries the sums weighted by
 // u / w = c / q and by log2(u / w) = log2 c - log2 q (see bang_adjoint.cu).  With
@@ -627,11 +650,12 @@ __device__ __noinline__ void fill_tail_coeffs(const ModelConst& m, float2* tail,
 //   sum W q^n log2(c / q) + log2 w sum W q^n
 //                            = w^n sum_j [binom(n, j) A'_j - f_j(n) A_j] w^-j,
 // f_j(n) = (d/dn binom(n, j)) / ln 2 = binom(n, j) sum_{i<j} 1 / (n - i) / ln 2, the
-// coefficients of (1 + z)^n log2(1 + z).  tail[0..T) hold binom(n, j) A_j (the sums),
-// tail[T..2T) binom(n-1, j) (A_j + A_{j+1}), tail[2T..3T) the log-weighted coefficients.
-template <int NQ>
-__device__ __noinline__ void fill_tail_coeffs_adj(const ModelConst& m, float2* tail, int lane) {
-  constexpr int base = NodeBase<NQ>::value, K = TailRule<NQ>::K, T = kTailTerms;
+// coefficients of (1 + z)^n log2(1 + z).  For the split at node K with T terms, set c of
+// stride ST (T <= ST, the entries from T on zero): tail[0..ST) hold binom(n, j) A_j (the
+// sums), tail[ST..2ST) binom(n-1, j) (A_j + A_{j+1}), tail[2ST..3ST) the log-weighted ones.
+template <int NQ, int K, int T, int ST>
+__device__ __noinline__ void fill_tail_level_adj(const ModelConst& m, float2* tail, int lane) {
+  constexpr int base = NodeBase<NQ>::value;
   constexpr float kInvLn2 = 1.44269504088896341f;
   for (int fam = 0; fam < 2; ++fam) {   // 0: Sigma (n = g - 4), 1: Sigma sigma^2 (n = 2g - 7)
     const float n = fam == 0 ? m.g4 : fmaf(2.0f, m.g4, 1.0f);
@@ -674,10 +698,24 @@ __device__ __noinline__ void fill_tail_coeffs_adj(const ModelConst& m, float2* t
         }
       }
       reinterpret_cast<float*>(tail + lane)[fam] = v0;
-      reinterpret_cast<float*>(tail + T + lane)[fam] = v1;
-      reinterpret_cast<float*>(tail + 2 * T + lane)[fam] = v2;
+      reinterpret_cast<float*>(tail + ST + lane)[fam] = v1;
+      reinterpret_cast<float*>(tail + 2 * ST + lane)[fam] = v2;
+    } else if (lane < ST) {
+      reinterpret_cast<float*>(tail + lane)[fam] = 0.f;
+      reinterpret_cast<float*>(tail + ST + lane)[fam] = 0.f;
+      reinterpret_cast<float*>(tail + 2 * ST + lane)[fam] = 0.f;
     }
   }
+}
+
+// The adjoint's coefficients into tail[kTailSetAdj] (one warp): the mid level only, three
+// sets of kTailTerms pairs.  (With the far level as well, the adjoint's three longer Horner
+// chains and extra node-loop segment raised its spills at 64 and 80 registers, and logL +
+// gradient ran 5.5% slower: 88.2k against 93.3k evaluations per second.)
+constexpr int kTailSetAdj = 3 * kTailTerms;
+template <int NQ>
+__device__ __forceinline__ void fill_tail_coeffs_adj(const ModelConst& m, float2* tail, int lane) {
+  fill_tail_level_adj<NQ, TailRule<NQ>::K, kTailTerms, kTailTerms>(m, tail, lane);
 }
 
 // Per-model node weights for bulge_projected_w, paired as (ws_k, ws_k+1, wq_k, wq_k+1)

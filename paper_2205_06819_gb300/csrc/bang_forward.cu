@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
   __shared__ int next_item;
   __shared__ int chunk_ctr[2];
   __shared__ float4 nodew[NQ / 2];
-  __shared__ float2 tailc[kTailTerms];
+  __shared__ float2 tailc[kTailSet];
   const int lane = threadIdx.x & 31;
   // first item by block index, then either the next one from the shared counter (dynamic
   // scheduling, longest items first) or a fixed stride
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
       const int npts = min(Gc, y_end - y0) * W;
       float4* st = stage + (size_t)(c & 1) * Gc * W;
       if (!BANG_IN(npts, Gc * W + 1, kSiteFwdStage)) return;
-      if (MODE == kModeLogL2) {   // two points per thread: their independent chains interleave
+      if constexpr (MODE == kModeLogL2) {   // two points per thread: their independent chains interleave
         for (;;) {
           int base = 0;
           if (lane == 0) base = atomicAdd(&chunk_ctr[c & 1], 64);
@@ -282,20 +282,20 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
             if (base + 32 + lane < npts) st[pB] = oB;
           }
         }
-        return;
-      }
-      for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&chunk_ctr[c & 1], 32);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= npts) break;
-        const int p = base + lane;
-        if (p < npts) {
-          const int gr = __float2int_rz(((float)p + 0.5f) * inv_W);   // p + 1/2 is never a multiple of W
-          const int qx = p - gr * W;
-          const float X = fmaf((float)qx, pk, mc.X0);
-          const float Y = fmaf((float)(y0 + gr), pk, mc.Y0);
-          st[p] = eval_point<NQ, ND>(mc, X, Y, tab, a.table_T, nodew, tailc);
+      } else {
+        for (;;) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&chunk_ctr[c & 1], 32);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (base >= npts) break;
+          const int p = base + lane;
+          if (p < npts) {
+            const int gr = __float2int_rz(((float)p + 0.5f) * inv_W);   // p + 1/2 is never a multiple of W
+            const int qx = p - gr * W;
+            const float X = fmaf((float)qx, pk, mc.X0);
+            const float Y = fmaf((float)(y0 + gr), pk, mc.Y0);
+            st[p] = eval_point<NQ, ND>(mc, X, Y, tab, a.table_T, nodew, tailc);
+          }
         }
       }
     };

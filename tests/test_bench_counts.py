@@ -19,17 +19,20 @@ def test_padded_points_and_sfu_count_of_the_batched_workload():
     # forward: per node below the series split one lg2 and one ex2; the series one reciprocal
     # and two ex2; per point 13 half-rate and 4 ex2 (one disc)
     per_eval = bench.algorithmic_sfu_ops(wl) / wl.batch
-    assert per_eval == 430 * 430 * (24 + 14 + 24 + 6)
+    assert per_eval == 430 * 430 * (18 + 14 + 18 + 6)
     ops, cyc = bench.sfu_work(wl)
-    assert cyc / wl.batch == pytest.approx(430 * 430 * ((24 + 14) / 16 + (24 + 6) / 32), rel=1e-12)
+    assert cyc / wl.batch == pytest.approx(430 * 430 * ((18 + 14) / 16 + (18 + 6) / 32), rel=1e-12)
 
 
 def test_series_split_matches_the_kernel_header():
     import re
     hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2205_06819_gb300",
                             "csrc", "bang_device.cuh")).read()
-    split = {int(n): int(k) for n, k in re.findall(r"struct TailRule<(\d+)> \{ static constexpr int K = (\d+);", hdr)}
-    assert split == bench.TAIL_SPLIT
+    rules = re.findall(r"struct TailRule<(\d+)> \{ static constexpr int K = (\d+), KF = (\d+);", hdr)
+    assert {int(n): int(kf) for n, _, kf in rules} == bench.TAIL_SPLIT
+    assert {int(n): int(k) for n, k, _ in rules} == bench.MID_SPLIT
+    assert int(re.search(r"constexpr int kTailTerms = (\d+);", hdr).group(1)) == bench.MID_TERMS
+    assert int(re.search(r"constexpr int kFarTerms = (\d+);", hdr).group(1)) == bench.FAR_TERMS
 
 
 def test_sfu_count_of_the_gradient_step():
@@ -39,25 +42,25 @@ def test_sfu_count_of_the_gradient_step():
     each pass."""
     wl = synth.workload("adjoint")
     ops, cyc = bench.sfu_work(wl, grad=True)
-    fwd = 430 * 430 * ((24 + 14) / 16 + (24 + 6) / 32)
+    fwd = 430 * 430 * ((18 + 14) / 16 + (18 + 6) / 32)
     adj = 430 * 430 * ((24 + 19) / 16 + (48 + 6) / 32)
     assert cyc / wl.batch == pytest.approx(fwd + adj, rel=1e-12)
-    assert ops / wl.batch == 430 * 430 * (24 + 14 + 24 + 6 + 24 + 19 + 48 + 6)
+    assert ops / wl.batch == 430 * 430 * (18 + 14 + 18 + 6 + 24 + 19 + 48 + 6)
     assert bench.sfu_ops_per_point(128, 2, True) == {"half": 48 + 19.5, "full": 96 + 7}
     assert bench.sfu_ops_per_point_node_by_node(128, 2, True) == {"half": 128 + 18.5, "full": 256 + 5}
-    assert bench.sfu_ops_per_point(128, 2, False) == {"half": 48 + 14.5, "full": 48 + 7}
+    assert bench.sfu_ops_per_point(128, 2, False) == {"half": 36 + 14.5, "full": 36 + 7}
 
 
 def test_fp32_count_of_the_batched_and_largest_workloads():
     wl = synth.workload("batched")
     L = 5 + 2 * 15
     psf = 4.0 * ((5 * 80 + 30) * 80 + 80 * 80) * L
-    expect = 430 * 430 * (6 * 24 + 16 + 200) + psf + 40 * 6400
+    expect = 430 * 430 * (6 * 18 + 28 + 200) + psf + 40 * 6400
     assert bench.algorithmic_fp32_ops(wl) / wl.batch == pytest.approx(expect, rel=1e-12)
     big = synth.workload("largest")                                   # Moffat: two-dimensional taps
     h = int(math.floor(3.0 * 2.5 / 2.35482 / (1.0 / 7)))
     L = 7 + 2 * h
-    expect = (7 * 128 + 2 * h) ** 2 * (6 * 48 + 16 + 200) + 4.0 * 128 * 128 * L * L + 40 * 128 * 128
+    expect = (7 * 128 + 2 * h) ** 2 * (6 * 36 + 28 + 200) + 4.0 * 128 * 128 * L * L + 40 * 128 * 128
     assert bench.algorithmic_fp32_ops(big) / big.batch == pytest.approx(expect, rel=1e-12)
 
 
@@ -65,21 +68,21 @@ def test_row_subsets_of_an_uneven_batch():
     wl = synth.workload("uneven")
     gi = [0] * 3 + [5] * 2
     per = [bench.points_per_eval(g) for g in wl.galaxies]
-    assert bench.algorithmic_sfu_ops(wl, gi, 5) == (3 * per[0] + 2 * per[5]) * (24 + 14 + 24 + 6)
+    assert bench.algorithmic_sfu_ops(wl, gi, 5) == (3 * per[0] + 2 * per[5]) * (18 + 14 + 18 + 6)
 
 
 def test_roofline_block_arithmetic():
     """frac = the SFU time of the step's operations at the per-SM issue rates over the
     measured time; peak = operations over that time."""
     wl = synth.workload("batched")
-    t_sfu = 1024 * 430 * 430 * ((24 + 14) / 16 + (24 + 6) / 32) / (152 * 2070e6)
+    t_sfu = 1024 * 430 * 430 * ((18 + 14) / 16 + (18 + 6) / 32) / (152 * 2070e6)
     r = bench.roofline_block(wl, 2.0 * t_sfu, mhz=2070.0, sms=152)
     assert r["sfu_frac"] == pytest.approx(0.5, rel=1e-12)
     assert r["frac"] == pytest.approx(max(r["sfu_frac"], r["fp32"]["frac"]), rel=1e-12)
-    ops = 1024 * 430 * 430 * 68
+    ops = 1024 * 430 * 430 * 56
     assert r["peak"] == pytest.approx(ops / t_sfu / 1e9, rel=1e-12)
     assert r["achieved"] == pytest.approx(r["peak"] / 2, rel=1e-12)
-    assert r["sfu_sm_cycles_per_point"] == pytest.approx((24 + 14) / 16 + (24 + 6) / 32, rel=1e-12)
+    assert r["sfu_sm_cycles_per_point"] == pytest.approx((18 + 14) / 16 + (18 + 6) / 32, rel=1e-12)
     nbn = 1024 * 430 * 430 * ((64 + 13) / 16 + (64 + 4) / 32) / (152 * 2070e6)
     assert r["node_by_node_sfu_frac"] == pytest.approx(nbn / (2.0 * t_sfu), rel=1e-12)
     g = bench.roofline_block(synth.workload("adjoint"), 1e-3, grad=True, mhz=2070.0, sms=152)

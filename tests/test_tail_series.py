@@ -4,12 +4,14 @@ node-by-node sum it replaces.
 
 For nodes k >= K of the rule r = R cosh t (t in [0, 16], n Gauss-Legendre nodes), a point's
 q_k = 1 + w m_k (m_k = cosh t_k - 1) is expanded as (w m_k)^p (1 + 1/(w m_k))^p, so that
-sum_{k>=K} W_k q_k^p = w^p sum_j binom(p, j) A_j w^-j with per-model A_j = sum W_k m_k^(p-j);
-the kernel keeps kTailTerms terms and uses the series where w m_K >= kTailZ.  The header's
-constants are read from the source; the claim pinned here is the one its comment makes:
-truncation below 1e-9 of the whole sum, for both projected integrals (Sigma: p = g - 4,
-W = w_k cosh t_k cosh^-g t_k; Sigma sigma^2: p = 2g - 7, W = w_k tanh^2 t_k cosh^(3-2g) t_k)
-over gamma in [0, 3) and every w the series serves.
+sum_{k>=K} W_k q_k^p = w^p sum_j binom(p, j) A_j w^-j with per-model A_j = sum W_k m_k^(p-j).
+The kernels use two levels: the far level splits at KF (t ~ 3) with kFarTerms terms where
+w m_KF >= kFarZ, the mid level at K (t ~ 5) with kTailTerms terms where w m_K >= kTailZ.
+The header's constants are read from the source; the claim pinned here is the one its
+comment makes: truncation below 1e-9 of the whole sum at both levels, for both projected
+integrals (Sigma: p = g - 4, W = w_k cosh t_k cosh^-g t_k; Sigma sigma^2: p = 2g - 7,
+W = w_k tanh^2 t_k cosh^(3-2g) t_k) over gamma in [0, 3) and every w each level serves,
+with float32 coefficients and Horner as the kernels form them.
 """
 import math
 import os
@@ -23,11 +25,28 @@ HEADER = os.path.join(os.path.dirname(HERE), "paper_2205_06819_gb300", "csrc", "
 
 
 def header_constants():
+    """(K, terms, z) of the mid level, as the earlier single-level tests read them."""
     text = open(HEADER).read()
-    K = {int(n): int(k) for n, k in re.findall(r"struct TailRule<(\d+)> \{ static constexpr int K = (\d+);", text)}
+    K = {int(n): int(k) for n, k, _ in
+         re.findall(r"struct TailRule<(\d+)> \{ static constexpr int K = (\d+), KF = (\d+);", text)}
     terms = int(re.search(r"constexpr int kTailTerms = (\d+);", text).group(1))
     z = float(re.search(r"constexpr float kTailZ = ([0-9.]+)f;", text).group(1))
     return K, terms, z
+
+
+def levels():
+    """[(name, n, K, terms, z)] of both series levels and both rules, read from the header."""
+    text = open(HEADER).read()
+    rules = re.findall(r"struct TailRule<(\d+)> \{ static constexpr int K = (\d+), KF = (\d+);", text)
+    tm = int(re.search(r"constexpr int kTailTerms = (\d+);", text).group(1))
+    zm = float(re.search(r"constexpr float kTailZ = ([0-9.]+)f;", text).group(1))
+    tf = int(re.search(r"constexpr int kFarTerms = (\d+);", text).group(1))
+    zf = float(re.search(r"constexpr float kFarZ = ([0-9.]+)f;", text).group(1))
+    out = []
+    for n, k, kf in rules:
+        out.append(("mid", int(n), int(k), tm, zm))
+        out.append(("far", int(n), int(kf), tf, zf))
+    return out
 
 
 def rule(n):
@@ -46,15 +65,18 @@ def series(W, m, p, K, terms, w):
     return w ** p * s
 
 
-@pytest.mark.parametrize("n", [64, 128])
-def test_series_truncation_below_1e9_of_the_sum(n):
-    K, terms, z = header_constants()
-    assert set(K) == {64, 128}
+LEVELS = levels()
+LEVEL_IDS = [f"{name}{n}" for name, n, *_ in LEVELS]
+
+
+@pytest.mark.parametrize("name,n,k,terms,z", LEVELS, ids=LEVEL_IDS)
+def test_series_truncation_below_1e9_of_the_sum(name, n, k, terms, z):
     t, wk, c, m, th2 = rule(n)
-    k = K[n]
-    assert k % 2 == 0 and 4.5 < t[k] < 5.5           # the split sits near t = 5
+    assert k % 2 == 0
+    lo, hi, wcap = (4.5, 5.5, 0.25) if name == "mid" else (2.8, 3.4, 0.8)
+    assert lo < t[k] < hi                              # the mid split near t = 5, the far one near 3
     wmin = z / m[k]
-    assert wmin < 0.25                                # the series serves all but the centre
+    assert wmin < wcap                                 # mid: all but the centre; far: R above ~2-3 a
     worst = 0.0
     for g in np.linspace(0.0, 2.999, 31):
         WS = wk * c * c ** -g
@@ -69,11 +91,21 @@ def test_series_truncation_below_1e9_of_the_sum(n):
     assert worst < 1e-9, worst
 
 
-def test_a_shorter_series_or_a_looser_threshold_would_fail():
-    """The pin has teeth: two terms, or the series used down to w m_K = 2, miss 1e-9."""
-    K, terms, z = header_constants()
-    t, wk, c, m, th2 = rule(64)
-    k = K[64]
+def test_the_levels_nest():
+    """Every point the mid level leaves to the far one is inside the far level's range:
+    the far threshold in w lies above the mid one, and the far split below the mid split."""
+    by = {(name, n): (k, z) for name, n, k, _, z in LEVELS}
+    for n in (64, 128):
+        (kf, zf), (km, zm) = by[("far", n)], by[("mid", n)]
+        m = rule(n)[3]
+        assert kf < km and zf / m[kf] > zm / m[km]
+
+
+@pytest.mark.parametrize("name,n,k,terms,z", [lv for lv in LEVELS if lv[1] == 64], ids=["mid64", "far64"])
+def test_a_shorter_series_or_a_looser_threshold_would_fail(name, n, k, terms, z):
+    """The pin has teeth: a quarter of the terms, or the series used down to w m_K = z / 8,
+    miss 1e-9 (at gamma = 2.5)."""
+    t, wk, c, m, th2 = rule(n)
     g = 2.5
     WQ = wk * th2 * c ** (3 - 2 * g)
 
@@ -83,8 +115,8 @@ def test_a_shorter_series_or_a_looser_threshold_would_fail():
         head = np.sum((WQ * q ** (2 * g - 7))[:k])
         return abs(head + series(WQ, m, 2 * g - 7, k, nterms, w) - full) / full
 
-    assert err(2, z / m[k]) > 1e-9
-    assert err(terms, 2.0 / m[k]) > 1e-9
+    assert err(terms // 4, z / m[k]) > 1e-9
+    assert err(terms, z / 8 / m[k]) > 1e-9
 
 
 def test_binomial_coefficients_by_the_product_formula():
@@ -99,15 +131,14 @@ def test_binomial_coefficients_by_the_product_formula():
             assert b == pytest.approx(ref, rel=1e-12)
 
 
-@pytest.mark.parametrize("n", [64, 128])
-def test_float32_coefficients_as_the_kernel_forms_them(n):
+@pytest.mark.parametrize("name,n,k,terms,z", LEVELS, ids=LEVEL_IDS)
+def test_float32_coefficients_as_the_kernel_forms_them(name, n, k, terms, z):
     """The kernels form A_j in float32 (node terms W_k 2^(pc log2 c_k + p log2 m_k), powers
-    of 1/m_k by multiplication): the upper nodes carry at most ~2e-4 of either sum, so the
-    float32 coefficients still leave the sums within 1e-9."""
-    K, terms, z = header_constants()
+    of 1/m_k by multiplication) and evaluate the polynomial by float32 Horner: the upper
+    nodes carry at most ~2e-4 (mid level) or ~1.5e-3 (far level) of either sum, so the sums
+    stay within 1e-9."""
     f32 = np.float32
     t, wk, c, m64, th2 = rule(n)
-    k = K[n]
     m = m64.astype(f32).astype(np.float64)                 # the kernels' float32 m_k
     WSf, WQf = f32(wk * c), f32(wk * th2)
     lcf, lmf = f32(np.log2(m + 1.0)), f32(np.log2(m))
@@ -133,26 +164,27 @@ def test_float32_coefficients_as_the_kernel_forms_them(n):
                 terms_full = W * q ** p
                 full = terms_full.sum()
                 share = max(share, terms_full[k:].sum() / full)
-                b, s = 1.0, 0.0
+                b, cf = 1.0, []
                 for j in range(terms):
                     if j:
                         b *= (p - (j - 1)) / j
-                    s += b * A[j] * w ** (-j)
-                worst = max(worst, abs(terms_full[:k].sum() + w ** p * s - full) / full)
-    assert share < 1e-3, share
+                    cf.append(f32(f32(b) * f32(A[j])))
+                u, P = f32(1.0 / w), cf[-1]
+                for j in range(terms - 2, -1, -1):
+                    P = f32(f32(P * u) + cf[j])
+                worst = max(worst, abs(terms_full[:k].sum() + w ** p * float(P) - full) / full)
+    assert share < (1e-3 if name == "mid" else 2e-3), share
     assert worst < 1e-9, worst
 
 
-@pytest.mark.parametrize("n", [64, 128])
-def test_adjoint_sums_of_the_series(n):
+@pytest.mark.parametrize("name,n,k,terms,z", [lv for lv in LEVELS if lv[0] == "mid"], ids=["mid64", "mid128"])
+def test_adjoint_sums_of_the_series(name, n, k, terms, z):
     """The adjoint's six sums over the upper nodes (bang_device.cuh, fill_tail_coeffs_adj):
     sum W q^p, w sum W q^p c / q (series in p - 1 with A_j + A_{j+1}) and
     sum W q^p log2(c / q) + log2 w sum W q^p (with A'_j and the derivative of the binomial
     coefficients), for both integrals, against the node-by-node sums: within 1e-9 of the
     sum (of Sigma, resp. Sigma sigma^2, for the log-weighted ones, which can cross zero)."""
-    K, terms, z = header_constants()
     t, wk, c, m, th2 = rule(n)
-    k = K[n]
     lcm = np.log2(c / m)
 
     def binom(p, j):
