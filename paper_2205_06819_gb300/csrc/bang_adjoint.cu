@@ -514,6 +514,7 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
       continue;
     }
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx, ny = gs.ny, n = nx * ny;
+    const float inv_os = 1.0f / (float)os, inv_nx = 1.0f / (float)nx;
     const int64_t soff = a.out_off ? a.out_off[w.b] : (int64_t)w.b * a.out_stride;
     const float* seed = a.seed + soff;
     // separable taps stored twice, (t, t): a 64-bit load gives the pair the packed
@@ -563,17 +564,18 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
       __syncthreads();   // taps loaded / previous chunk's lam and V no longer read
       if (!BANG_IN(nj, nj_max + 1, kSiteAdjLam)) break;   // uniform: every thread leaves the item's loop
       for (int t = tid; t < nj * nx; t += kAdjThreads) {
-        const int s = (jlo + t / nx) * nx + (t % nx);
+        const int tj = floor_div(t, inv_nx);
+        const int s = (jlo + tj) * nx + (t - tj * nx);
         lam[t] = make_float4(__ldg(seed + s), __ldg(seed + n + s), __ldg(seed + 2 * n + s), __ldg(seed + 3 * n + s));
       }
       __syncthreads();
       if (PSF == 0) {
         // vertical transposed pass: V[g][i] = sum_j T[y - j os] lambda(i, j)
         for (int t = tid; t < G * nx; t += kAdjThreads) {
-          const int gr = t / nx, i = t - gr * nx;
+          const int gr = floor_div(t, inv_nx), i = t - gr * nx;
           const int y = y0 + gr;
-          int j0 = y - L + 1 <= 0 ? 0 : (y - L + os) / os;
-          const int j1 = min(ny - 1, y / os);
+          int j0 = y - L + 1 <= 0 ? 0 : floor_div(y - L + os, inv_os);
+          const int j1 = min(ny - 1, floor_div(y, inv_os));
           float2 vxy = make_float2(0.f, 0.f), vzw = vxy;
           for (int j = j0; j <= j1; ++j) {
             if (!BANG_IN(y - j * os, L, kSiteAdjTap) || !BANG_IN(j - jlo, nj, kSiteAdjLam)) continue;
@@ -597,8 +599,8 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
         const int gr = __float2int_rz(((float)p + 0.5f) * inv_W);   // p + 1/2 is never a multiple of W
         const int qx = p - gr * W;
         const int y = y0 + gr;
-        int i0 = qx - L + 1 <= 0 ? 0 : (qx - L + os) / os;
-        const int i1 = min(nx - 1, qx / os);
+        int i0 = qx - L + 1 <= 0 ? 0 : floor_div(qx - L + os, inv_os);
+        const int i1 = min(nx - 1, floor_div(qx, inv_os));
         float2 sxy = make_float2(0.f, 0.f), szw = sxy;
         if (PSF == 0) {
           for (int i = i0; i <= i1; ++i) {
@@ -609,8 +611,8 @@ __global__ void __launch_bounds__(kAdjThreads, MINB) adjoint_kernel(AdjArgs a) {
             szw = __ffma2_rn(th_, make_float2(v.z, v.w), szw);
           }
         } else {
-          int j0 = y - L + 1 <= 0 ? 0 : (y - L + os) / os;
-          const int j1 = min(ny - 1, y / os);
+          int j0 = y - L + 1 <= 0 ? 0 : floor_div(y - L + os, inv_os);
+          const int j1 = min(ny - 1, floor_div(y, inv_os));
           for (int j = j0; j <= j1; ++j) {
             if (!BANG_IN(y - j * os, L, kSiteAdjTap) || !BANG_IN(j - jlo, nj, kSiteAdjLam)) continue;
             const float* wrow = taps2d + (y - j * os) * L;

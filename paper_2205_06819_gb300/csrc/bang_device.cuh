@@ -99,6 +99,12 @@ struct ModelConst {
   int valid;
 };
 
+// floor(n / d) for 0 <= n < 2^21 from inv_d = 1.0f / d (d >= 1): n + 1/2 is never a
+// multiple of d and (n + 1/2) / d lies at least 1 / (2d) from an integer, more than the
+// float32 rounding of the reciprocal and the product can move it; one multiply and one
+// conversion instead of the integer division sequence (the stencils' index ranges).
+__device__ __forceinline__ int floor_div(int n, float inv_d) { return __float2int_rz(((float)n + 0.5f) * inv_d); }
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
     if (a.consts_out && tid == 0 && w.j0 == 0) a.consts_out[w.b] = mc;
     const int L = gs.L, os = gs.os, W = gs.W, nx = gs.nx;
     const int NA = (L + os - 1) / os;                       // open spaxel rows
+    const float inv_os = 1.0f / (float)os, inv_nx = 1.0f / (float)nx, inv_NA = 1.0f / (float)NA;
     // separable taps stored twice, (t, t): a 64-bit load gives the pair the packed
     // two-lane FMAs need; of the L x L two-dimensional taps only the Lq x Lq quadrant
     // (Lq = (L + 1) / 2): every two-dimensional window here is even in dx and dy about the
@@ -321,22 +322,26 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
               hxy = __ffma2_rn(tw, make_float2(v.x, v.y), hxy);
               hzw = __ffma2_rn(tw, make_float2(v.z, v.w), hzw);
             }
-            int jlo = y - L + 1 <= 0 ? 0 : (y - L + os) / os;  // ceil((y - L + 1) / os)
+            int jlo = y - L + 1 <= 0 ? 0 : floor_div(y - L + os, inv_os);  // ceil((y - L + 1) / os)
             jlo = max(jlo, w.j0);
-            const int jhi = min(y / os, w.j1 - 1);
+            const int jhi = min(floor_div(y, inv_os), w.j1 - 1);
+            int ring = jlo - NA * floor_div(jlo, inv_NA);         // jlo % NA, then kept in step
             for (int j = jlo; j <= jhi; ++j) {
-              if (!BANG_IN(y - j * os, L, kSiteFwdTap)) continue;
-              const float2 tv = taps[y - j * os];
-              float4& A = acc[(j % NA) * nx + i];
-              const float2 axy = __ffma2_rn(tv, hxy, make_float2(A.x, A.y));
-              const float2 azw = __ffma2_rn(tv, hzw, make_float2(A.z, A.w));
-              A = make_float4(axy.x, axy.y, azw.x, azw.y);
+              if (BANG_IN(y - j * os, L, kSiteFwdTap)) {
+                const float2 tv = taps[y - j * os];
+                float4& A = acc[ring * nx + i];
+                const float2 axy = __ffma2_rn(tv, hxy, make_float2(A.x, A.y));
+                const float2 azw = __ffma2_rn(tv, hzw, make_float2(A.z, A.w));
+                A = make_float4(axy.x, axy.y, azw.x, azw.y);
+              }
+              ring = ring + 1 == NA ? 0 : ring + 1;
             }
             const int yl = y - L + 1;                             // spaxel row ending here
-            if (yl >= 0 && yl % os == 0) {
-              const int j = yl / os;
+            const int jl = yl >= 0 ? floor_div(yl, inv_os) : -1;
+            if (yl >= 0 && jl * os == yl) {
+              const int j = jl;
               if (j >= w.j0 && j < w.j1) {
-                float4& A = acc[(j % NA) * nx + i];
+                float4& A = acc[(j - NA * floor_div(j, inv_NA)) * nx + i];
                 float lam_v;
                 chi_thread += (double)finish_spaxel<MODE>(gs, mc, A, i, j, out, lam_v);
                 if (MODE == kModeSeed) vsys_thread += (double)lam_v;
@@ -353,9 +358,11 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
         const int jhi = min(ylast / os, w.j1 - 1);
         const int nj = jhi - jlo + 1;
         for (int t = tid; t < nj * nx; t += kThreads) {
-          const int j = jlo + t / nx;
-          const int i = t - (t / nx) * nx;
-          float4 A = acc[(j % NA) * nx + i];
+          const int tj = floor_div(t, inv_nx);
+          const int j = jlo + tj;
+          const int i = t - tj * nx;
+          const int rj = j - NA * floor_div(j, inv_NA);           // j % NA
+          float4 A = acc[rj * nx + i];
           const int ga = max(0, j * os - y0);
           const int gb = min(G - 1, j * os + L - 1 - y0);
           for (int gr = ga; gr <= gb; ++gr) {
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kModeLogL2 ? 3 : 4) forward_
             if (MODE == kModeSeed) vsys_thread += (double)lam_v;
             A = make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          acc[(j % NA) * nx + i] = A;
+          acc[rj * nx + i] = A;
         }
       }
       // meanwhile (and after its share of the stencil) every warp evaluates chunk c + 1
