@@ -350,10 +350,12 @@ __device__ __forceinline__ void disc_F_d(float y, float u, float& F, float& dF) 
 }
 
 // m(x) = ln(1 + x) - x / (1 + x) of the NFW enclosed mass.  For x <= 1, with z = x / (2 + x):
-// m = 2 z^2 / (1 + z) + 2 z^3 (1/3 + z^2/5 + z^4/7 + ...), free of the cancellation at small x.
+// m = 2 z^2 / (1 + z) + 2 z^3 (1/3 + z^2/5 + z^4/7 + ...), free of the cancellation at small x;
+// z and 2 z^2 / (1 + z) = x^2 / ((1 + x)(2 + x)) share one reciprocal.
 __device__ __forceinline__ float nfw_m(float x) {
   if (x <= 1.0f) {
-    const float z = __fdividef(x, 2.0f + x);
+    const float x1 = 1.0f + x, rr = rcp_approx(x1 * (2.0f + x));   // 1 / ((1 + x)(2 + x))
+    const float z = x * x1 * rr;                                     // x / (2 + x)
     const float z2 = z * z;
     float s = 1.0f / 19.0f;
     s = fmaf(s, z2, 1.0f / 17.0f);
@@ -364,7 +366,7 @@ __device__ __forceinline__ float nfw_m(float x) {
     s = fmaf(s, z2, 1.0f / 7.0f);
     s = fmaf(s, z2, 1.0f / 5.0f);
     s = fmaf(s, z2, 1.0f / 3.0f);
-    return __fdividef(2.0f * z2, 1.0f + z) + 2.0f * z2 * z * s;
+    return x * x * rr + 2.0f * z2 * z * s;   // 2 z^2 / (1 + z) = x^2 / ((1 + x)(2 + x))
   }
   return lg2_approx(1.0f + x) * 0.693147181f - __fdividef(x, 1.0f + x);
 }
