@@ -55,12 +55,12 @@ MUFU_LG2_PER_CLK_SM = 16.0
 FP32_PER_CLK_SM = 122.0
 # DRAM traffic of one forward launch from an ncu capture, valid only for the kernel source
 # it was taken on (sha256 prefix of bang_forward.cu + bang_device.cuh); otherwise null.
-NCU_TRAFFIC = {"stamp": "b981f597b10393ff", "bytes_per_launch": 403968}
+NCU_TRAFFIC = {"stamp": "a8a345c8424ec33f", "bytes_per_launch": 404480}
 # Pipe activity of the forward kernel from the same kind of capture (ncu --set full on one
 # timed launch of the tuned benchmark batch): SFU (xu) and FMA pipes, issue active, thread
 # instructions per fine point; stamp-checked like the traffic.
-NCU_PIPES = {"stamp": "b981f597b10393ff", "pipe_xu_pct": 35.3, "pipe_fma_pct": 31.9, "pipe_fma_cycles_pct": 45.8,
-             "issue_active_pct": 66.2, "thread_instr_per_point": 435}
+NCU_PIPES = {"stamp": "a8a345c8424ec33f", "pipe_xu_pct": 35.3, "pipe_fma_pct": 32.0, "pipe_fma_cycles_pct": 45.8,
+             "issue_active_pct": 66.5, "thread_instr_per_point": 436}
 
 
 def kernel_stamp() -> str:

@@ -247,7 +247,8 @@ bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t 
                               void *stream);
 
 /* Chooses the launch parameters of bang_loglike_batch (kernel form, fine rows per block
- * step, spaxel-row bands per row) for batches of B rows by timing candidates on the device;
+ * step, spaxel-row bands per row, lanes per spaxel column of the separable stencil) for
+ * batches of B rows by timing candidates on the device;
  * the choice is cached in the model.
  * With a host gal_idx (or NULL: galaxy 0 for every row) it applies to later calls with that
  * same gal_idx and B; with a device gal_idx (read here, this call being synchronous) it
@@ -255,21 +256,23 @@ bang_status bang_loglike_fp64(bang_model *m, const double *theta, const int32_t 
 bang_status bang_model_tune(bang_model *m, const int32_t *gal_idx, int B);
 
 /* As bang_model_tune, and then the launch parameters of bang_loglike_grad_batch for the same
- * batches (the forward seed pass's spaxel-row bands and fine rows per block step, the
- * adjoint's fine rows per work item and, for the one-disc model without the radial table,
- * the adjoint's blocks per SM, 3 or 4), timed on whole logL + gradient calls.  Synchronous; a gradient call costs a
+ * batches (the forward seed pass's spaxel-row bands, fine rows per block step and stencil
+ * lanes per spaxel column, the adjoint's fine rows per work item and, for the one-disc
+ * model without the radial table, the adjoint's blocks per SM, 3 or 4), timed on whole
+ * logL + gradient calls.  Synchronous; a gradient call costs a
  * few times a logL call, so this takes correspondingly longer. */
 bang_status bang_model_tune_grad(bang_model *m, const int32_t *gal_idx, int B);
 
 /* The launch shape bang_loglike_batch (grad = 0) or bang_loglike_grad_batch (grad = 1)
- * would use for (gal_idx, B), after any bang_model_tune: info[12] (host) receives
+ * would use for (gal_idx, B), after any bang_model_tune: info[13] (host) receives
  *   0 fine rows per block step of the forward kernel, 1 spaxel-row bands per batch row,
  *   2 forward blocks per SM, 3 forward grid, 4 forward work items, 5 forward dynamic shared
  *   memory per block (bytes), 6 fine rows per adjoint work item, 7 adjoint grid,
  *   8 adjoint work items (6-8 zero when grad = 0), 9 1 when the work items are derived on
  *   the device (device gal_idx), else 0, 10 fine points per thread of the forward kernel
  *   (2: the two-point form the autotuner may choose for logL batches, 3 blocks per SM),
- *   11 adjoint blocks per SM (zero when grad = 0).
+ *   11 adjoint blocks per SM (zero when grad = 0), 12 1 when the forward kernel's separable
+ *   stencil gives each spaxel column several lanes (an autotuner choice), else 0.
  * Builds (and caches) the batch's plan like a call; launches nothing.  Synchronous.  For
  * diagnostics (the paper has no counterpart). */
 bang_status bang_model_launch_info(bang_model *m, const int32_t *gal_idx, int B, int grad, int32_t *info);

@@ -286,6 +286,7 @@ struct Plan {
   uint64_t key = 0;
   int B = 0, n_items = 0, G = 4, grid = 0, blocks_per_sm = 0;
   int max_W = 0;   // widest fine grid among the plan's galaxies (chunk_pts = G max_W)
+  int col_lanes = 0;   // FwdArgs::col_lanes of the launch
   size_t smem = 0;
   int mode = 0;
   int kmode = 0;   // the forward kernel form launched (kModeLogL2 for a tuned logL batch)
@@ -387,6 +388,8 @@ struct bang_model {
     int seed_G = 0;  // fine rows per block step of the gradient call's forward pass (0: G)
     int adj_minb = 0;  // blocks per SM of the one-disc quadrature adjoint, 3 or 4 (0: 4)
     int seed_bands = 0;  // spaxel-row bands per row of the gradient call's forward pass (0: bands)
+    int lanes = 0;       // logL launch: several lanes per spaxel column in the separable stencil
+    int seed_lanes = 0;  // the same for the gradient call's forward pass
   };
   std::map<uint64_t, Tuning> tuned;         // batch-shape key -> launch parameters
   std::mutex mu;
@@ -547,6 +550,7 @@ bang_status get_plan(bang_model* m, const int32_t* gal_idx, int B, int mode, Pla
   }
   p->smem = smem;
   p->kmode = (mode == bang::kModeLogL && tune.pair) ? bang::kModeLogL2 : mode;
+  p->col_lanes = mode == bang::kModeLogL ? tune.lanes : mode == bang::kModeSeed ? tune.seed_lanes : 0;
   const void* kp = bang::forward_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, p->kmode);
   cudaFuncAttributes fa;
   BANG_CUDA(cudaFuncGetAttributes(&fa, kp));
@@ -697,6 +701,7 @@ bang_status get_dplan(bang_model* m, int B, int mode, Plan** out) {
   }
   p->smem = smem;
   p->kmode = (mode == bang::kModeLogL && tune.pair) ? bang::kModeLogL2 : mode;
+  p->col_lanes = mode == bang::kModeLogL ? tune.lanes : mode == bang::kModeSeed ? tune.seed_lanes : 0;
   const void* kp = bang::forward_kernel_ptr(m->opts.n_quad, m->opts.n_discs, psf2d, p->kmode);
   cudaFuncAttributes fa;
   BANG_CUDA(cudaFuncGetAttributes(&fa, kp));
@@ -783,6 +788,7 @@ cudaError_t enqueue_forward(bang_model* m, Plan* p, const float* theta, int mode
   a.n_items = p->n_items;
   a.G = p->G;
   a.chunk_pts = p->G * p->max_W;
+  a.col_lanes = p->col_lanes;
   a.partial = p->d_partial.as<double>();
   a.maps = mode == bang::kModeMaps ? out : nullptr;
   a.seed = mode == bang::kModeSeed ? out : nullptr;
@@ -1486,9 +1492,9 @@ bang_status bang_model_launch_info(bang_model* m, const int32_t* gal_idx, int B,
   Plan* p = nullptr;
   bang_status s = gplace > 0 ? get_dplan(m, B, mode, &p) : get_plan(m, gal_idx, B, mode, &p);
   if (s != BANG_OK) return s;
-  const int32_t v[12] = {p->G, p->bands, p->blocks_per_sm, p->grid, p->n_items, (int32_t)p->smem,
+  const int32_t v[13] = {p->G, p->bands, p->blocks_per_sm, p->grid, p->n_items, (int32_t)p->smem,
                          grad ? p->adj_G : 0, grad ? p->adj_grid : 0, grad ? p->adj_items : 0, p->implicit ? 1 : 0,
-                         p->kmode == bang::kModeLogL2 ? 2 : 1, grad ? p->adj_blocks_per_sm : 0};
+                         p->kmode == bang::kModeLogL2 ? 2 : 1, grad ? p->adj_blocks_per_sm : 0, p->col_lanes};
   std::memcpy(info, v, sizeof v);
   return BANG_OK;
 }
@@ -1568,10 +1574,17 @@ bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) 
   float best = 1e30f;
   bang_model::Tuning best_t;
   bool any = false;
+  bool separable = false;   // the lanes-per-column choice applies to Gaussian-PSF galaxies
+  for (const bang::GalDev& g : m->gals) separable |= g.psf_kind == 0;
+  for (int lanes : {0, 1}) {
+  if (lanes && !separable) continue;
   for (int pair : {0, 1}) {
+  if (lanes && pair) continue;   // the two-point form has one thread per spaxel column
   for (int G : {1, 2, 4, 8}) {
     for (int nb : bands) {
-      m->tuned[skey] = bang_model::Tuning{G, nb, 0, pair};
+      bang_model::Tuning cand{G, nb, 0, pair};
+      cand.lanes = lanes;
+      m->tuned[skey] = cand;
       m->plans.clear();
       Plan* p = nullptr;
       if ((dgal ? get_dplan(m, B, bang::kModeLogL, &p) : get_plan(m, hgal, B, bang::kModeLogL, &p)) != BANG_OK)
@@ -1590,10 +1603,11 @@ bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) 
       }
       if (t_min < best) {
         best = t_min;
-        best_t = bang_model::Tuning{G, nb, 0, pair};
+        best_t = cand;
         any = true;
       }
     }
+  }
   }
   }
   if (!any) {
@@ -1608,28 +1622,31 @@ bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) 
   // each timed on whole logL + gradient calls
   if (grad) {
     float best_g = 1e30f;
-    int best_rows = 0, best_sg = best_t.G, best_minb = 0, best_sb = 0;
+    int best_rows = 0, best_sg = best_t.G, best_minb = 0, best_sb = 0, best_sl = 0;
     struct Cand {
-      int sb, sg, rows, minb;   // -1: the best value so far
+      int sb, sg, rows, minb, sl;   // -1: the best value so far
     };
     std::vector<Cand> cands;
     // the seed pass's bands (0: the logL launch's), chosen for its own kernel form, whose
     // blocks per SM can differ from the tuned logL form's
     for (int sb : {0, 1, 2, 3, 4, 6, 8})
-      if (sb <= ny_max && (sb == 0 || B < 2 * m->num_sms)) cands.push_back({sb, best_t.G, 0, 0});
-    for (int sg : {1, 2, 4}) cands.push_back({-1, sg, 0, 0});
-    for (int rows : {4, 8, 16, 24, 32}) cands.push_back({-1, -1, rows, 0});
-    if (m->opts.n_discs == 1 && m->opts.bulge_table == 0) cands.push_back({-1, -1, -1, 3});   // 4 is the default
+      if (sb <= ny_max && (sb == 0 || B < 2 * m->num_sms)) cands.push_back({sb, best_t.G, 0, 0, 0});
+    for (int sg : {1, 2, 4}) cands.push_back({-1, sg, 0, 0, 0});
+    for (int rows : {4, 8, 16, 24, 32}) cands.push_back({-1, -1, rows, 0, 0});
+    if (m->opts.n_discs == 1 && m->opts.bulge_table == 0) cands.push_back({-1, -1, -1, 3, 0});   // 4 is the default
+    if (separable) cands.push_back({-1, -1, -1, -1, 1});   // several lanes per column in the seed pass
     for (const Cand& c : cands) {
       const int sb = c.sb < 0 ? best_sb : c.sb;
       const int sg = c.sg < 0 ? best_sg : c.sg;
       const int rows = c.rows < 0 ? best_rows : c.rows;
-      const int minb = c.minb;
+      const int minb = c.minb < 0 ? best_minb : c.minb;
+      const int sl = c.sl < 0 ? best_sl : c.sl;
       bang_model::Tuning tg = best_t;
       tg.seed_bands = sb;
       tg.seed_G = sg;
       tg.adj_G = rows;
       tg.adj_minb = minb;
+      tg.seed_lanes = sl;
       m->tuned[skey] = tg;
       m->plans.clear();
       Plan* p = nullptr;
@@ -1659,17 +1676,20 @@ bang_status tune_paths(bang_model* m, const int32_t* gal_idx, int B, bool grad) 
         best_rows = rows;
         best_sg = sg;
         best_minb = minb;
+        best_sl = sl;
       }
     }
     best_t.seed_bands = best_sb;
     best_t.adj_G = best_rows;
     best_t.seed_G = best_sg;
     best_t.adj_minb = best_minb;
+    best_t.seed_lanes = best_sl;
   } else {
     best_t.seed_bands = prior.seed_bands;
     best_t.adj_G = prior.adj_G;
     best_t.seed_G = prior.seed_G;
     best_t.adj_minb = prior.adj_minb;
+    best_t.seed_lanes = prior.seed_lanes;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

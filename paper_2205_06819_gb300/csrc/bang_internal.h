@@ -59,6 +59,7 @@ struct FwdArgs {
   int* queue;               // dynamic item counter, zeroed before the launch (NULL = static striding)
   int G;                    // fine rows per block step (at least)
   int chunk_pts;            // > 0: a narrower galaxy's items take chunk_pts / W rows per step, as shared memory allows
+  int col_lanes;            // separable stencil: 1 = several lanes per spaxel column share its taps
   double* partial;          // [n_items] chi^2 of each item (NaN for an out-of-domain row)
   float* maps;              // kModeMaps: model maps, row b at out_off[b]
   float* seed;              // kModeSeed: d logL / dF per spaxel, row b at out_off[b]
@@ -89,6 +90,7 @@ struct AdjArgs {
   int* queue;               // dynamic item counter, zeroed before the launch (NULL = static striding)
   int G;                    // fine rows per block step (at least)
   int chunk_pts;            // > 0: a narrower galaxy's items take chunk_pts / W rows per step, as shared memory allows
+  int col_lanes;            // separable stencil: 1 = several lanes per spaxel column share its taps
   const float* seed;        // d logL / dF at the spaxels, row b at out_off[b] (NULL: b * out_stride)
   const int64_t* out_off;
   int64_t out_stride;

@@ -202,10 +202,10 @@ class Model:
     def launch_info(self, B: int, gal_idx=None, grad: bool = False) -> dict:
         """The launch shape a call on (gal_idx, B) would use (bang_model_launch_info)."""
         gi, gptr = self._gal_idx(gal_idx, B)
-        info = (ctypes.c_int32 * 12)()
+        info = (ctypes.c_int32 * 13)()
         _lib.check(_lib.lib().bang_model_launch_info(self._h, gptr, B, int(grad), info))
         keys = ["rows_per_step", "bands", "blocks_per_sm", "grid", "items", "smem_bytes", "adj_rows_per_item",
-                "adj_grid", "adj_items", "device_items", "points_per_thread", "adj_blocks_per_sm"]
+                "adj_grid", "adj_items", "device_items", "points_per_thread", "adj_blocks_per_sm", "column_lanes"]
         return dict(zip(keys, list(info)))
 
 

@@ -137,3 +137,4 @@ def test_launch_info_reports_the_plan(setup):
     assert h["adj_rows_per_item"] == 0 and g["adj_rows_per_item"] >= 1 and g["adj_items"] >= 24
     assert 1 <= g["adj_grid"] <= g["adj_items"]
     assert g["adj_blocks_per_sm"] in (3, 4) and h["adj_blocks_per_sm"] == 0
+    assert h["column_lanes"] == 0 and g["column_lanes"] == 0   # untuned: one thread per spaxel column
